@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused lattice Boltzmann warm-plasma step on GB300.
+
+Default workload: 2D Cartesian (z, x) LB at 1024 x 512 nodes (dx = 0.05
+k_p^-1), local-equilibrium closure (D = 3, k_B T / m c^2 = 1e-2), Gaussian
+driver n_b/n_0 = 0.1, sigma_z = 1, sigma_r = 0.5 k_p^-1, C = 0.1, tau = 0.53,
+FP32 population storage.  One step = one launch of the fused
+collide-stream-field kernel over the whole grid.  The metric is MLUPS (node
+updates per second, all population sets plus the field update) and the
+fraction of the measured HBM copy bandwidth that the step kernel's
+algorithmic bytes reach.
+
+Timing: W untimed steps, then K steps, each bracketed by CUDA events on the
+stream the kernel is launched on; L2 is flushed (256 MiB write) between timed
+steps, outside the events.  Under torchrun every rank runs its own replica of
+the workload; value = all ranks' node updates / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on the host cores on the same
+workload (bounded sample) and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline per closure/precision; adjoint cost ratio vs forward"
+
+WORKLOAD_2D = dict(dim=2, n=(1024, 512), dx=0.05, courant=0.1, tau=0.53, closure="lec", dv=3, mu=1e-2,
+                   alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=4.0, boundary="open", init_fields=True)
+WORKLOAD_NAME = "2d_lec_1024x512_fp32"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1],
+                    help="0: TMA-staged 2D kernel (default), 1: plain global-memory pull kernel")
+    ap.add_argument("--no-modes", action="store_true", help="skip the per-precision mode table")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def _config_block(cfg, precision, extra=None):
+    d = {"workload": WORKLOAD_NAME if precision == "fp32" else f"2d_lec_1024x512_{precision}",
+         "grid_zx": list(cfg["n"]), "dx": cfg["dx"], "courant": cfg["courant"], "tau": cfg["tau"],
+         "closure": cfg["closure"], "D": cfg["dv"], "mu": cfg["mu"], "alpha": cfg["alpha"],
+         "sigma_z": cfg["sigma_z"], "sigma_r": cfg["sigma_r"], "precision": precision,
+         "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.device), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        time.sleep(0.15)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), util=float(parts[4]),
+                                 hw=parts[6], hwt=parts[7], swt=parts[8], pcap=parts[9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        load = [r for r in rows if r["util"] >= 50] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(load)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def _time_steps(run, stream, steps, warmup, flush):
+    import torch
+    for _ in range(warmup):
+        run.step(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[k][0].record(stream)
+        run.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]  # ms
+
+
+def _traffic_for(kernel_key):
+    """Per-launch DRAM bytes of the step kernel from a committed ncu capture,
+    valid only while the kernel sources are unchanged."""
+    try:
+        from paper_2309_04872_gb300 import build as B
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tab = json.load(f)
+        ent = tab.get(kernel_key)
+        if ent and ent.get("sources_sha256") == B._sources_digest():
+            return ent.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def _oracle_sample(cfg, budget_s=15.0):
+    import oracle as O
+    o = O.Oracle(cfg)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    nsteps = max(1, int(budget_s / max(t1, 1e-6)))
+    nsteps = min(nsteps, 200)
+    t0 = time.perf_counter()
+    o.step(nsteps)
+    dt = time.perf_counter() - t0
+    ncell = 1
+    for v in cfg["n"]:
+        ncell *= v
+    return ncell * nsteps / dt / 1e6, nsteps, dt
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2309_04872_gb300 import lbpwfa as lb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lb.load_library()
+    cfg = dict(WORKLOAD_2D)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peaks, peak_kind = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    def measure(prec, steps, warmup, mu=None, variant=None):
+        c = dict(cfg)
+        if mu is not None:
+            c["mu"] = mu
+        v = a.variant if variant is None else variant
+        with lb.Run(c, prec, stream=stream.cuda_stream, variant=v) as run:
+            info = run.info()
+            times = _time_steps(run, stream, steps, warmup, flush)
+            bad = run.reduce()[2]
+        mean_ms = sum(times) / len(times)
+        mlups = info.ncell / (mean_ms * 1e-3) / 1e6
+        gbs = info.bytes_per_update * info.ncell / (mean_ms * 1e-3) / 1e9
+        return dict(mlups=mlups, ms=mean_ms, gbs=gbs, frac=gbs / hbm, bytes_per_update=info.bytes_per_update,
+                    ncell=info.ncell, total_ms=sum(times), nonfinite=bad, times=times,
+                    kernel="lb_step_tma2d_kernel" if info.kernel_variant == 0 else "lb_step_kernel")
+
+    with ClockSampler(local) as clk:
+        main = measure(a.precision, a.steps, a.warmup)
+    clocks = clk.summary()
+
+    total_s = main["total_ms"] * 1e-3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = main["ncell"] * a.steps * world / total_s / 1e6
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": round(total_s * 1e3 / a.steps, 6),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if a.precision != "fp64" else "f64",
+        "data": "synthetic",
+        "config": _config_block(cfg, a.precision, {"kernel": main["kernel"]}),
+        "roofline": {
+            "bound": "hbm", "achieved": round(main["gbs"], 2), "peak": hbm, "unit": "GB/s",
+            "frac": round(main["frac"], 4), "traffic": _traffic_for(f"lb_step_2d_lec_{a.precision}_1024x512"),
+            "bytes_per_update": main["bytes_per_update"], "peak_source": f"{peak_kind} hbm_gbs",
+        },
+        "clocks": clocks,
+        "gpu_launches": a.steps,
+    }
+    if main["nonfinite"]:
+        out["warning"] = "non-finite populations at the end of the timed run"
+
+    if rank == 0 and not a.no_modes:
+        modes = {}
+        for prec in ("fp64", "fp32", "fp16s"):
+            for mu in (1e-3, 1e-2):
+                for variant in (0, 1):
+                    steps = 300 if prec == "fp64" else 1000
+                    r = measure(prec, steps, 5, mu=mu, variant=variant)
+                    key = f"lec_{prec}_mu{mu:g}" + ("" if variant == 0 else "_plain")
+                    modes[key] = {"mlups": round(r["mlups"], 2), "ms_per_step": round(r["ms"], 5),
+                                  "achieved_gbs": round(r["gbs"], 1), "frac_of_measured_hbm": round(r["frac"], 4),
+                                  "bytes_per_update": r["bytes_per_update"], "steps": steps, "kernel": r["kernel"]}
+        out["modes"] = modes
+
+    if rank == 0 and not a.no_e2e:
+        out["e2e"] = _e2e(cfg, a, world)
+
+    if rank == 0 and world == 1 and not a.no_cpu:
+        mlups, ns, dt = _oracle_sample(cfg)
+        out["cpu_baseline"] = {"value": round(mlups, 4), "unit": "MLUPS", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": f"{ns} FP64 oracle steps of the full 1024x512 grid ({dt:.1f} s)"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def _e2e(cfg, a, world):
+    """Same metric through the public C ABI with host buffers: upload of the
+    initial state from pinned host memory, K steps, read-back of n and E_z."""
+    import torch
+
+    from paper_2309_04872_gb300 import lbpwfa as lb
+    steps = a.steps
+    with lb.Run(cfg, a.precision) as run:
+        f0, E0, B0 = run.get_state()
+        nc, K, Q = run.ncell, run.K, run.Q
+    pin = lambda x: torch.from_numpy(x).pin_memory()  # noqa: E731
+    f0p, E0p, B0p = pin(f0), pin(E0), pin(B0)
+    n_out = torch.empty((1, nc), dtype=torch.float64).pin_memory()
+    e_out = torch.empty((1, nc), dtype=torch.float64).pin_memory()
+    with lb.Run(cfg, a.precision) as run:
+        run.set_state(f0p, E0p, B0p)  # first call allocates the staging buffer
+        run.step(2)
+        run.moments(lb.M_N, out=n_out)
+        run.synchronize()
+        t0 = time.perf_counter()
+        run.set_state(f0p, E0p, B0p)
+        run.step(steps)
+        run.moments(lb.M_N, out=n_out)
+        run.fields(lb.F_EZ, out=e_out)
+        t1 = time.perf_counter()
+    h2d = (f0.nbytes + E0.nbytes + B0.nbytes) / steps
+    d2h = (n_out.numel() + e_out.numel()) * 8 / steps
+    return {"value": round(nc * steps * world / (t1 - t0) / 1e6, 3), "unit": "MLUPS",
+            "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1),
+            "note": "lbpwfa_set_state from pinned host + lbpwfa_step(K) + lbpwfa_moments/fields to host"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    cfg = dict(WORKLOAD_2D)
+    o = O.Oracle(cfg)
+    for _ in range(max(0, min(a.warmup, 3))):
+        o.step(1)
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    budget = 120.0
+    nsteps = max(1, min(a.steps, int(budget / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(nsteps)
+    dt = time.perf_counter() - t0
+    ncell = cfg["n"][0] * cfg["n"][1]
+    value = ncell * nsteps / dt / 1e6
+    sample = f"{nsteps} FP64 oracle steps of the full 1024x512 grid ({dt:.1f} s)"
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": round(dt * 1e3 / nsteps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config_block(cfg, a.precision, {"impl": "oracle"}),
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -1,0 +1,194 @@
+/*
+ * lbpwfa: lattice Boltzmann warm-plasma wakefield solver for NVIDIA GB300
+ * (sm_103a).  C ABI of the CUDA library liblbpwfa.so.
+ *
+ * The method is the moment-matching lattice Boltzmann (LB) scheme of
+ * arXiv 2309.04872 (Simeoni et al.): every advected scalar A_k of a warm
+ * relativistic electron fluid is carried by its own set of populations f_ki
+ * on a D1Q3 / D2Q9 / D3Q19 lattice (Sec. 2.2, Eq. ade-feq, lbe), the fluid is
+ * closed either by the local-equilibrium closure LEC (Sec. 4, Eq.
+ * lb-ade-lec-comps-A/F) or by the warm-plasma closure WARMC (Sec. 5, Eq.
+ * lb-ade-warmc-comps-A/F, App. A), and it is coupled to an FDTD Maxwell
+ * solver driven by a rigid Gaussian bunch moving at c (Sec. 6, Eq.
+ * bunch-density).
+ *
+ * Units (Sec. 6): length k_p^-1, time omega_p^-1, density n_i, momentum m c,
+ * velocity c, E in m c omega_p / e, B in E/c.
+ *
+ * Common conventions
+ *  - Spatial axes: z (driver direction), x, y.  A 1D run uses z; 2D uses
+ *    (z, x) with fields (E_z, E_x, B_y); 3D uses (z, x, y).
+ *  - Cell index c = iz + nz * (ix + nx * iy) (z fastest) for every host or
+ *    device array crossing this interface (unpadded).
+ *  - Node positions: z = iz dx, x = (ix - (nx-1)/2) dx, y = (iy - (ny-1)/2) dx.
+ *  - Fields live on a dual Yee grid: E_a half a cell up along the two axes
+ *    other than a, B_a half a cell up along a.  E is stored at t_{n-1/2},
+ *    B at t_n, populations at t_n.  Transverse boundaries are conducting
+ *    walls half a cell outside the outermost nodes.
+ *  - Populations f[k][i][c]: k = advected scalar, i = lattice velocity in the
+ *    order below, c = cell.  Advected scalars:
+ *      LEC  : n, n H p_z, (n H p_x), (n H p_y),
+ *             H = 1 + (1 + D/2) mu (n/gamma)^(2/D)
+ *      WARMC: n, n lambda, n lambda u_z, (n lambda u_x), (n lambda u_y),
+ *             lambda theta^{ab} for the pairs
+ *             1D: zz;  2D: zz, xx, yy, zx;  3D: zz, xx, yy, zx, zy, xy.
+ *  - Velocity order (components z, x, y):
+ *      D1Q3 : 0, +z, -z
+ *      D2Q9 : 0, +z, -z, +x, -x, (+z+x), (-z-x), (+z-x), (-z+x)
+ *      D3Q19: 0, +z, -z, +x, -x, +y, -y, (+z+x), (-z-x), (+z-x), (-z+x),
+ *             (+z+y), (-z-y), (+z-y), (-z+y), (+x+y), (-x-y), (+x-y), (-x+y)
+ *  - Every function returns an lbpwfa_status; nothing else crosses the ABI
+ *    (no exceptions, no exit).  A handle must not be used from two host
+ *    threads at once.  Work is queued on the handle's stream; functions that
+ *    return host data synchronise that stream.
+ */
+#ifndef LBPWFA_H
+#define LBPWFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbpwfa_s* lbpwfa_t;
+
+typedef enum {
+  LBPWFA_OK = 0,
+  LBPWFA_ERR_INVALID = -1,    /* bad argument or parameter */
+  LBPWFA_ERR_OOM = -2,        /* device or host allocation failed */
+  LBPWFA_ERR_CUDA = -3,       /* a CUDA call failed; see lbpwfa_last_error */
+  LBPWFA_ERR_NONFINITE = -4,  /* a NaN/Inf population was found */
+  LBPWFA_ERR_TIMEOUT = -5,    /* a bounded device wait gave up */
+  LBPWFA_ERR_STATE = -6,      /* call not valid in the handle's state */
+  LBPWFA_ERR_IO = -7          /* checkpoint file error or CRC mismatch */
+} lbpwfa_status;
+
+enum { LBPWFA_LEC = 0, LBPWFA_WARMC = 1 };
+enum { LBPWFA_FP64 = 0, LBPWFA_FP32 = 1, LBPWFA_FP16S = 2 };
+enum { LBPWFA_OPEN = 0, LBPWFA_PERIODIC = 1 };
+
+/* Problem statement (Sec. 6, Eq. bunch-density and Qtilde). */
+typedef struct {
+  int dim;                 /* 1, 2 or 3 */
+  int n[3];                /* nodes along z, x, y; absent axes ignored; >= 3 */
+  double dx;               /* lattice spacing, k_p^-1 */
+  double courant;          /* C = c dt / dx; dt = C dx. 0 < C <= 1/sqrt(dim) */
+  double tau;              /* BGK relaxation time in units of dt, > 1/2
+                              (Eq. diff-coeff: kappa = nu^2 (tau - 1/2)) */
+  int closure;             /* LBPWFA_LEC or LBPWFA_WARMC */
+  int dv;                  /* kinetic momentum dimensions D: 1 or 3 */
+  double mu;               /* k_B T_i / (m c^2) >= 0 */
+  double alpha;            /* driver peak n_b / n_i */
+  double sigma_z;          /* rms length of the driver, k_p^-1 (> 0) */
+  double sigma_r;          /* rms radius of the driver, k_p^-1 (> 0, 2D/3D) */
+  double z0;               /* driver centre at t = 0, k_p^-1 */
+  const double* profile;   /* optional longitudinal profile L(zeta) sampled at
+                              zeta_j = (j - (len-1)/2) profile_dz about the
+                              driver centre, linearly interpolated, 0 outside;
+                              replaces alpha exp(-zeta^2/2 sigma_z^2).
+                              Copied at create; NULL for the Gaussian. */
+  int profile_len;         /* >= 2 when profile != NULL */
+  double profile_dz;       /* > 0 when profile != NULL */
+  int precision;           /* population storage: FP64, FP32 (deviation from
+                              w_i A_rest), FP16S (binary16 deviation, scaled) */
+  int boundary;            /* LBPWFA_OPEN (Eq. open-bc; conducting transverse
+                              walls) or LBPWFA_PERIODIC (all axes) */
+  int init_fields;         /* 1: start from the v -> c field of the driver
+                              (2D, 3D); 0: zero fields */
+  void* stream;            /* cudaStream_t to queue work on; NULL = a stream
+                              owned by the library */
+  int kernel_variant;      /* 0: automatic (2D open-boundary runs stage each
+                              tile's populations in shared memory with a TMA
+                              bulk-tensor load), 1: plain global-memory pull.
+                              Both compute the same step. */
+} lbpwfa_params;
+
+typedef struct {
+  int K;                   /* advected scalars */
+  int Q;                   /* lattice velocities */
+  int64_t ncell;           /* nodes */
+  int64_t step;            /* steps taken */
+  double dt;               /* time step, omega_p^-1 */
+  double time;             /* step * dt */
+  size_t device_bytes;     /* device memory held by the handle */
+  double bytes_per_update; /* algorithmic HBM bytes of one node update of the
+                              step kernel (populations + fields [+ WARMC
+                              previous-step values]) */
+  int kernel_variant;      /* step kernel in use: 0 TMA-staged, 1 plain */
+} lbpwfa_info_t;
+
+/* Create a run: validates *p, allocates all device state on the handle's
+ * stream and sets the rest state n = 1, u = 0 (f = f^eq, Eq. ade-feq) with
+ * the initial fields.  The library owns all device memory; *out receives the
+ * handle.  Errors: INVALID (bad parameters, out == NULL), OOM, CUDA. */
+int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out);
+
+/* Advance nsteps >= 0 time steps (Sec. 2.1 algorithm with the Sec. 4.1
+ * coupling): decode, E^{n+1/2} = E^{n-1/2} + dt (curl B^n + n u + n_b z),
+ * B^{n+1} = B^n - dt curl E^{n+1/2}, sources with E^{n+1/2} and B^n,
+ * BGK + w_i dt F, pull streaming with the open-boundary copy.
+ * One fused kernel launch per step; asynchronous.  Errors: INVALID, CUDA. */
+int lbpwfa_step(lbpwfa_t h, int64_t nsteps);
+
+/* Macroscopic fields decoded in FP64 from the current populations.
+ * mask bits (output blocks in increasing bit order, each ncell doubles):
+ *   0 n, 1 u_z, 2 u_x, 3 u_y, 4 gamma, 5 p_z, 6 p_x, 7 p_y (gamma u),
+ *   8 LEC rest-frame pressure P0 = mu (n/gamma)^(1+2/D) (0 for WARMC),
+ *   9 lambda = n/h (WARMC; 0 for LEC),
+ *   10..15 theta zz, xx, yy, zx, zy, xy (WARMC; 0 for LEC).
+ * dst holds count >= popcount(mask & 0xFFFF) * ncell doubles, on the device
+ * when dst_is_device, else on the host.  Errors: INVALID, CUDA. */
+int lbpwfa_moments(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_is_device);
+
+/* Raw field slots (FP64), mask bits 0 E_x, 1 E_y, 2 E_z, 3 B_x, 4 B_y, 5 B_z;
+ * E at t_{n-1/2}, B at t_n, on the dual Yee grid described above. */
+int lbpwfa_fields(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_is_device);
+
+/* Advected scalars A_k = sum_i f_ki (Eq. disc-moments-ade), FP64,
+ * [K][ncell]; count >= K * ncell. */
+int lbpwfa_advected(lbpwfa_t h, double* dst, size_t count, int dst_is_device);
+
+/* Replace the state: f = populations at t_n after streaming, FP64
+ * [K][Q][ncell]; E [3][ncell] (z, x, y) at t_{n-1/2}; B [3][ncell] at t_n.
+ * Any pointer may be NULL to keep that part.  With open boundaries the
+ * boundary nodes take the populations of their nearest bulk node
+ * (Eq. open-bc) and wall slots of E are zeroed.  The backward time
+ * differences of WARMC restart (zero on the next step).
+ * Errors: INVALID, OOM, CUDA. */
+int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double* B,
+                     int src_is_device);
+
+/* Read the state in the layout of lbpwfa_set_state (FP64). */
+int lbpwfa_get_state(lbpwfa_t h, double* f, double* E, double* B, int dst_is_device);
+
+/* FP64 global sums over nodes, in a fixed order (deterministic):
+ * out[0] = sum n, out[1] = sum n_b(t_n), out[2] = number of non-finite
+ * populations.  Synchronises.  Returns NONFINITE when out[2] > 0. */
+int lbpwfa_reduce(lbpwfa_t h, double out[3]);
+
+int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info);
+
+/* Checkpoint: binary file with a header (parameters, step, precision), the
+ * stored populations, fields and WARMC previous-step values, and a CRC32.
+ * Resume is bitwise.  lbpwfa_load requires a handle created with the same
+ * parameters.  Errors: IO (open/short read/CRC/header mismatch), CUDA. */
+int lbpwfa_save(lbpwfa_t h, const char* path);
+int lbpwfa_load(lbpwfa_t h, const char* path);
+
+/* Queue subsequent work on another stream (NULL = the library stream). */
+int lbpwfa_set_stream(lbpwfa_t h, void* stream);
+/* Wait for the handle's queued work; returns TIMEOUT when a bounded device
+ * wait gave up (the step is then incomplete). */
+int lbpwfa_synchronize(lbpwfa_t h);
+
+void lbpwfa_destroy(lbpwfa_t h);
+const char* lbpwfa_status_string(int status);
+/* Text of the last CUDA error seen by this handle ("" if none). */
+const char* lbpwfa_last_error(lbpwfa_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBPWFA_H */

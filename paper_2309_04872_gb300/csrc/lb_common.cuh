@@ -1,0 +1,261 @@
+// Device-side building blocks of the GB300 lattice Boltzmann warm-plasma
+// solver: lattice tables, model traits, launch parameters, storage codecs,
+// closure decoders and the boundary index rules.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbp {
+
+enum { CL_LEC = 0, CL_WARMC = 1 };
+enum { PR_F64 = 0, PR_F32 = 1, PR_F16S = 2 };
+
+// ---------------------------------------------------------------------------
+// Lattices.  D3Q19 is the set of Fig. 1 (weights 1/3, 1/18, 1/36); D1Q3 and
+// D2Q9 are its 1D and 2D members with the same nu^2 = 1/3 (Eq. ade-feq).
+// Velocity order is part of the ABI (lbpwfa.h).  Component index 0 = z,
+// 1 = x, 2 = y.
+// ---------------------------------------------------------------------------
+template <int DIM> struct Lattice;
+
+template <> struct Lattice<1> {
+  static constexpr int Q = 3;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    return a != 0 ? 0 : (i == 1 ? 1 : (i == 2 ? -1 : 0));
+  }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+};
+
+template <> struct Lattice<2> {
+  static constexpr int Q = 9;
+  // 0 rest, 1 +z, 2 -z, 3 +x, 4 -x, 5 +z+x, 6 -z-x, 7 +z-x, 8 -z+x
+  __host__ __device__ static constexpr int c(int i, int a) {
+    return a == 0 ? ((i == 1 || i == 5 || i == 7) ? 1 : ((i == 2 || i == 6 || i == 8) ? -1 : 0))
+         : a == 1 ? ((i == 3 || i == 5 || i == 8) ? 1 : ((i == 4 || i == 6 || i == 7) ? -1 : 0))
+                  : 0;
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+};
+
+template <> struct Lattice<3> {
+  static constexpr int Q = 19;
+  // 0 rest; faces 1..6: +z -z +x -x +y -y; edges 7..18:
+  // (+z+x) (-z-x) (+z-x) (-z+x) (+z+y) (-z-y) (+z-y) (-z+y) (+x+y) (-x-y) (+x-y) (-x+y)
+  __host__ __device__ static constexpr int c(int i, int a) {
+    return a == 0 ? cz(i) : (a == 1 ? cx(i) : cy(i));
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : ((i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : ((i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Model traits.  K advected scalars per closure (Sec. 4.1 LEC: n, n H p;
+// Sec. 5.1 WARMC: n, n w^beta, n theta^{beta gamma} / h) and the record of
+// decoded values each node publishes to its neighbours (shared memory).
+//   LEC   record: n, u[DIM], Pi = (n/gamma)^(1+2/D)
+//   WARMC record: n, lambda, u[DIM], theta pairs[NTH], theta^{0a}[DIM]
+// WARMC theta pairs: 1D zz; 2D zz xx yy zx; 3D zz xx yy zx zy xy.
+// ---------------------------------------------------------------------------
+template <int DIM, int CL> struct Model {
+  static constexpr int Q = Lattice<DIM>::Q;
+  static constexpr int NTH = CL == CL_WARMC ? (DIM == 1 ? 1 : (DIM == 2 ? 4 : 6)) : 0;
+  static constexpr int K = CL == CL_LEC ? 1 + DIM : 2 + DIM + NTH;
+  static constexpr int NM = CL == CL_LEC ? 2 + DIM : 2 + 2 * DIM + NTH;
+  static constexpr int NPREV = CL == CL_WARMC ? 1 + 2 * DIM : 0;  // th00, th0[DIM], w[DIM]
+  // record slots
+  static constexpr int R_N = 0;
+  static constexpr int R_U = CL == CL_LEC ? 1 : 2;
+  static constexpr int R_PI = 1 + DIM;          // LEC
+  static constexpr int R_LAM = 1;               // WARMC
+  static constexpr int R_TH = 2 + DIM;          // WARMC
+  static constexpr int R_TH0 = 2 + DIM + NTH;   // WARMC
+  __host__ __device__ static constexpr int tha(int j) {
+    return j == 0 ? 0 : (j == 1 ? 1 : (j == 2 ? 2 : (j == 3 ? 0 : (j == 4 ? 0 : 1))));
+  }
+  __host__ __device__ static constexpr int thb(int j) {
+    return j == 0 ? 0 : (j == 1 ? 1 : (j == 2 ? 2 : (j == 3 ? 1 : (j == 4 ? 2 : 2))));
+  }
+  // index of pair (a, b) in the stored list, -1 if not stored
+  __host__ __device__ static constexpr int thidx(int a, int b) {
+    return DIM == 1 ? ((a == 0 && b == 0) ? 0 : -1)
+         : (a == b ? a
+            : (((a == 0 && b == 1) || (a == 1 && b == 0)) ? (DIM >= 2 ? 3 : -1)
+               : (((a == 0 && b == 2) || (a == 2 && b == 0)) ? (DIM == 3 ? 4 : -1)
+                  : (DIM == 3 ? 5 : -1))));
+  }
+};
+
+template <int PR> struct Prec;
+template <> struct Prec<PR_F64> { using real = double; using store = double; };
+template <> struct Prec<PR_F32> { using real = float; using store = float; };
+template <> struct Prec<PR_F16S> { using real = float; using store = __half; };
+
+// Present field components on the dual Yee grid (component index z, x, y).
+template <int DIM> __host__ __device__ constexpr bool e_present(int a) {
+  return DIM == 1 ? a == 0 : (DIM == 2 ? (a == 0 || a == 1) : true);
+}
+template <int DIM> __host__ __device__ constexpr bool b_present(int a) {
+  return DIM == 1 ? false : (DIM == 2 ? a == 2 : true);
+}
+template <int DIM> __host__ __device__ constexpr bool axis_present(int a) { return a < DIM; }
+
+// ---------------------------------------------------------------------------
+// Launch parameters of the step kernel (all derived on the host).  Every
+// scalar the kernel computes with comes pre-converted in both precisions
+// (StepConst), so no double -> float conversion runs on the device.
+// ---------------------------------------------------------------------------
+template <typename real>
+struct StepConst {
+  real dx, idx, i2dx;     // dx, 1/dx, 1/(2 dx)
+  real dt, idt;           // dt, 1/dt
+  real courant, inv_tau;  // C, 1/tau
+  real mu, cH;            // mu, (1 + D/2) mu
+  real zeta0;             // driver centre z0 + t_n
+  real alpha, inv2sz2, inv2sr2;
+  real xoff, yoff;        // (nx-1)/2, (ny-1)/2
+  real pdz_inv, phalf;    // 1/profile_dz, (len-1)/2
+  real Arest[11];
+};
+
+struct StepParams {
+  const void* fin;       // populations, stored deviations, [K][Q][plane]
+  void* fout;
+  const void* Ein;       // E^{n-1/2} slots [3][plane] (real)
+  void* Eout;            // E^{n+1/2}
+  const void* Bin;       // B^n
+  void* Bout;            // B^{n+1}
+  void* prev;            // WARMC previous-step th00, th0[DIM], w[DIM]: [NPREV][plane]
+  int have_prev;
+  int n[3];              // nodes along z, x, y (1 for absent axes)
+  int nzp;               // padded row pitch along z
+  long long plane;       // nzp * nx * ny (Q * plane < 2^31 is enforced)
+  int axis_stride[3];    // 1, nzp, nzp * nx
+  int periodic;
+  int D;
+  const double* profile; int plen;
+  float inv_scale[11];   // FP16S: 1/s_k
+  float scale[11];       // FP16S: s_k
+  int* err;              // device error word (bit 0: a bounded wait gave up)
+  StepConst<float> cf;
+  StepConst<double> cd;
+};
+
+template <typename real> __device__ __forceinline__ const StepConst<real>& consts(const StepParams& P);
+template <> __device__ __forceinline__ const StepConst<float>& consts<float>(const StepParams& P) { return P.cf; }
+template <> __device__ __forceinline__ const StepConst<double>& consts<double>(const StepParams& P) { return P.cd; }
+
+// Storage codec: populations are kept as deviations from w_i A_rest,k.
+template <int PR> struct Codec;
+template <> struct Codec<PR_F64> {
+  __device__ static double load(const double* p, long long i, float) { return __ldg(p + i); }
+  __device__ static void store(double* p, long long i, double v, float) { p[i] = v; }
+};
+template <> struct Codec<PR_F32> {
+  __device__ static float load(const float* p, long long i, float) { return __ldg(p + i); }
+  __device__ static void store(float* p, long long i, float v, float) { p[i] = v; }
+};
+template <> struct Codec<PR_F16S> {
+  __device__ static float load(const __half* p, long long i, float inv_s) {
+    return __half2float(__ldg(p + i)) * inv_s;
+  }
+  __device__ static void store(__half* p, long long i, float v, float s) {
+    p[i] = __float2half_rn(v * s);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Index rules.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrap_or_clamp(int v, int n, int periodic) {
+  if (periodic) return v < 0 ? v + n : (v >= n ? v - n : v);
+  return v < 0 ? 0 : (v >= n ? n - 1 : v);
+}
+__device__ __forceinline__ int cell_index32(const StepParams& P, int z, int x, int y) {
+  return z + x * P.axis_stride[1] + y * P.axis_stride[2];
+}
+
+__device__ __forceinline__ float rsqrt_t(float x) { return 1.0f / sqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+
+// Power (n/gamma)^(2/D) of the LEC closure (Eq. temp-scaling).
+template <typename real> __device__ __forceinline__ real pow_2_over_D(real x, int D);
+template <> __device__ __forceinline__ double pow_2_over_D<double>(double x, int D) {
+  return D == 1 ? x * x : (D == 3 ? cbrt(x * x) : x);
+}
+template <> __device__ __forceinline__ float pow_2_over_D<float>(float x, int D) {
+  return D == 1 ? x * x : (D == 3 ? cbrtf(x * x) : x);
+}
+
+// LEC transport velocity, Sec. 4.1: p^(0) = A_p / n, then
+// gamma^(k) = sqrt(1 + |p^(k)|^2), p^(k+1) = p^(0) / (1 + (1 + D/2) mu (n/gamma^(k))^(2/D)),
+// stopped when the largest change is within a few ulps of the largest |p|.
+// cH = (1 + D/2) mu.
+template <int DIM, typename real>
+__device__ __forceinline__ void decode_lec(real n, const real* Ap, real cH, int D, real* u, real& Pi,
+                                           real* gamma_out = nullptr) {
+  constexpr bool dbl = sizeof(real) == 8;
+  const real tol = dbl ? real(1e-15) : real(4e-7);
+  const int maxit = dbl ? 64 : 32;
+  const real in_ = real(1) / n;
+  real p0[DIM], p[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { p0[a] = Ap[a] * in_; p[a] = p0[a]; }
+  for (int it = 0; it < maxit; ++it) {
+    real s = real(1);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) s += p[a] * p[a];
+    const real ig = rsqrt_t(s);
+    const real iH = real(1) / (real(1) + cH * pow_2_over_D<real>(n * ig, D));
+    real d = 0, pm = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const real pn = p0[a] * iH;
+      d = fmax(d, fabs(pn - p[a]));
+      pm = fmax(pm, fabs(pn));
+      p[a] = pn;
+    }
+    if (d <= tol * pm) break;
+  }
+  real s = real(1);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) s += p[a] * p[a];
+  const real g = sqrt(s);
+  const real ig = real(1) / g;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) u[a] = p[a] * ig;
+  const real x = n * ig;
+  Pi = x * pow_2_over_D<real>(x, D);
+  if (gamma_out) *gamma_out = g;
+}
+
+// Driver longitudinal factor L(zeta) (Eq. bunch-density, rms reading).
+template <typename real>
+__device__ __forceinline__ real driver_long(const StepParams& P, const StepConst<real>& S, real zeta) {
+  if (P.profile) {
+    const real q = zeta * S.pdz_inv + S.phalf;
+    if (q < real(0) || q > real(P.plen - 1)) return real(0);
+    const int j = (int)floor(q);
+    if (j >= P.plen - 1) return real(P.profile[P.plen - 1]);
+    const real fr = q - real(j);
+    return (real(1) - fr) * real(P.profile[j]) + fr * real(P.profile[j + 1]);
+  }
+  return S.alpha * exp(-zeta * zeta * S.inv2sz2);
+}
+
+}  // namespace lbp

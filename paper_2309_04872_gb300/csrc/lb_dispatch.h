@@ -1,0 +1,43 @@
+// Kernel table of one (dimension, closure, precision) combination; the
+// runtime picks one at create time.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lbp {
+
+struct StepParams;
+struct AuxParams;
+
+struct KernelSet {
+  int tz, tx, ty;        // step tile
+  size_t step_smem;      // dynamic shared memory of the step kernel
+  cudaError_t (*prepare)();
+  void (*step)(const StepParams&, dim3 grid, cudaStream_t);
+  void (*init_fields)(const AuxParams&, void* E, void* B, cudaStream_t);
+  void (*import_pops)(const AuxParams&, const double* src, void* dst, cudaStream_t);
+  void (*export_pops)(const AuxParams&, const void* src, double* dst, cudaStream_t);
+  void (*advected)(const AuxParams&, const void* src, double* dst, cudaStream_t);
+  void (*moments)(const AuxParams&, const void* src, uint32_t mask, double* dst, cudaStream_t);
+  void (*import_fields)(const AuxParams&, const double* E, const double* B, void* Ed, void* Bd, cudaStream_t);
+  void (*export_fields)(const AuxParams&, const void* E, const void* B, int ncomp, int4 comps, int4 isb,
+                        double* dst, cudaStream_t);
+  void (*reduce_partial)(const AuxParams&, const void* src, double* partial, int nblk, cudaStream_t);
+  // TMA-staged 2D step (open boundaries); has_tma == false when not built
+  bool has_tma;
+  int tma_tz, tma_tx;            // tile
+  int tma_box[3];                // box extent (z, x, planes) in elements
+  int tma_halo_z;                // box starts this many elements before the tile
+  int tma_elem_bytes;
+  size_t tma_smem;
+  cudaError_t (*prepare_tma)();
+  void (*step_tma)(const StepParams&, const void* tensor_map, dim3 grid, cudaStream_t);
+};
+
+bool kernels_f64(int dim, int closure, KernelSet* ks);
+bool kernels_f32(int dim, int closure, KernelSet* ks);
+bool kernels_f16s(int dim, int closure, KernelSet* ks);
+
+}  // namespace lbp

@@ -1,0 +1,109 @@
+// Instantiation of the kernel table for one storage precision.
+#pragma once
+
+#include "lb_aux.cuh"
+#include "lb_dispatch.h"
+#include "lb_step_tma.cuh"
+
+namespace lbp {
+
+template <int DIM> struct Tile;
+template <> struct Tile<1> { static constexpr int TZ = 128, TX = 1, TY = 1; };
+template <> struct Tile<2> { static constexpr int TZ = 32, TX = 8, TY = 1; };
+template <> struct Tile<3> { static constexpr int TZ = 32, TX = 4, TY = 2; };
+
+inline unsigned grid1(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <int DIM, int CL, int PR>
+struct Impl {
+  using T = Tile<DIM>;
+  using Cfg = StepCfg<DIM, CL, PR, T::TZ, T::TX, T::TY>;
+  using real = typename Prec<PR>::real;
+  using store = typename Prec<PR>::store;
+
+  static cudaError_t prepare() {
+    return cudaFuncSetAttribute(lb_step_kernel<DIM, CL, PR, T::TZ, T::TX, T::TY>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes);
+  }
+  static void step(const StepParams& P, dim3 grid, cudaStream_t s) {
+    lb_step_kernel<DIM, CL, PR, T::TZ, T::TX, T::TY><<<grid, Cfg::NT, Cfg::smem_bytes, s>>>(P);
+  }
+  static void init_fields(const AuxParams& A, void* E, void* B, cudaStream_t s) {
+    init_fields_kernel<DIM, real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, (real*)E, (real*)B);
+  }
+  static void import_pops(const AuxParams& A, const double* src, void* dst, cudaStream_t s) {
+    import_pops_kernel<DIM, CL, PR><<<grid1(A.ncell, 128), 128, 0, s>>>(A, src, (store*)dst);
+  }
+  static void export_pops(const AuxParams& A, const void* src, double* dst, cudaStream_t s) {
+    export_pops_kernel<DIM, CL, PR><<<grid1(A.ncell, 128), 128, 0, s>>>(A, (const store*)src, dst);
+  }
+  static void advected(const AuxParams& A, const void* src, double* dst, cudaStream_t s) {
+    advected_kernel<DIM, CL, PR><<<grid1(A.ncell, 128), 128, 0, s>>>(A, (const store*)src, dst);
+  }
+  static void moments(const AuxParams& A, const void* src, uint32_t mask, double* dst, cudaStream_t s) {
+    moments_kernel<DIM, CL, PR><<<grid1(A.ncell, 128), 128, 0, s>>>(A, (const store*)src, mask, dst);
+  }
+  static void import_fields(const AuxParams& A, const double* E, const double* B, void* Ed, void* Bd,
+                            cudaStream_t s) {
+    import_fields_kernel<DIM, real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, E, B, (real*)Ed, (real*)Bd);
+  }
+  static void export_fields(const AuxParams& A, const void* E, const void* B, int ncomp, int4 comps,
+                            int4 isb, double* dst, cudaStream_t s) {
+    export_fields_kernel<real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, (const real*)E, (const real*)B, ncomp,
+                                                                    comps, isb, dst);
+  }
+  static void reduce_partial(const AuxParams& A, const void* src, double* partial, int nblk, cudaStream_t s) {
+    reduce_partial_kernel<DIM, CL, PR><<<nblk, 256, 0, s>>>(A, (const store*)src, partial);
+  }
+  using TC = TmaCfg2D<CL, PR>;
+  static constexpr bool kTma = DIM == 2 && TC::enabled;
+  static cudaError_t prepare_tma() {
+    if constexpr (kTma)
+      return cudaFuncSetAttribute(lb_step_tma2d_kernel<CL, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TC::smem_bytes);
+    return cudaErrorNotSupported;
+  }
+  static void step_tma(const StepParams& P, const void* map, dim3 grid, cudaStream_t s) {
+    if constexpr (kTma)
+      lb_step_tma2d_kernel<CL, PR><<<grid, TC::TZ * TC::TX, TC::smem_bytes, s>>>(
+          P, *reinterpret_cast<const CUtensorMap*>(map));
+  }
+  static void fill(KernelSet* ks) {
+    ks->has_tma = kTma;
+    ks->tma_tz = TC::TZ;
+    ks->tma_tx = TC::TX;
+    ks->tma_box[0] = TC::BZ;
+    ks->tma_box[1] = TC::BX;
+    ks->tma_box[2] = TC::BK;
+    ks->tma_halo_z = TC::HZ;
+    ks->tma_elem_bytes = (int)sizeof(store);
+    ks->tma_smem = TC::smem_bytes;
+    ks->prepare_tma = &prepare_tma;
+    ks->step_tma = &step_tma;
+    ks->tz = T::TZ; ks->tx = T::TX; ks->ty = T::TY;
+    ks->step_smem = Cfg::smem_bytes;
+    ks->prepare = &prepare;
+    ks->step = &step;
+    ks->init_fields = &init_fields;
+    ks->import_pops = &import_pops;
+    ks->export_pops = &export_pops;
+    ks->advected = &advected;
+    ks->moments = &moments;
+    ks->import_fields = &import_fields;
+    ks->export_fields = &export_fields;
+    ks->reduce_partial = &reduce_partial;
+  }
+};
+
+template <int PR>
+bool kernels_for(int dim, int closure, KernelSet* ks) {
+  if (dim == 1 && closure == CL_LEC) { Impl<1, CL_LEC, PR>::fill(ks); return true; }
+  if (dim == 1 && closure == CL_WARMC) { Impl<1, CL_WARMC, PR>::fill(ks); return true; }
+  if (dim == 2 && closure == CL_LEC) { Impl<2, CL_LEC, PR>::fill(ks); return true; }
+  if (dim == 2 && closure == CL_WARMC) { Impl<2, CL_WARMC, PR>::fill(ks); return true; }
+  if (dim == 3 && closure == CL_LEC) { Impl<3, CL_LEC, PR>::fill(ks); return true; }
+  if (dim == 3 && closure == CL_WARMC) { Impl<3, CL_WARMC, PR>::fill(ks); return true; }
+  return false;
+}
+
+}  // namespace lbp

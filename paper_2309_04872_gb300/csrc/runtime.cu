@@ -1,0 +1,731 @@
+// Host runtime of liblbpwfa.so: the C ABI declared in include/lbpwfa.h.
+// It owns all device state of a run (double-buffered populations and fields,
+// WARMC previous-step values, reduction partials), validates the problem
+// statement and queues the kernels of lb_step.cuh / lb_aux.cuh on the
+// handle's stream.  No compute happens on the host.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbpwfa.h"
+#include "lb_aux.cuh"
+#include "lb_dispatch.h"
+
+using namespace lbp;
+
+namespace {
+
+constexpr int kReduceBlocks = 256;   // fixed: the FP64 sums do not depend on the GPU
+constexpr float kF16Scale = 1024.0f; // binary16 deviations are stored times 2^10
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct lbpwfa_s {
+  lbpwfa_params prm{};
+  std::vector<double> profile_h;
+  double* profile_d = nullptr;
+  KernelSet ks{};
+  int K = 0, Q = 0, NPREV = 0;
+  int n[3] = {1, 1, 1};
+  int nzp = 0;
+  long long plane = 0, ncell = 0;
+  size_t store_sz = 0, real_sz = 0;
+  double dt = 0.0;
+  long long step = 0;
+  int cur = 0;  // index of the buffers holding the current state
+  Buf f[2], E[2], B[2], prev, partial, out3, scratch;
+  int have_prev = 0;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  double Arest[11] = {0};
+  float scale[11], inv_scale[11];
+  size_t device_bytes = 0;
+  std::string err;
+  bool use_tma = false;
+  alignas(64) CUtensorMap maps[2];
+  int* err_d = nullptr;  // device error word written by bounded waits
+};
+
+namespace {
+
+int fail_cuda(lbpwfa_s* h, cudaError_t e, const char* what) {
+  if (h) {
+    h->err = std::string(what) + ": " + cudaGetErrorString(e);
+  }
+  return LBPWFA_ERR_CUDA;
+}
+
+#define CK(h, call)                                       \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return fail_cuda((h), e_, #call); \
+  } while (0)
+
+#define CK_LAUNCH(h, what)                                \
+  do {                                                    \
+    cudaError_t e_ = cudaGetLastError();                  \
+    if (e_ != cudaSuccess) return fail_cuda((h), e_, what); \
+  } while (0)
+
+int alloc(lbpwfa_s* h, Buf& b, size_t bytes) {
+  if (bytes == 0) return LBPWFA_OK;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    b.p = nullptr;
+    return LBPWFA_ERR_OOM;
+  }
+  b.bytes = bytes;
+  h->device_bytes += bytes;
+  return LBPWFA_OK;
+}
+
+void release(Buf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+int ensure_scratch(lbpwfa_s* h, size_t bytes) {
+  if (h->scratch.bytes >= bytes) return LBPWFA_OK;
+  if (h->scratch.p) {
+    cudaStreamSynchronize(h->stream);
+    h->device_bytes -= h->scratch.bytes;
+    release(h->scratch);
+  }
+  return alloc(h, h->scratch, bytes);
+}
+
+int validate(const lbpwfa_params* p) {
+  if (!p) return LBPWFA_ERR_INVALID;
+  if (p->dim < 1 || p->dim > 3) return LBPWFA_ERR_INVALID;
+  for (int a = 0; a < p->dim; ++a)
+    if (p->n[a] < 3 || p->n[a] > (1 << 24)) return LBPWFA_ERR_INVALID;
+  if (!(p->dx > 0.0) || !std::isfinite(p->dx)) return LBPWFA_ERR_INVALID;
+  if (!(p->courant > 0.0) || p->courant > 1.0 / std::sqrt((double)p->dim) + 1e-12) return LBPWFA_ERR_INVALID;
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return LBPWFA_ERR_INVALID;
+  if (p->closure != LBPWFA_LEC && p->closure != LBPWFA_WARMC) return LBPWFA_ERR_INVALID;
+  if (p->dv != 1 && p->dv != 3) return LBPWFA_ERR_INVALID;
+  if (!(p->mu >= 0.0) || !std::isfinite(p->mu)) return LBPWFA_ERR_INVALID;
+  if (!std::isfinite(p->alpha) || !std::isfinite(p->z0)) return LBPWFA_ERR_INVALID;
+  if (p->profile) {
+    if (p->profile_len < 2 || !(p->profile_dz > 0.0)) return LBPWFA_ERR_INVALID;
+  } else if (!(p->sigma_z > 0.0)) {
+    return LBPWFA_ERR_INVALID;
+  }
+  if (p->dim >= 2 && !(p->sigma_r > 0.0)) return LBPWFA_ERR_INVALID;
+  if (p->precision < LBPWFA_FP64 || p->precision > LBPWFA_FP16S) return LBPWFA_ERR_INVALID;
+  if (p->boundary != LBPWFA_OPEN && p->boundary != LBPWFA_PERIODIC) return LBPWFA_ERR_INVALID;
+  if (p->kernel_variant != 0 && p->kernel_variant != 1) return LBPWFA_ERR_INVALID;
+  long long cells = 1;
+  for (int a = 0; a < p->dim; ++a) cells *= p->n[a];
+  if (cells > (1LL << 34)) return LBPWFA_ERR_INVALID;
+  return LBPWFA_OK;
+}
+
+AuxParams aux_params(const lbpwfa_s* h) {
+  AuxParams A{};
+  for (int a = 0; a < 3; ++a) A.n[a] = h->n[a];
+  A.nzp = h->nzp;
+  A.plane = h->plane;
+  A.ncell = h->ncell;
+  A.periodic = h->prm.boundary == LBPWFA_PERIODIC;
+  A.dx = h->prm.dx;
+  A.dt = h->dt;
+  A.mu = h->prm.mu;
+  A.D = h->prm.dv;
+  for (int k = 0; k < 11; ++k) {
+    A.Arest[k] = h->Arest[k];
+    A.scale[k] = h->scale[k];
+    A.inv_scale[k] = h->inv_scale[k];
+  }
+  A.alpha = h->prm.alpha;
+  A.inv2sz2 = h->prm.sigma_z > 0 ? 1.0 / (2.0 * h->prm.sigma_z * h->prm.sigma_z) : 0.0;
+  A.sigma_r = h->prm.sigma_r;
+  A.inv2sr2 = h->prm.sigma_r > 0 ? 1.0 / (2.0 * h->prm.sigma_r * h->prm.sigma_r) : 0.0;
+  A.z0 = h->prm.z0;
+  A.profile = h->profile_d;
+  A.plen = (int)h->profile_h.size();
+  A.pdz = h->prm.profile_dz;
+  A.xoff = 0.5 * (h->n[1] - 1);
+  A.yoff = 0.5 * (h->n[2] - 1);
+  A.t = h->step * h->dt;
+  return A;
+}
+
+template <typename real>
+void fill_consts(const lbpwfa_s* h, StepConst<real>& c) {
+  const double dx = h->prm.dx, dt = h->dt;
+  c.dx = (real)dx;
+  c.idx = (real)(1.0 / dx);
+  c.i2dx = (real)(0.5 / dx);
+  c.dt = (real)dt;
+  c.idt = (real)(1.0 / dt);
+  c.courant = (real)h->prm.courant;
+  c.inv_tau = (real)(1.0 / h->prm.tau);
+  c.mu = (real)h->prm.mu;
+  c.cH = (real)((1.0 + 0.5 * h->prm.dv) * h->prm.mu);
+  c.zeta0 = (real)(h->prm.z0 + h->step * dt);
+  c.alpha = (real)h->prm.alpha;
+  c.inv2sz2 = (real)(h->prm.sigma_z > 0 ? 1.0 / (2.0 * h->prm.sigma_z * h->prm.sigma_z) : 0.0);
+  c.inv2sr2 = (real)(h->prm.sigma_r > 0 ? 1.0 / (2.0 * h->prm.sigma_r * h->prm.sigma_r) : 0.0);
+  c.xoff = (real)(0.5 * (h->n[1] - 1));
+  c.yoff = (real)(0.5 * (h->n[2] - 1));
+  c.pdz_inv = (real)(h->prm.profile_dz > 0 ? 1.0 / h->prm.profile_dz : 0.0);
+  c.phalf = (real)(0.5 * ((double)h->profile_h.size() - 1.0));
+  for (int k = 0; k < 11; ++k) c.Arest[k] = (real)h->Arest[k];
+}
+
+StepParams step_params(const lbpwfa_s* h) {
+  StepParams P{};
+  const int in = h->cur, out = 1 - h->cur;
+  P.fin = h->f[in].p;
+  P.fout = h->f[out].p;
+  P.Ein = h->E[in].p;
+  P.Eout = h->E[out].p;
+  P.Bin = h->B[in].p;
+  P.Bout = h->B[out].p;
+  P.prev = h->prev.p;
+  P.have_prev = h->have_prev;
+  for (int a = 0; a < 3; ++a) P.n[a] = h->n[a];
+  P.nzp = h->nzp;
+  P.plane = h->plane;
+  P.axis_stride[0] = 1;
+  P.axis_stride[1] = h->nzp;
+  P.axis_stride[2] = h->nzp * h->n[1];
+  P.periodic = h->prm.boundary == LBPWFA_PERIODIC;
+  P.D = h->prm.dv;
+  P.profile = h->profile_d;
+  P.plen = (int)h->profile_h.size();
+  for (int k = 0; k < 11; ++k) {
+    P.scale[k] = h->scale[k];
+    P.inv_scale[k] = h->inv_scale[k];
+  }
+  P.err = h->err_d;
+  fill_consts<float>(h, P.cf);
+  fill_consts<double>(h, P.cd);
+  return P;
+}
+
+dim3 step_grid(const lbpwfa_s* h) {
+  return dim3((unsigned)((h->n[0] + h->ks.tz - 1) / h->ks.tz),
+              (unsigned)((h->n[1] + h->ks.tx - 1) / h->ks.tx),
+              (unsigned)((h->n[2] + h->ks.ty - 1) / h->ks.ty));
+}
+
+// Copy device results to a caller buffer (host or device).
+int deliver(lbpwfa_s* h, const void* src, void* dst, size_t bytes, int dst_is_device) {
+  CK(h, cudaMemcpyAsync(dst, src, bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        h->stream));
+  if (!dst_is_device) CK(h, cudaStreamSynchronize(h->stream));
+  return LBPWFA_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// Tensor map of one population buffer viewed as [K*Q planes][nx rows][nzp]:
+// the step's box is (z, x, planes) = ks.tma_box.
+bool make_pop_map(lbpwfa_s* h, void* base, CUtensorMap* map) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t es = (cuuint64_t)h->ks.tma_elem_bytes;
+  const CUtensorMapDataType dt = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                               : (es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+  cuuint64_t dims[3] = {(cuuint64_t)h->nzp, (cuuint64_t)h->n[1], (cuuint64_t)h->K * h->Q};
+  cuuint64_t strides[2] = {(cuuint64_t)h->nzp * es, (cuuint64_t)h->plane * es};
+  cuuint32_t box[3] = {(cuuint32_t)h->ks.tma_box[0], (cuuint32_t)h->ks.tma_box[1], (cuuint32_t)h->ks.tma_box[2]};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int check_err_word(lbpwfa_s* h) {
+  int v = 0;
+  CK(h, cudaMemcpyAsync(&v, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (v != 0) {
+    h->err = "a bounded device wait gave up";
+    return LBPWFA_ERR_TIMEOUT;
+  }
+  return LBPWFA_OK;
+}
+
+uint32_t crc32_update(uint32_t crc, const void* data, size_t len) {
+  static uint32_t table[256];
+  static bool init = false;
+  if (!init) {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t c = i;
+      for (int j = 0; j < 8; ++j) c = (c & 1) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+      table[i] = c;
+    }
+    init = true;
+  }
+  const unsigned char* p = (const unsigned char*)data;
+  crc = ~crc;
+  for (size_t i = 0; i < len; ++i) crc = table[(crc ^ p[i]) & 0xFF] ^ (crc >> 8);
+  return ~crc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbpwfa_status_string(int s) {
+  switch (s) {
+    case LBPWFA_OK: return "ok";
+    case LBPWFA_ERR_INVALID: return "invalid argument";
+    case LBPWFA_ERR_OOM: return "out of memory";
+    case LBPWFA_ERR_CUDA: return "CUDA error";
+    case LBPWFA_ERR_NONFINITE: return "non-finite populations";
+    case LBPWFA_ERR_TIMEOUT: return "device wait timed out";
+    case LBPWFA_ERR_STATE: return "invalid state";
+    case LBPWFA_ERR_IO: return "checkpoint I/O error";
+    default: return "unknown status";
+  }
+}
+
+const char* lbpwfa_last_error(lbpwfa_t h) { return h ? h->err.c_str() : ""; }
+
+void lbpwfa_destroy(lbpwfa_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int j = 0; j < 2; ++j) { release(h->f[j]); release(h->E[j]); release(h->B[j]); }
+  release(h->prev);
+  release(h->partial);
+  release(h->out3);
+  release(h->scratch);
+  if (h->err_d) cudaFree(h->err_d);
+  if (h->profile_d) cudaFree(h->profile_d);
+  if (h->owns_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
+  if (!out) return LBPWFA_ERR_INVALID;
+  *out = nullptr;
+  int st = validate(p);
+  if (st != LBPWFA_OK) return st;
+  lbpwfa_s* h = new lbpwfa_s();
+  h->prm = *p;
+  h->prm.profile = nullptr;
+  if (p->profile) h->profile_h.assign(p->profile, p->profile + p->profile_len);
+  const int dim = p->dim;
+  bool ok = false;
+  if (p->precision == LBPWFA_FP64) ok = kernels_f64(dim, p->closure, &h->ks);
+  else if (p->precision == LBPWFA_FP32) ok = kernels_f32(dim, p->closure, &h->ks);
+  else ok = kernels_f16s(dim, p->closure, &h->ks);
+  if (!ok) { delete h; return LBPWFA_ERR_INVALID; }
+
+  h->Q = dim == 1 ? 3 : (dim == 2 ? 9 : 19);
+  const int nth = p->closure == LBPWFA_WARMC ? (dim == 1 ? 1 : (dim == 2 ? 4 : 6)) : 0;
+  h->K = p->closure == LBPWFA_LEC ? 1 + dim : 2 + dim + nth;
+  h->NPREV = p->closure == LBPWFA_WARMC ? 1 + 2 * dim : 0;
+  for (int a = 0; a < 3; ++a) h->n[a] = a < dim ? p->n[a] : 1;
+  h->nzp = (h->n[0] + 31) / 32 * 32;
+  h->plane = (long long)h->nzp * h->n[1] * h->n[2];
+  h->ncell = (long long)h->n[0] * h->n[1] * h->n[2];
+  if ((long long)h->Q * h->plane >= (1LL << 31)) { delete h; return LBPWFA_ERR_INVALID; }  // 32-bit plane offsets
+  h->store_sz = p->precision == LBPWFA_FP64 ? 8 : (p->precision == LBPWFA_FP32 ? 4 : 2);
+  h->real_sz = p->precision == LBPWFA_FP64 ? 8 : 4;
+  h->dt = p->courant * p->dx;
+
+  // Rest advected values.  WARMC: Eq. (traces3) at rest (theta^{00} = 0,
+  // theta^{ij} = mu delta^{ij} over the D kinetic dimensions, n_0 = 1):
+  // h^2 + D mu h - 1 = 0, lambda = 1/h.
+  h->Arest[0] = 1.0;
+  if (p->closure == LBPWFA_WARMC) {
+    const double D = p->dv, mu = p->mu;
+    const double h0 = 2.0 / (D * mu + std::sqrt(D * D * mu * mu + 4.0));
+    const double lam0 = 1.0 / h0;
+    h->Arest[1] = lam0;
+    const int ta[6] = {0, 1, 2, 0, 0, 1}, tb[6] = {0, 1, 2, 1, 2, 2};
+    for (int j = 0; j < nth; ++j) {
+      const bool diag = ta[j] == tb[j];
+      const double th = (diag && (p->dv == 3 || ta[j] == 0)) ? mu : 0.0;
+      h->Arest[2 + dim + j] = lam0 * th;
+    }
+  }
+  for (int k = 0; k < 11; ++k) {
+    h->scale[k] = p->precision == LBPWFA_FP16S ? kF16Scale : 1.0f;
+    h->inv_scale[k] = 1.0f / h->scale[k];
+  }
+
+  if (p->stream) {
+    h->stream = (cudaStream_t)p->stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { int r = fail_cuda(h, e, "cudaStreamCreate"); lbpwfa_destroy(h); return r; }
+    h->owns_stream = true;
+  }
+  cudaError_t pe = h->ks.prepare();
+  if (pe != cudaSuccess) { fail_cuda(h, pe, "cudaFuncSetAttribute"); lbpwfa_destroy(h); return LBPWFA_ERR_CUDA; }
+
+  const size_t pop_bytes = (size_t)h->K * h->Q * h->plane * h->store_sz;
+  const size_t fld_bytes = 3 * (size_t)h->plane * h->real_sz;
+  int r = LBPWFA_OK;
+  for (int j = 0; j < 2 && r == LBPWFA_OK; ++j) {
+    r = alloc(h, h->f[j], pop_bytes);
+    if (r == LBPWFA_OK) r = alloc(h, h->E[j], fld_bytes);
+    if (r == LBPWFA_OK) r = alloc(h, h->B[j], fld_bytes);
+  }
+  if (r == LBPWFA_OK && h->NPREV) r = alloc(h, h->prev, (size_t)h->NPREV * h->plane * h->real_sz);
+  if (r == LBPWFA_OK) r = alloc(h, h->partial, (size_t)kReduceBlocks * 3 * sizeof(double));
+  if (r == LBPWFA_OK) r = alloc(h, h->out3, 4 * sizeof(double));
+  if (r != LBPWFA_OK) { lbpwfa_destroy(h); return r; }
+  {
+    cudaError_t e = cudaMalloc(&h->err_d, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err_d, 0, sizeof(int), h->stream);
+    if (e != cudaSuccess) { int rr = fail_cuda(h, e, "error word"); lbpwfa_destroy(h); return rr; }
+  }
+  h->use_tma = p->kernel_variant == 0 && h->ks.has_tma && dim == 2 && p->boundary == LBPWFA_OPEN;
+  if (h->use_tma) {
+    cudaError_t e = h->ks.prepare_tma();
+    bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0]) && make_pop_map(h, h->f[1].p, &h->maps[1]);
+    if (!ok) {
+      cudaGetLastError();
+      h->use_tma = false;  // the plain kernel computes the same step
+    }
+  }
+  if (!h->profile_h.empty()) {
+    cudaError_t e = cudaMalloc(&h->profile_d, h->profile_h.size() * sizeof(double));
+    if (e != cudaSuccess) { lbpwfa_destroy(h); return LBPWFA_ERR_OOM; }
+    e = cudaMemcpyAsync(h->profile_d, h->profile_h.data(), h->profile_h.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) { int rr = fail_cuda(h, e, "profile upload"); lbpwfa_destroy(h); return rr; }
+  }
+  // rest state: all deviations zero (every storage format encodes 0 as zero bits)
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+    e = cudaMemsetAsync(h->f[j].p, 0, pop_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->E[j].p, 0, fld_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->B[j].p, 0, fld_bytes, h->stream);
+  }
+  if (e == cudaSuccess && h->prev.p) e = cudaMemsetAsync(h->prev.p, 0, h->prev.bytes, h->stream);
+  if (e != cudaSuccess) { int rr = fail_cuda(h, e, "cudaMemsetAsync"); lbpwfa_destroy(h); return rr; }
+  if (p->init_fields && dim >= 2) {
+    AuxParams A = aux_params(h);
+    h->ks.init_fields(A, h->E[0].p, h->B[0].p, h->stream);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { int rr = fail_cuda(h, e, "init_fields"); lbpwfa_destroy(h); return rr; }
+  }
+  h->cur = 0;
+  h->step = 0;
+  h->have_prev = 0;
+  *out = h;
+  return LBPWFA_OK;
+}
+
+int lbpwfa_step(lbpwfa_t h, int64_t nsteps) {
+  if (!h || nsteps < 0) return LBPWFA_ERR_INVALID;
+  const dim3 grid = h->use_tma ? dim3((unsigned)((h->n[0] + h->ks.tma_tz - 1) / h->ks.tma_tz),
+                                      (unsigned)((h->n[1] + h->ks.tma_tx - 1) / h->ks.tma_tx), 1)
+                               : step_grid(h);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    StepParams P = step_params(h);
+    if (h->use_tma) h->ks.step_tma(P, &h->maps[h->cur], grid, h->stream);
+    else h->ks.step(P, grid, h->stream);
+    CK_LAUNCH(h, "lb_step_kernel launch");
+    h->cur = 1 - h->cur;
+    h->step += 1;
+    if (h->NPREV) h->have_prev = 1;
+  }
+  return LBPWFA_OK;
+}
+
+int lbpwfa_advected(lbpwfa_t h, double* dst, size_t count, int dst_is_device) {
+  if (!h || !dst) return LBPWFA_ERR_INVALID;
+  const size_t need = (size_t)h->K * h->ncell;
+  if (count < need) return LBPWFA_ERR_INVALID;
+  AuxParams A = aux_params(h);
+  double* out = dst;
+  if (!dst_is_device) {
+    int r = ensure_scratch(h, need * sizeof(double));
+    if (r != LBPWFA_OK) return r;
+    out = (double*)h->scratch.p;
+  }
+  h->ks.advected(A, h->f[h->cur].p, out, h->stream);
+  CK_LAUNCH(h, "advected_kernel launch");
+  if (!dst_is_device) return deliver(h, out, dst, need * sizeof(double), 0);
+  return LBPWFA_OK;
+}
+
+int lbpwfa_moments(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_is_device) {
+  if (!h || !dst) return LBPWFA_ERR_INVALID;
+  mask &= 0xFFFFu;
+  int nb = 0;
+  for (int b = 0; b < 16; ++b) nb += (mask >> b) & 1u;
+  const size_t need = (size_t)nb * h->ncell;
+  if (nb == 0) return LBPWFA_OK;
+  if (count < need) return LBPWFA_ERR_INVALID;
+  AuxParams A = aux_params(h);
+  double* out = dst;
+  if (!dst_is_device) {
+    int r = ensure_scratch(h, need * sizeof(double));
+    if (r != LBPWFA_OK) return r;
+    out = (double*)h->scratch.p;
+  }
+  h->ks.moments(A, h->f[h->cur].p, mask, out, h->stream);
+  CK_LAUNCH(h, "moments_kernel launch");
+  if (!dst_is_device) return deliver(h, out, dst, need * sizeof(double), 0);
+  return LBPWFA_OK;
+}
+
+int lbpwfa_fields(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_is_device) {
+  if (!h || !dst) return LBPWFA_ERR_INVALID;
+  mask &= 0x3Fu;
+  // bits: E_x, E_y, E_z, B_x, B_y, B_z -> internal component (z=0, x=1, y=2)
+  const int comp_of_bit[6] = {1, 2, 0, 1, 2, 0};
+  int comps[6], isb[6], nb = 0;
+  for (int b = 0; b < 6; ++b)
+    if (mask & (1u << b)) { comps[nb] = comp_of_bit[b]; isb[nb] = b >= 3; ++nb; }
+  if (nb == 0) return LBPWFA_OK;
+  const size_t need = (size_t)nb * h->ncell;
+  if (count < need) return LBPWFA_ERR_INVALID;
+  AuxParams A = aux_params(h);
+  double* out = dst;
+  if (!dst_is_device) {
+    int r = ensure_scratch(h, need * sizeof(double));
+    if (r != LBPWFA_OK) return r;
+    out = (double*)h->scratch.p;
+  }
+  for (int j0 = 0; j0 < nb; j0 += 4) {
+    const int m = nb - j0 < 4 ? nb - j0 : 4;
+    int c4[4] = {0, 0, 0, 0}, b4[4] = {0, 0, 0, 0};
+    for (int j = 0; j < m; ++j) { c4[j] = comps[j0 + j]; b4[j] = isb[j0 + j]; }
+    h->ks.export_fields(A, h->E[h->cur].p, h->B[h->cur].p, m, make_int4(c4[0], c4[1], c4[2], c4[3]),
+                        make_int4(b4[0], b4[1], b4[2], b4[3]), out + (size_t)j0 * h->ncell, h->stream);
+    CK_LAUNCH(h, "export_fields_kernel launch");
+  }
+  if (!dst_is_device) return deliver(h, out, dst, need * sizeof(double), 0);
+  return LBPWFA_OK;
+}
+
+int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double* B, int src_is_device) {
+  if (!h) return LBPWFA_ERR_INVALID;
+  AuxParams A = aux_params(h);
+  const size_t nf = (size_t)h->K * h->Q * h->ncell, nfl = 3 * (size_t)h->ncell;
+  size_t need = 0;
+  if (!src_is_device) need = (f ? nf : 0) + (E ? nfl : 0) + (B ? nfl : 0);
+  if (need) {
+    int r = ensure_scratch(h, need * sizeof(double));
+    if (r != LBPWFA_OK) return r;
+  }
+  double* sp = (double*)h->scratch.p;
+  const double *fd = f, *Ed = E, *Bd = B;
+  if (!src_is_device) {
+    size_t o = 0;
+    if (f) { CK(h, cudaMemcpyAsync(sp + o, f, nf * 8, cudaMemcpyHostToDevice, h->stream)); fd = sp + o; o += nf; }
+    if (E) { CK(h, cudaMemcpyAsync(sp + o, E, nfl * 8, cudaMemcpyHostToDevice, h->stream)); Ed = sp + o; o += nfl; }
+    if (B) { CK(h, cudaMemcpyAsync(sp + o, B, nfl * 8, cudaMemcpyHostToDevice, h->stream)); Bd = sp + o; o += nfl; }
+  }
+  if (fd) {
+    h->ks.import_pops(A, fd, h->f[h->cur].p, h->stream);
+    CK_LAUNCH(h, "import_pops_kernel launch");
+  }
+  if (Ed || Bd) {
+    h->ks.import_fields(A, Ed, Bd, h->E[h->cur].p, h->B[h->cur].p, h->stream);
+    CK_LAUNCH(h, "import_fields_kernel launch");
+  }
+  h->have_prev = 0;
+  if (!src_is_device) CK(h, cudaStreamSynchronize(h->stream));
+  return LBPWFA_OK;
+}
+
+int lbpwfa_get_state(lbpwfa_t h, double* f, double* E, double* B, int dst_is_device) {
+  if (!h) return LBPWFA_ERR_INVALID;
+  AuxParams A = aux_params(h);
+  const size_t nf = (size_t)h->K * h->Q * h->ncell, nfl = 3 * (size_t)h->ncell;
+  if (f) {
+    double* out = f;
+    if (!dst_is_device) {
+      int r = ensure_scratch(h, nf * 8);
+      if (r != LBPWFA_OK) return r;
+      out = (double*)h->scratch.p;
+    }
+    h->ks.export_pops(A, h->f[h->cur].p, out, h->stream);
+    CK_LAUNCH(h, "export_pops_kernel launch");
+    if (!dst_is_device) {
+      int r = deliver(h, out, f, nf * 8, 0);
+      if (r != LBPWFA_OK) return r;
+    }
+  }
+  // E and B in the ABI's component order z, x, y
+  for (int which = 0; which < 2; ++which) {
+    double* dst = which == 0 ? E : B;
+    if (!dst) continue;
+    double* out = dst;
+    if (!dst_is_device) {
+      int r = ensure_scratch(h, nfl * 8);
+      if (r != LBPWFA_OK) return r;
+      out = (double*)h->scratch.p;
+    }
+    h->ks.export_fields(A, h->E[h->cur].p, h->B[h->cur].p, 3, make_int4(0, 1, 2, 0),
+                        make_int4(which, which, which, 0), out, h->stream);
+    CK_LAUNCH(h, "export_fields_kernel launch");
+    if (!dst_is_device) {
+      int r = deliver(h, out, dst, nfl * 8, 0);
+      if (r != LBPWFA_OK) return r;
+    }
+  }
+  return LBPWFA_OK;
+}
+
+int lbpwfa_reduce(lbpwfa_t h, double out[3]) {
+  if (!h || !out) return LBPWFA_ERR_INVALID;
+  AuxParams A = aux_params(h);
+  h->ks.reduce_partial(A, h->f[h->cur].p, (double*)h->partial.p, kReduceBlocks, h->stream);
+  CK_LAUNCH(h, "reduce_partial_kernel launch");
+  reduce_final_kernel<<<1, 32, 0, h->stream>>>((const double*)h->partial.p, kReduceBlocks, (double*)h->out3.p);
+  CK_LAUNCH(h, "reduce_final_kernel launch");
+  CK(h, cudaMemcpyAsync(out, h->out3.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  int st = check_err_word(h);
+  if (st != LBPWFA_OK) return st;
+  return out[2] > 0 ? LBPWFA_ERR_NONFINITE : LBPWFA_OK;
+}
+
+int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info) {
+  if (!h || !info) return LBPWFA_ERR_INVALID;
+  info->K = h->K;
+  info->Q = h->Q;
+  info->ncell = h->ncell;
+  info->step = h->step;
+  info->dt = h->dt;
+  info->time = h->step * h->dt;
+  info->device_bytes = h->device_bytes;
+  const int dim = h->prm.dim;
+  const int ne = dim == 1 ? 1 : (dim == 2 ? 2 : 3);
+  const int nbf = dim == 1 ? 0 : (dim == 2 ? 1 : 3);
+  info->bytes_per_update = 2.0 * h->K * h->Q * h->store_sz + 2.0 * (ne + nbf + h->NPREV) * h->real_sz;
+  info->kernel_variant = h->use_tma ? 0 : 1;
+  return LBPWFA_OK;
+}
+
+int lbpwfa_set_stream(lbpwfa_t h, void* stream) {
+  if (!h) return LBPWFA_ERR_INVALID;
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (stream) {
+    if (h->owns_stream) { cudaStreamDestroy(h->stream); h->owns_stream = false; }
+    h->stream = (cudaStream_t)stream;
+  } else if (!h->owns_stream) {
+    CK(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->owns_stream = true;
+  }
+  return LBPWFA_OK;
+}
+
+int lbpwfa_synchronize(lbpwfa_t h) {
+  if (!h) return LBPWFA_ERR_INVALID;
+  CK(h, cudaStreamSynchronize(h->stream));
+  return check_err_word(h);
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints.
+// ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version;
+  int32_t dim, n0, n1, n2, closure, dv, precision, boundary, K, Q, have_prev;
+  int64_t step;
+  double dx, courant, tau, mu, alpha, sigma_z, sigma_r, z0;
+  uint64_t pop_bytes, fld_bytes, prev_bytes;
+};
+}  // namespace
+
+int lbpwfa_save(lbpwfa_t h, const char* path) {
+  if (!h || !path) return LBPWFA_ERR_INVALID;
+  CkptHeader H{};
+  std::memcpy(H.magic, "LBPWFA01", 8);
+  H.version = 1;
+  H.dim = h->prm.dim; H.n0 = h->n[0]; H.n1 = h->n[1]; H.n2 = h->n[2];
+  H.closure = h->prm.closure; H.dv = h->prm.dv; H.precision = h->prm.precision; H.boundary = h->prm.boundary;
+  H.K = h->K; H.Q = h->Q; H.have_prev = h->have_prev; H.step = h->step;
+  H.dx = h->prm.dx; H.courant = h->prm.courant; H.tau = h->prm.tau; H.mu = h->prm.mu;
+  H.alpha = h->prm.alpha; H.sigma_z = h->prm.sigma_z; H.sigma_r = h->prm.sigma_r; H.z0 = h->prm.z0;
+  H.pop_bytes = h->f[h->cur].bytes; H.fld_bytes = h->E[h->cur].bytes; H.prev_bytes = h->prev.bytes;
+  std::vector<char> buf(H.pop_bytes + 2 * H.fld_bytes + H.prev_bytes);
+  char* q = buf.data();
+  CK(h, cudaMemcpyAsync(q, h->f[h->cur].p, H.pop_bytes, cudaMemcpyDeviceToHost, h->stream));
+  q += H.pop_bytes;
+  CK(h, cudaMemcpyAsync(q, h->E[h->cur].p, H.fld_bytes, cudaMemcpyDeviceToHost, h->stream));
+  q += H.fld_bytes;
+  CK(h, cudaMemcpyAsync(q, h->B[h->cur].p, H.fld_bytes, cudaMemcpyDeviceToHost, h->stream));
+  q += H.fld_bytes;
+  if (H.prev_bytes) CK(h, cudaMemcpyAsync(q, h->prev.p, H.prev_bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  uint32_t crc = crc32_update(0, &H, sizeof(H));
+  crc = crc32_update(crc, buf.data(), buf.size());
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return LBPWFA_ERR_IO;
+  bool ok = std::fwrite(&H, sizeof(H), 1, fp) == 1 && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size() &&
+            std::fwrite(&crc, sizeof(crc), 1, fp) == 1;
+  ok = (std::fclose(fp) == 0) && ok;
+  return ok ? LBPWFA_OK : LBPWFA_ERR_IO;
+}
+
+int lbpwfa_load(lbpwfa_t h, const char* path) {
+  if (!h || !path) return LBPWFA_ERR_INVALID;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return LBPWFA_ERR_IO;
+  CkptHeader H{};
+  if (std::fread(&H, sizeof(H), 1, fp) != 1 || std::memcmp(H.magic, "LBPWFA01", 8) != 0) {
+    std::fclose(fp);
+    return LBPWFA_ERR_IO;
+  }
+  const bool match = H.dim == h->prm.dim && H.n0 == h->n[0] && H.n1 == h->n[1] && H.n2 == h->n[2] &&
+                     H.closure == h->prm.closure && H.dv == h->prm.dv && H.precision == h->prm.precision &&
+                     H.boundary == h->prm.boundary && H.K == h->K && H.Q == h->Q &&
+                     H.pop_bytes == h->f[0].bytes && H.fld_bytes == h->E[0].bytes && H.prev_bytes == h->prev.bytes &&
+                     H.dx == h->prm.dx && H.courant == h->prm.courant && H.tau == h->prm.tau && H.mu == h->prm.mu;
+  if (!match) { std::fclose(fp); return LBPWFA_ERR_IO; }
+  std::vector<char> buf(H.pop_bytes + 2 * H.fld_bytes + H.prev_bytes);
+  uint32_t crc_file = 0;
+  bool ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size() && std::fread(&crc_file, sizeof(crc_file), 1, fp) == 1;
+  std::fclose(fp);
+  if (!ok) return LBPWFA_ERR_IO;
+  uint32_t crc = crc32_update(0, &H, sizeof(H));
+  crc = crc32_update(crc, buf.data(), buf.size());
+  if (crc != crc_file) return LBPWFA_ERR_IO;
+  const char* q = buf.data();
+  CK(h, cudaMemcpyAsync(h->f[h->cur].p, q, H.pop_bytes, cudaMemcpyHostToDevice, h->stream));
+  q += H.pop_bytes;
+  CK(h, cudaMemcpyAsync(h->E[h->cur].p, q, H.fld_bytes, cudaMemcpyHostToDevice, h->stream));
+  q += H.fld_bytes;
+  CK(h, cudaMemcpyAsync(h->B[h->cur].p, q, H.fld_bytes, cudaMemcpyHostToDevice, h->stream));
+  q += H.fld_bytes;
+  if (H.prev_bytes) CK(h, cudaMemcpyAsync(h->prev.p, q, H.prev_bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->step = H.step;
+  h->have_prev = H.have_prev;
+  return LBPWFA_OK;
+}
+
+}  // extern "C"

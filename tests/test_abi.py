@@ -1,0 +1,73 @@
+"""The C ABI: the library loads (no GPU needed to load it), exports every
+function that include/lbpwfa.h declares, and the binding refuses to run
+without it.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbpwfa_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2309_04872_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_core_calls():
+    d = _declared()
+    for name in ("lbpwfa_create", "lbpwfa_step", "lbpwfa_moments", "lbpwfa_fields",
+                 "lbpwfa_destroy", "lbpwfa_status_string"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2309_04872_gb300 import lbpwfa
+    assert set(lbpwfa.EXPORTED) == _declared()
+
+
+def test_status_strings(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    lib.lbpwfa_status_string.restype = ctypes.c_char_p
+    assert lib.lbpwfa_status_string(0) == b"ok"
+    assert lib.lbpwfa_status_string(-1) == b"invalid argument"
+    assert lib.lbpwfa_status_string(12345) == b"unknown status"
+
+
+def test_invalid_parameters_rejected_before_any_device_work(lib_path):
+    """Validation runs on the host before the first CUDA call, so it can be
+    exercised without a GPU."""
+    from paper_2309_04872_gb300 import lbpwfa
+    lib = lbpwfa.load_library()
+    base = dict(dim=2, n=(16, 8), dx=0.05, courant=0.1, tau=0.53, closure="lec", dv=3, mu=1e-2,
+                alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=1.0)
+    bad = [dict(tau=0.5), dict(courant=0.8), dict(n=(2, 8)), dict(dim=4, n=(8, 8, 8)), dict(dv=2),
+           dict(mu=-1e-3), dict(sigma_z=0.0), dict(sigma_r=-1.0), dict(dx=0.0), dict(closure=5)]
+    for b in bad:
+        p, keep = lbpwfa.make_params({**base, **b})
+        h = ctypes.c_void_p()
+        assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1, b
+        assert not h.value
+    p, keep = lbpwfa.make_params(base, precision=7)
+    h = ctypes.c_void_p()
+    assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1
+    assert lib.lbpwfa_create(None, ctypes.byref(h)) == -1
+    assert lib.lbpwfa_step(None, 1) == -1

@@ -1,0 +1,325 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Same seeded inputs on both sides; element-by-element comparison of the
+advected scalars A_k, the decoded moments and the raw field slots.  FP64
+storage must match to 1e-12 relative (and the perturbation from the rest
+state to 1e-9, see _check); FP32 and FP16-shifted storage to the bounds
+written in each test (the unit round-off of the stored deviations, 2^-24 and
+2^-11, times the amplification named there)."""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+lb = pytest.importorskip("paper_2309_04872_gb300.lbpwfa")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lb.load_library()
+
+
+SHAPES = {1: (301,), 2: (77, 45), 3: (37, 21, 13)}
+
+
+def _cfg(dim, closure, boundary, **kw):
+    n = SHAPES[dim]
+    cfg = dict(dim=dim, n=n, dx=0.05, courant=0.5 if dim == 1 else (0.1 if dim == 2 else 0.08),
+               tau=0.53, closure=closure, dv=3, mu=1e-2, alpha=0.2, sigma_z=0.6, sigma_r=0.3,
+               z0=0.3 * n[0] * 0.05, boundary=boundary, init_fields=dim > 1)
+    cfg.update(kw)
+    return cfg
+
+
+def _random_state(o, seed, mu):
+    base = o.rest_advected()
+    amp = np.abs(base) * 0.05
+    K = o.K
+    dim = o.cfg["dim"]
+    if o.cfg["closure"] == "lec":
+        amp[1:] = 0.02
+    else:
+        amp[2:2 + dim] = 0.02
+        for j in range(K - 2 - dim):
+            if base[2 + dim + j] == 0.0:
+                amp[2 + dim + j] = 0.05 * mu
+    f = inputs.random_populations(seed, K, o.Q, o.ncell, base, amp)
+    E, B = inputs.random_fields(seed + 1, o.ncell, 0.01)
+    return f, E, B
+
+
+def _check(got, ref, rest, tol, ptol, floor, what):
+    """Relative error of the quantity itself (the spec definition), and
+    a second bound on its perturbation from the rest value with an absolute
+    floor: the oracle keeps plain populations, whose sum drifts by the
+    round-off of sum_i w_i != 1 (a few 1e-16 per step), while the CUDA path
+    keeps deviations from the rest state."""
+    d = np.linalg.norm(got - ref)
+    nrm = np.linalg.norm(ref)
+    sq = np.sqrt(ref.size)
+    assert d <= tol * nrm + floor * sq, f"{what}: |d| {d:.3e} vs {tol:.0e} * {nrm:.3e}"
+    if rest != 0.0:
+        pert = np.linalg.norm(ref - rest)
+        assert d <= ptol * pert + floor * abs(rest) * sq, \
+            f"{what}: |d| {d:.3e} vs {ptol:.0e} * |ref - rest| {pert:.3e}"
+    return d / nrm if nrm > 0 else d
+
+
+def _compare(run, orc, tol, ptol=None, floor=1e-13, label=""):
+    """Advected scalars A_k = sum_i f_ki and the raw field slots."""
+    ptol = 1e3 * tol if ptol is None else ptol
+    A_g = run.advected()
+    A_o = orc.advected()
+    rest = orc.rest_advected()
+    errs = {}
+    for k in range(orc.K):
+        errs[f"A{k}"] = _check(A_g[k], A_o[k], rest[k], tol, ptol, floor, f"{label} A{k}")
+    _, E_g, B_g = run.get_state()
+    _, E_o, B_o = orc.get_state()
+    # field floor on the scale of all field components: a component that is
+    # itself a near-cancellation residue (E_z of the v -> c driver field,
+    # where curl B and the driver current almost cancel) is not held to its
+    # own norm
+    fscale = max(np.abs(E_o).max(), np.abs(B_o).max())
+    for a in range(3):
+        for nm, g, o in (("E", E_g[a], E_o[a]), ("B", B_g[a], B_o[a])):
+            if np.abs(o).max() == 0.0:
+                # zero by symmetry in the oracle; contracted FMAs on the GPU
+                # leave a round-off residue of (a - b) * c with a == b
+                assert np.abs(g).max() <= floor * fscale, f"{label} {nm}{a} should be zero"
+                continue
+            errs[f"{nm}{a}"] = _check(g, o, 0.0, tol, ptol, floor * fscale, f"{label} {nm}{a}")
+    return errs
+
+
+def _fp64_tol(nsteps):
+    """1e-12 relative, growing linearly past 1000 steps: the two FP64
+    evaluation orders (deviation form and contracted FMAs on the GPU, plain
+    populations in the oracle) differ by round-off that a neutrally stable
+    plasma oscillation accumulates linearly in time."""
+    return 1e-12 * max(1.0, nsteps / 1000.0)
+
+
+# ---------------------------------------------------------------------------
+# FP64: random states, every dimension, closure and boundary, ragged sizes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+@pytest.mark.parametrize("boundary", ["open", "periodic"])
+def test_fp64_random_state_parity(dim, closure, boundary):
+    cfg = _cfg(dim, closure, boundary)
+    orc = O.Oracle(cfg)
+    f, E, B = _random_state(orc, 100 + 7 * dim, cfg["mu"])
+    orc.set_state(f, E, B)
+    with lb.Run(cfg, "fp64") as run:
+        run.set_state(f, E, B)
+        _compare(run, orc, 1e-12, label="t0")
+        nsteps = 12 if dim == 3 else 25
+        orc.step(nsteps)
+        run.step(nsteps)
+        _compare(run, orc, 1e-12, label=f"t{nsteps}")
+        # decoded moments (FP64 decode of the stored state); n and gamma are
+        # also bounded through their perturbations from 1
+        mask = 0xFFFF
+        m_g = run.moments(mask)
+        m_o = orc.moments(mask)
+        for b in range(16):
+            if np.abs(m_o[b]).max() == 0:
+                assert np.abs(m_g[b]).max() == 0
+                continue
+            rest = 1.0 if b in (0, 4) else 0.0
+            _check(m_g[b], m_o[b], rest, 1e-12, 1e-8, 1e-13, f"moment bit {b}")
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+def test_fp64_driver_from_rest_parity(dim, closure):
+    cfg = _cfg(dim, closure, "open", dv=1 if dim == 1 else 3)
+    orc = O.Oracle(cfg)
+    with lb.Run(cfg, "fp64") as run:
+        nsteps = 40 if dim == 3 else 120
+        orc.step(nsteps)
+        run.step(nsteps)
+        _compare(run, orc, 1e-12, label="driver")
+
+
+def test_fp64_config1_full_run_matches_oracle():
+    """1D, 2048 cells over 40 k_p^-1, C = 0.5, LEC D = 1, mu = 1e-3,
+    alpha = 0.01, sigma_z = 1, z0 = -5, 4000 steps."""
+    cfg = dict(dim=1, n=(2048,), dx=40 / 2048, courant=0.5, tau=0.52, closure="lec", dv=1, mu=1e-3,
+               alpha=0.01, sigma_z=1.0, z0=-5.0, boundary="open")
+    orc = O.Oracle(cfg)
+    orc.step(4000)
+    with lb.Run(cfg, "fp64") as run:
+        run.step(4000)
+        _compare(run, orc, _fp64_tol(4000), label="config1")
+
+
+def test_fp64_2d_full_size_matches_oracle():
+    """2D 1024 x 512 (dx = 0.05), LEC D = 3, mu = 1e-2, alpha = 0.1, sigma_z = 1,
+    sigma_r = 0.5, z0 = 4, C = 0.1, tau = 0.53: the bench's grid and launch
+    configuration, compared in full after 30 steps."""
+    cfg = dict(dim=2, n=(1024, 512), dx=0.05, courant=0.1, tau=0.53, closure="lec", dv=3, mu=1e-2,
+               alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=4.0, boundary="open", init_fields=True)
+    orc = O.Oracle(cfg)
+    orc.step(30)
+    with lb.Run(cfg, "fp64") as run:
+        run.step(30)
+        _compare(run, orc, 1e-12, label="2d full")
+
+
+def test_fp64_3d_reduced_grid_matches_oracle():
+    """3D WARMC on a reduced grid (64 x 32 x 32) with the 3D driver
+    (alpha = 1, sigma_z = 0.7, sigma_r = 0.3, mu = 1e-2)."""
+    cfg = dict(dim=3, n=(64, 32, 32), dx=0.05, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=1e-2,
+               alpha=1.0, sigma_z=0.7, sigma_r=0.3, z0=1.4, boundary="open", init_fields=True)
+    orc = O.Oracle(cfg)
+    orc.step(20)
+    with lb.Run(cfg, "fp64") as run:
+        run.step(20)
+        _compare(run, orc, 1e-12, label="3d")
+
+
+# ---------------------------------------------------------------------------
+# Reduced-precision storage against the FP64 oracle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+@pytest.mark.parametrize("prec,tol,floor", [("fp32", 1e-4, 1e-7), ("fp16s", 2e-2, 1e-4)])
+def test_reduced_precision_driver_parity(dim, closure, prec, tol, floor):
+    """Bounds: the unit round-off of the stored deviations (2^-24, 2^-11)
+    times the amplification of the field source, where curl B and the driver
+    current nearly cancel in the v -> c field (about 1e3 early in the run)."""
+    cfg = _cfg(dim, closure, "open")
+    orc = O.Oracle(cfg)
+    nsteps = 30 if dim == 3 else 100
+    orc.step(nsteps)
+    with lb.Run(cfg, prec) as run:
+        run.step(nsteps)
+        _compare(run, orc, tol, ptol=tol, floor=floor, label=prec)
+
+
+# ---------------------------------------------------------------------------
+# Invariants that hold at any size
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp32", "fp16s"])
+@pytest.mark.parametrize("dim,closure", [(1, "lec"), (2, "warmc"), (3, "lec")])
+def test_rest_state_is_exact_in_shifted_storage(prec, dim, closure):
+    cfg = _cfg(dim, closure, "periodic", alpha=0.0, init_fields=False)
+    with lb.Run(cfg, prec) as run:
+        run.step(7)
+        A = run.advected()
+    orc = O.Oracle(cfg)
+    rest = orc.rest_advected()
+    for k in range(orc.K):
+        assert np.all(A[k] == np.float64(np.float32(rest[k])) ) or np.all(A[k] == rest[k])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mass_conservation_periodic(prec):
+    cfg = _cfg(2, "warmc", "periodic")
+    orc = O.Oracle(cfg)
+    f, E, B = _random_state(orc, 5, cfg["mu"])
+    with lb.Run(cfg, prec) as run:
+        run.set_state(f, E, B)
+        m0 = run.reduce()[0]
+        run.step(50)
+        m1, _, bad = run.reduce()
+        assert bad == 0
+        tol = 1e-12 if prec == "fp64" else 1e-6
+        assert abs(m1 - m0) <= tol * abs(m0)
+
+
+def test_reduce_matches_oracle():
+    cfg = _cfg(2, "lec", "open")
+    orc = O.Oracle(cfg)
+    orc.step(10)
+    with lb.Run(cfg, "fp64") as run:
+        run.step(10)
+        r = run.reduce()
+    ro = orc.reduce()
+    assert abs(r[0] - ro[0]) <= 1e-12 * abs(ro[0])
+    assert abs(r[1] - ro[1]) <= 1e-12 * abs(ro[1])
+    assert r[2] == 0
+
+
+def test_state_roundtrip_and_checkpoint_resume():
+    cfg = _cfg(3, "warmc", "open")
+    orc = O.Oracle(cfg)
+    f, E, B = _random_state(orc, 9, cfg["mu"])
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        with lb.Run(cfg, "fp32") as a:
+            a.set_state(f, E, B)
+            a.step(5)
+            a.save(path)
+            a.step(6)
+            A1 = a.advected()
+            F1 = a.fields()
+        with lb.Run(cfg, "fp32") as b:
+            b.load(path)
+            assert b.info().step == 5
+            b.step(6)
+            assert np.array_equal(b.advected(), A1)
+            assert np.array_equal(b.fields(), F1)
+        # a corrupted checkpoint is refused
+        raw = bytearray(open(path, "rb").read())
+        raw[len(raw) // 2] ^= 0xFF
+        open(path, "wb").write(bytes(raw))
+        with lb.Run(cfg, "fp32") as c:
+            with pytest.raises(lb.LbpwfaError) as ei:
+                c.load(path)
+            assert ei.value.status == -7
+
+
+def test_zero_steps_and_edge_sizes():
+    for dim in (1, 2, 3):
+        cfg = _cfg(dim, "lec", "open", n=(3, 3, 3)[:dim])
+        orc = O.Oracle(cfg)
+        with lb.Run(cfg, "fp64") as run:
+            run.step(0)
+            assert run.info().step == 0
+            orc.step(9)
+            run.step(9)
+            _compare(run, orc, 1e-12, label="tiny")
+
+
+# ---------------------------------------------------------------------------
+# The TMA-staged 2D kernel and the plain kernel compute the same step
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+def test_tma_and_plain_kernels_agree_bitwise(closure, prec):
+    cfg = _cfg(2, closure, "open", n=(131, 37))
+    orc = O.Oracle(cfg)
+    f, E, B = _random_state(orc, 77, cfg["mu"])
+    out = []
+    for variant in (0, 1):
+        with lb.Run(cfg, prec, variant=variant) as run:
+            expect_tma = variant == 0 and not (closure == "warmc" and prec == "fp64")
+            assert run.info().kernel_variant == (0 if expect_tma else 1)
+            run.set_state(f, E, B)
+            run.step(17)
+            out.append((run.advected(), run.fields()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("prec,tol,floor", [("fp64", 1e-12, 1e-13), ("fp32", 1e-4, 1e-7)])
+def test_plain_kernel_2d_parity(prec, tol, floor):
+    cfg = _cfg(2, "lec", "open")
+    orc = O.Oracle(cfg)
+    orc.step(60)
+    with lb.Run(cfg, prec, variant=1) as run:
+        assert run.info().kernel_variant == 1
+        run.step(60)
+        _compare(run, orc, tol, ptol=1e3 * tol if prec == "fp64" else tol, floor=floor, label="plain")
