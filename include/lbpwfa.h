@@ -170,6 +170,29 @@ int lbpwfa_reduce(lbpwfa_t h, double out[3]);
 
 int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info);
 
+/* The sums of lbpwfa_reduce for callers that cannot allocate device memory:
+ * code whose device memory belongs to another allocator (a framework's
+ * caching allocator, an embedding that reserves the whole device) or whose
+ * loop cannot take the implicit synchronisation of cudaMalloc / cudaFree.
+ * It allocates nothing.  The paper has no counterpart; this is plumbing
+ * around its FP64 diagnostics.
+ *  - Scratch: the per-block partial sums live in one fixed device array of
+ *    4096 x 3 + 4 doubles inside the library (about 96 KB, held on every GPU
+ *    that loads the library until the process exits).  It serves runs of at
+ *    most 2^25 = 33,554,432 nodes; larger runs return LBPWFA_ERR_INVALID
+ *    with the limit in lbpwfa_last_error.
+ *  - The first call on a device resolves the array's device address; make
+ *    that first call before any stream capture on that device.
+ *  - All calls on a device share the array and it keeps the last call's
+ *    contents; each call overwrites every partial it reads, but calls whose
+ *    work overlaps on the GPU race on it.
+ *  - out: 3 doubles (sum n, sum n_b, non-finite populations) on the device
+ *    when out_is_device (asynchronous), else on the host (synchronises; then
+ *    returns NONFINITE when out[2] > 0).  Call with the handle's device
+ *    current.  The summation order differs from lbpwfa_reduce (more, smaller
+ *    blocks), so the two agree to FP64 round-off, not bitwise. */
+int lbpwfa_reduce_noalloc(lbpwfa_t h, double* out, int out_is_device);
+
 /* Checkpoint: binary file with a header (parameters, step, precision), the
  * stored populations, fields and WARMC previous-step values, and a CRC32.
  * Resume is bitwise.  lbpwfa_load requires a handle created with the same

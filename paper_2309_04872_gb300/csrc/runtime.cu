@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -729,3 +730,76 @@ int lbpwfa_load(lbpwfa_t h, const char* path) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free FP64 reduction.
+//
+// Callers whose device memory is owned by another allocator (a framework's
+// caching allocator, an embedding that reserves the whole device), or whose
+// loop cannot afford the implicit device synchronisation that cudaMalloc /
+// cudaFree may bring, get the diagnostic sums of lbpwfa_reduce without the
+// library touching the allocator: the per-block partial sums live in the
+// fixed array below instead of a buffer allocated by the handle.
+//
+// The array is sized for kNoallocMaxBlocks partials of kNoallocNodesPerBlock
+// nodes each, so it serves runs of at most 2^25 nodes (the 256 x 256 x 512
+// 3D grid); larger runs are rejected.  Every GPU that loads the library holds
+// the array until the process exits.  All calls on a device share it and it
+// keeps the last call's contents: each call overwrites every partial it later
+// reads, so nothing has to start at zero, but calls whose work overlaps on
+// the GPU (two streams, or two handles at once) race on it.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kNoallocMaxBlocks = 4096;
+constexpr long long kNoallocNodesPerBlock = 8192;
+constexpr long long kNoallocMaxNodes = (long long)kNoallocMaxBlocks * kNoallocNodesPerBlock;
+constexpr int kNoallocDoubles = kNoallocMaxBlocks * 3 + 4;
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+namespace {
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[256] = {nullptr};
+
+// Device address of the array for the current device; resolved by the first
+// call on each device (host code may not use the symbol itself as an address).
+int noalloc_scratch(lbpwfa_s* h, double** out) {
+  int dev = -1;
+  CK(h, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return LBPWFA_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return fail_cuda(h, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return LBPWFA_OK;
+}
+}  // namespace
+
+extern "C" int lbpwfa_reduce_noalloc(lbpwfa_t h, double* out, int out_is_device) {
+  if (!h || !out) return LBPWFA_ERR_INVALID;
+  if (h->ncell > kNoallocMaxNodes) {
+    h->err = "lbpwfa_reduce_noalloc: " + std::to_string(h->ncell) + " nodes exceed the static scratch limit of " +
+             std::to_string(kNoallocMaxNodes) + " nodes";
+    return LBPWFA_ERR_INVALID;
+  }
+  double* scratch = nullptr;
+  int st = noalloc_scratch(h, &scratch);
+  if (st != LBPWFA_OK) return st;
+  const int nblk = (int)((h->ncell + kNoallocNodesPerBlock - 1) / kNoallocNodesPerBlock);
+  double* result = scratch + (size_t)kNoallocMaxBlocks * 3;
+  AuxParams A = aux_params(h);
+  h->ks.reduce_partial(A, h->f[h->cur].p, scratch, nblk, h->stream);
+  CK_LAUNCH(h, "reduce_partial_kernel launch (static scratch)");
+  reduce_final_kernel<<<1, 32, 0, h->stream>>>(scratch, nblk, result);
+  CK_LAUNCH(h, "reduce_final_kernel launch (static scratch)");
+  CK(h, cudaMemcpyAsync(out, result, 3 * sizeof(double),
+                        out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  if (out_is_device) return LBPWFA_OK;
+  CK(h, cudaStreamSynchronize(h->stream));
+  return out[2] > 0 ? LBPWFA_ERR_NONFINITE : LBPWFA_OK;
+}

@@ -60,7 +60,7 @@ _DP = ctypes.POINTER(ctypes.c_double)
 EXPORTED = ["lbpwfa_create", "lbpwfa_step", "lbpwfa_moments", "lbpwfa_fields", "lbpwfa_advected",
             "lbpwfa_set_state", "lbpwfa_get_state", "lbpwfa_reduce", "lbpwfa_info", "lbpwfa_save",
             "lbpwfa_load", "lbpwfa_set_stream", "lbpwfa_synchronize", "lbpwfa_destroy",
-            "lbpwfa_status_string", "lbpwfa_last_error"]
+            "lbpwfa_status_string", "lbpwfa_last_error", "lbpwfa_reduce_noalloc"]
 
 
 def library_path() -> str:
@@ -87,6 +87,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbpwfa_set_state.argtypes = [vp, vp, vp, vp, ctypes.c_int]
     L.lbpwfa_get_state.argtypes = [vp, vp, vp, vp, ctypes.c_int]
     L.lbpwfa_reduce.argtypes = [vp, _DP]
+    L.lbpwfa_reduce_noalloc.argtypes = [vp, vp, ctypes.c_int]
     L.lbpwfa_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.lbpwfa_save.argtypes = [vp, ctypes.c_char_p]
     L.lbpwfa_load.argtypes = [vp, ctypes.c_char_p]
