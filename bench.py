@@ -11,8 +11,9 @@ fraction of the measured HBM copy bandwidth that the step kernel's
 algorithmic bytes reach.
 
 Timing: W untimed steps, then K steps, each bracketed by CUDA events on the
-stream the kernel is launched on; L2 is flushed (256 MiB write) between timed
-steps, outside the events.  Under torchrun every rank runs its own replica of
+stream the kernel is launched on; L2 is flushed between timed steps (a 256 MiB
+write, then a 256 MiB read, so no dirty lines drain inside the timed step),
+outside the events.  Under torchrun every rank runs its own replica of
 the workload; value = all ranks' node updates / the slowest rank's time.
 
 --impl reference times the FP64 CPU oracle on the host cores on the same
@@ -39,6 +40,13 @@ WORKLOAD_2D = dict(dim=2, n=(1024, 512), dx=0.05, courant=0.1, tau=0.53, closure
                    alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=4.0, boundary="open", init_fields=True)
 WORKLOAD_NAME = "2d_lec_1024x512_fp32"
 
+# the 1D configuration (launch-bound, 0.2 MB of state: reported as steps/s)
+CONFIG_1D = dict(dim=1, n=(2048,), dx=40 / 2048, courant=0.5, tau=0.52, closure="lec", dv=1, mu=1e-3,
+                 alpha=0.01, sigma_z=1.0, z0=-5.0, boundary="open")
+# the 3D configuration: 512 (z) x 256 x 256, warm-plasma closure
+CONFIG_3D = dict(dim=3, n=(512, 256, 256), dx=0.05, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=1e-2,
+                 alpha=1.0, sigma_z=0.7, sigma_r=0.3, z0=2.8, boundary="open", init_fields=True)
+
 
 def _args():
     ap = argparse.ArgumentParser()
@@ -47,20 +55,27 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
-    ap.add_argument("--variant", type=int, default=0, choices=[0, 1],
-                    help="0: TMA-staged 2D kernel (default), 1: plain global-memory pull kernel")
+    ap.add_argument("--workload", default="2d_lec", choices=["2d_lec", "3d_warmc", "3d_warmc_128"],
+                    help="2d_lec: 1024 x 512 LEC (default); 3d_warmc: 512 x 256 x 256 WARMC; "
+                         "3d_warmc_128: 128^3 WARMC (small case for profiling)")
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="0: automatic (TMA box per CTA in 2D), 1: plain global-memory pull kernel, "
+                         "2: TMA box per CTA, 3: persistent CTAs with two TMA boxes in flight")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-precision mode table")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 1D and 3D configuration measurements")
     return ap.parse_args()
 
 
 def _config_block(cfg, precision, extra=None):
-    d = {"workload": WORKLOAD_NAME if precision == "fp32" else f"2d_lec_1024x512_{precision}",
-         "grid_zx": list(cfg["n"]), "dx": cfg["dx"], "courant": cfg["courant"], "tau": cfg["tau"],
+    grid = "x".join(str(v) for v in cfg["n"])
+    d = {"workload": f"{cfg['dim']}d_{cfg['closure']}_{grid}_{precision}",
+         "grid": list(cfg["n"]), "dx": cfg["dx"], "courant": cfg["courant"], "tau": cfg["tau"],
          "closure": cfg["closure"], "D": cfg["dv"], "mu": cfg["mu"], "alpha": cfg["alpha"],
          "sigma_z": cfg["sigma_z"], "sigma_r": cfg["sigma_r"], "precision": precision,
-         "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+         "l2": "flushed between timed steps (256 MiB write, then 256 MiB read)", "parallelism": "replicas"}
     if extra:
         d.update(extra)
     return d
@@ -144,14 +159,19 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 def _time_steps(run, stream, steps, warmup, flush):
+    """Per-step CUDA events on the launch stream.  Between timed steps L2 is
+    flushed by writing one 256 MiB buffer and then reading another, so the
+    timed step finds its inputs in HBM and no dirty flush lines left in L2."""
     import torch
+    wbuf, rbuf, sink = flush
     for _ in range(warmup):
         run.step(1)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
     for k in range(steps):
         with torch.cuda.stream(stream):
-            flush.zero_()
+            wbuf.fill_(k & 0xFF)
+            torch.amax(rbuf, dim=0, out=sink)
         ev[k][0].record(stream)
         run.step(1)
         ev[k][1].record(stream)
@@ -205,9 +225,13 @@ def run_ours(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lb.load_library()
-    cfg = dict(WORKLOAD_2D)
+    cfg = {"2d_lec": WORKLOAD_2D, "3d_warmc": CONFIG_3D,
+           "3d_warmc_128": dict(CONFIG_3D, n=(128, 128, 128), z0=2.0)}[a.workload]
+    cfg = dict(cfg)
     stream = torch.cuda.Stream(device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = (torch.empty(256 << 20, dtype=torch.uint8, device=dev),
+             torch.zeros((1024, 64 << 10), dtype=torch.float32, device=dev),
+             torch.empty(64 << 10, dtype=torch.float32, device=dev))
     peaks, peak_kind = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
 
@@ -225,7 +249,8 @@ def run_ours(a):
         gbs = info.bytes_per_update * info.ncell / (mean_ms * 1e-3) / 1e9
         return dict(mlups=mlups, ms=mean_ms, gbs=gbs, frac=gbs / hbm, bytes_per_update=info.bytes_per_update,
                     ncell=info.ncell, total_ms=sum(times), nonfinite=bad, times=times,
-                    kernel="lb_step_tma2d_kernel" if info.kernel_variant == 0 else "lb_step_kernel")
+                    kernel={3: "lb_step_persist2d_kernel", 1: "lb_step_kernel",
+                            2: "lb_step_tma2d_kernel"}[info.kernel_variant])
 
     with ClockSampler(local) as clk:
         main = measure(a.precision, a.steps, a.warmup)
@@ -255,7 +280,8 @@ def run_ours(a):
         "config": _config_block(cfg, a.precision, {"kernel": main["kernel"]}),
         "roofline": {
             "bound": "hbm", "achieved": round(main["gbs"], 2), "peak": hbm, "unit": "GB/s",
-            "frac": round(main["frac"], 4), "traffic": _traffic_for(f"lb_step_2d_lec_{a.precision}_1024x512"),
+            "frac": round(main["frac"], 4),
+            "traffic": _traffic_for(f"{main['kernel']}:{_config_block(cfg, a.precision)['workload']}"),
             "bytes_per_update": main["bytes_per_update"], "peak_source": f"{peak_kind} hbm_gbs",
         },
         "clocks": clocks,
@@ -264,18 +290,21 @@ def run_ours(a):
     if main["nonfinite"]:
         out["warning"] = "non-finite populations at the end of the timed run"
 
-    if rank == 0 and not a.no_modes:
+    if rank == 0 and not a.no_modes and a.workload == "2d_lec":
         modes = {}
         for prec in ("fp64", "fp32", "fp16s"):
             for mu in (1e-3, 1e-2):
-                for variant in (0, 1):
+                for variant in (0, 1, 3):
                     steps = 300 if prec == "fp64" else 1000
                     r = measure(prec, steps, 5, mu=mu, variant=variant)
-                    key = f"lec_{prec}_mu{mu:g}" + ("" if variant == 0 else "_plain")
+                    key = f"lec_{prec}_mu{mu:g}" + {0: "", 1: "_plain", 3: "_persistent"}[variant]
                     modes[key] = {"mlups": round(r["mlups"], 2), "ms_per_step": round(r["ms"], 5),
                                   "achieved_gbs": round(r["gbs"], 1), "frac_of_measured_hbm": round(r["frac"], 4),
                                   "bytes_per_update": r["bytes_per_update"], "steps": steps, "kernel": r["kernel"]}
         out["modes"] = modes
+
+    if rank == 0 and not a.no_configs and a.workload == "2d_lec":
+        out["configs_measured"] = _configs(stream, flush, hbm)
 
     if rank == 0 and not a.no_e2e:
         out["e2e"] = _e2e(cfg, a, world)
@@ -290,6 +319,44 @@ def run_ours(a):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def _configs(stream, flush, hbm):
+    """The 1D configuration as a whole run (4000 steps, FP64) and the 3D
+    configuration (FP32 storage) over a few timed steps."""
+    import torch
+
+    from paper_2309_04872_gb300 import lbpwfa as lb
+    res = {}
+    with lb.Run(CONFIG_1D, "fp64", stream=stream.cuda_stream) as run:
+        run.step(10)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run.step(4000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res["1d_lec_fp64_2048"] = {"steps": 4000, "ms_total": round(ms, 3), "steps_per_s": round(4000 / ms * 1e3, 1),
+                                   "mlups": round(2048 * 4000 / ms / 1e3, 2),
+                                   "note": "state is L2-resident and launch-bound; no flush"}
+    for prec in ("fp32", "fp64"):
+        try:
+            with lb.Run(CONFIG_3D, prec, stream=stream.cuda_stream) as run:
+                info = run.info()
+                times = _time_steps(run, stream, 6 if prec == "fp64" else 10, 3, flush)
+        except lb.LbpwfaError as err:
+            res[f"3d_warmc_{prec}_512x256x256"] = {"error": str(err)}
+            continue
+        mean = sum(times) / len(times)
+        gbs = info.bytes_per_update * info.ncell / (mean * 1e-3) / 1e9
+        res[f"3d_warmc_{prec}_512x256x256"] = {
+            "mlups": round(info.ncell / (mean * 1e-3) / 1e6, 2), "ms_per_step": round(mean, 3),
+            "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
+            "bytes_per_update": info.bytes_per_update, "steps": len(times),
+            "kernel": {3: "lb_step_persist2d_kernel", 1: "lb_step_kernel", 2: "lb_step_tma2d_kernel"}[info.kernel_variant],
+            "device_gb": round(info.device_bytes / 1e9, 2)}
+    return res
 
 
 def _e2e(cfg, a, world):

@@ -100,9 +100,12 @@ typedef struct {
   void* stream;            /* cudaStream_t to queue work on; NULL = a stream
                               owned by the library */
   int kernel_variant;      /* 0: automatic (2D open-boundary runs stage each
-                              tile's populations in shared memory with a TMA
-                              bulk-tensor load), 1: plain global-memory pull.
-                              Both compute the same step. */
+                              tile's populations in shared memory with one
+                              TMA bulk-tensor load per CTA; the rest pull
+                              from global memory); 1: plain global-memory
+                              pull; 2: one TMA box per CTA (as 0 for 2D);
+                              3: LEC 2D with one persistent CTA per SM and two
+                              TMA boxes in flight.  All compute the same step. */
 } lbpwfa_params;
 
 typedef struct {
@@ -116,7 +119,8 @@ typedef struct {
   double bytes_per_update; /* algorithmic HBM bytes of one node update of the
                               step kernel (populations + fields [+ WARMC
                               previous-step values]) */
-  int kernel_variant;      /* step kernel in use: 0 TMA-staged, 1 plain */
+  int kernel_variant;      /* step kernel in use: 1 plain, 2 TMA box per CTA,
+                              3 persistent TMA */
 } lbpwfa_info_t;
 
 /* Create a run: validates *p, allocates all device state on the handle's

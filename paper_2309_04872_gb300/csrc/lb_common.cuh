@@ -244,6 +244,45 @@ __device__ __forceinline__ void decode_lec(real n, const real* Ap, real cH, int 
   if (gamma_out) *gamma_out = g;
 }
 
+// FP32 form of the same iteration for the reduced-precision modes.  Inside
+// the loop H uses the hardware reciprocal square root and log2/exp2 for
+// (n/gamma)^(2/D); their error is scaled by (1 + D/2) mu in H (below 1e-8
+// for mu <= 5e-2).  The returned u and Pi are evaluated once more with
+// correctly rounded sqrt, reciprocal and cbrt.
+template <int DIM>
+__device__ __forceinline__ void decode_lec_f32(float n, const float* Ap, float cH, int D, float* u, float& Pi) {
+  const float in_ = __frcp_rn(n);
+  float p0[DIM], p[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { p0[a] = Ap[a] * in_; p[a] = p0[a]; }
+  const float e = 2.0f / (float)D;
+  for (int it = 0; it < 32; ++it) {
+    float s = 1.0f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) s = fmaf(p[a], p[a], s);
+    const float x = n * rsqrtf(s);
+    const float pw = D == 1 ? x * x : exp2f(e * __log2f(x));
+    const float iH = __frcp_rn(fmaf(cH, pw, 1.0f));
+    float d = 0.0f, pm = 0.0f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const float pn = p0[a] * iH;
+      d = fmaxf(d, fabsf(pn - p[a]));
+      pm = fmaxf(pm, fabsf(pn));
+      p[a] = pn;
+    }
+    if (d <= 4e-7f * pm) break;
+  }
+  float s = 1.0f;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) s = fmaf(p[a], p[a], s);
+  const float ig = __frcp_rn(sqrtf(s));
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) u[a] = p[a] * ig;
+  const float x = n * ig;
+  Pi = x * pow_2_over_D<float>(x, D);
+}
+
 // Driver longitudinal factor L(zeta) (Eq. bunch-density, rms reading).
 template <typename real>
 __device__ __forceinline__ real driver_long(const StepParams& P, const StepConst<real>& S, real zeta) {

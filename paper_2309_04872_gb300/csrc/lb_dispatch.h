@@ -34,6 +34,13 @@ struct KernelSet {
   size_t tma_smem;
   cudaError_t (*prepare_tma)();
   void (*step_tma)(const StepParams&, const void* tensor_map, dim3 grid, cudaStream_t);
+  // persistent double-buffered TMA 2D step (LEC); has_persist == false when not built
+  bool has_persist;
+  int per_tz, per_tx;
+  int per_box[3];
+  size_t per_smem;
+  cudaError_t (*prepare_persist)();
+  void (*step_persist)(const StepParams&, const void* tensor_map, int grid, int ntz, int ntiles, cudaStream_t);
 };
 
 bool kernels_f64(int dim, int closure, KernelSet* ks);

@@ -7,16 +7,23 @@
 
 namespace lbp {
 
-template <int DIM> struct Tile;
-template <> struct Tile<1> { static constexpr int TZ = 128, TX = 1, TY = 1; };
-template <> struct Tile<2> { static constexpr int TZ = 32, TX = 8, TY = 1; };
-template <> struct Tile<3> { static constexpr int TZ = 32, TX = 4, TY = 2; };
+// Tiles of the plain step kernel.  1D: 64 nodes per CTA spreads the 2048-node
+// run over 32 SMs.  3D: 32 x 4 x 4 keeps the decode halo at 2.4x the tile
+// (512 threads, register budget 128) where the closure fits that budget
+// (LEC in FP32/FP16S); the WARMC sources need more registers, so WARMC and
+// FP64 keep 32 x 4 x 2 (256 threads).
+template <int DIM, int CL, int PR> struct Tile;
+template <int CL, int PR> struct Tile<1, CL, PR> { static constexpr int TZ = 64, TX = 1, TY = 1; };
+template <int CL, int PR> struct Tile<2, CL, PR> { static constexpr int TZ = 32, TX = 8, TY = 1; };
+template <int CL, int PR> struct Tile<3, CL, PR> {
+  static constexpr int TZ = 32, TX = 4, TY = (PR == PR_F64 || CL == CL_WARMC) ? 2 : 4;
+};
 
 inline unsigned grid1(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 template <int DIM, int CL, int PR>
 struct Impl {
-  using T = Tile<DIM>;
+  using T = Tile<DIM, CL, PR>;
   using Cfg = StepCfg<DIM, CL, PR, T::TZ, T::TX, T::TY>;
   using real = typename Prec<PR>::real;
   using store = typename Prec<PR>::store;
@@ -68,7 +75,29 @@ struct Impl {
       lb_step_tma2d_kernel<CL, PR><<<grid, TC::TZ * TC::TX, TC::smem_bytes, s>>>(
           P, *reinterpret_cast<const CUtensorMap*>(map));
   }
+  using PC = PersistCfg2D<CL, PR>;
+  static constexpr bool kPersist = DIM == 2 && PC::enabled;
+  static cudaError_t prepare_persist() {
+    if constexpr (kPersist)
+      return cudaFuncSetAttribute(lb_step_persist2d_kernel<CL, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)PC::smem_bytes);
+    return cudaErrorNotSupported;
+  }
+  static void step_persist(const StepParams& P, const void* map, int grid, int ntz, int ntiles, cudaStream_t s) {
+    if constexpr (kPersist)
+      lb_step_persist2d_kernel<CL, PR><<<grid, PC::TZ * PC::TX, PC::smem_bytes, s>>>(
+          P, *reinterpret_cast<const CUtensorMap*>(map), ntz, ntiles);
+  }
   static void fill(KernelSet* ks) {
+    ks->has_persist = kPersist;
+    ks->per_tz = PC::TZ;
+    ks->per_tx = PC::TX;
+    ks->per_box[0] = PC::BZ;
+    ks->per_box[1] = PC::BX;
+    ks->per_box[2] = PC::BK;
+    ks->per_smem = PC::smem_bytes;
+    ks->prepare_persist = &prepare_persist;
+    ks->step_persist = &step_persist;
     ks->has_tma = kTma;
     ks->tma_tz = TC::TZ;
     ks->tma_tx = TC::TX;

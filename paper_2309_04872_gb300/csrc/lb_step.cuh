@@ -19,6 +19,15 @@
 
 namespace lbp {
 
+template <int DIM>
+__host__ __device__ constexpr bool opposite_pairs() {
+  using L = Lattice<DIM>;
+  for (int i = 1; i + 1 < L::Q; i += 2)
+    for (int a = 0; a < 3; ++a)
+      if (L::c(i + 1, a) != -L::c(i, a) || L::w(i + 1) != L::w(i)) return false;
+  return true;
+}
+
 __host__ __device__ constexpr int levi(int i, int j, int k) {
   return (i == j || j == k || i == k) ? 0
        : (((i == 0 && j == 1) || (i == 1 && j == 2) || (i == 2 && j == 0)) ? 1 : -1);
@@ -33,18 +42,20 @@ struct StepCfg {
   static constexpr int RX = DIM >= 2 ? TX + 2 : 1;
   static constexpr int RY = DIM >= 3 ? TY + 2 : 1;
   static constexpr int NR = RZ * RX * RY;
-  static constexpr size_t smem_bytes = (size_t)(M::NM + 3) * NR * sizeof(real);
+  // records, E slots, and the separable driver factors of the tile's slots
+  static constexpr int NDRV = (TZ + 1) + (TX + 1) + (TY + 1);
+  static constexpr size_t smem_bytes = ((size_t)(M::NM + 3) * NR + NDRV) * sizeof(real);
   __host__ __device__ static constexpr int stride(int a) { return a == 0 ? 1 : (a == 1 ? RZ : RZ * RX); }
 };
 
 // Deviations of the pulled populations f^n_ki - w_i A_rest,k at node
 // (z, x, y) (already inside the domain), straight from global memory.
-template <int DIM, int CL, int PR>
+template <int DIM, int CL, int PR, bool EDGE>
 __device__ __forceinline__ void pulled_dev(const StepParams& P, int z, int x, int y, int k,
                                            typename Prec<PR>::real* df) {
   using L = Lattice<DIM>;
   using store = typename Prec<PR>::store;
-  if (!P.periodic) {
+  if (EDGE && !P.periodic) {
     z = min(max(z, 1), P.n[0] - 2);
     if (DIM >= 2) x = min(max(x, 1), P.n[1] - 2);
     if (DIM >= 3) y = min(max(y, 1), P.n[2] - 2);
@@ -55,7 +66,7 @@ __device__ __forceinline__ void pulled_dev(const StepParams& P, int z, int x, in
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     int sz = z - L::c(i, 0), sx = x - L::c(i, 1), sy = y - L::c(i, 2);
-    if (P.periodic) {
+    if (EDGE && P.periodic) {
       sz = sz < 0 ? sz + P.n[0] : (sz >= P.n[0] ? sz - P.n[0] : sz);
       if (DIM >= 2) sx = sx < 0 ? sx + P.n[1] : (sx >= P.n[1] ? sx - P.n[1] : sx);
       if (DIM >= 3) sy = sy < 0 ? sy + P.n[2] : (sy >= P.n[2] ? sy - P.n[2] : sy);
@@ -69,8 +80,9 @@ __device__ __forceinline__ void pulled_dev(const StepParams& P, int z, int x, in
 template <int DIM, int CL, int PR>
 struct GlobalPull {
   const StepParams& P;
-  __device__ __forceinline__ void operator()(int z, int x, int y, int k, typename Prec<PR>::real* df) const {
-    pulled_dev<DIM, CL, PR>(P, z, x, y, k, df);
+  template <bool EDGE>
+  __device__ __forceinline__ void get(int z, int x, int y, int k, typename Prec<PR>::real* df) const {
+    pulled_dev<DIM, CL, PR, EDGE>(P, z, x, y, k, df);
   }
 };
 
@@ -84,7 +96,8 @@ __device__ __forceinline__ void decode_record(const StepParams& P, const StepCon
     real Ap[DIM], u[DIM], Pi;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) Ap[a] = dA[1 + a];
-    decode_lec<DIM, real>(n, Ap, S.cH, P.D, u, Pi);
+    if constexpr (sizeof(real) == 4) decode_lec_f32<DIM>(n, Ap, S.cH, P.D, u, Pi);
+    else decode_lec<DIM, real>(n, Ap, S.cH, P.D, u, Pi);
     rec[M::R_N] = n;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) rec[M::R_U + a] = u[a];
@@ -121,49 +134,212 @@ __device__ __forceinline__ void decode_record(const StepParams& P, const StepCon
   }
 }
 
+// Field values around the own node, loaded at the start of the kernel so
+// that their latency overlaps the population staging and the decode.
+//   Ec[a]    = E_a^{n-1/2} at the node's slot
+//   Bc[a]    = B_a^n at the node's slot
+//   Bp[d][b] = B_d^n one node up along axis b (curl at the E slot)
+//   Bm[a]    = B_a^n one node down along a (node average of B_a)
+template <typename real>
+struct FieldPF {
+  real Ec[3], Bc[3], Bp[3][3], Bm[3];
+};
+
+template <bool EDGE>
+__device__ __forceinline__ int nb_offset(const StepParams& P, int e, int axis, int delta) {
+  if (!EDGE) return delta * P.axis_stride[axis];
+  const int v = wrap_or_clamp(e + delta, P.n[axis], P.periodic);
+  return (v - e) * P.axis_stride[axis];
+}
+
+template <int DIM, typename real, bool EDGE>
+__device__ __forceinline__ void load_fields(const StepParams& P, int e0, int e1, int e2, int id, FieldPF<real>& F) {
+  const real* Ein = reinterpret_cast<const real*>(P.Ein);
+  const real* Bin = reinterpret_cast<const real*>(P.Bin);
+  const int pl = (int)P.plane;
+  const int e[3] = {e0, e1, e2};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (e_present<DIM>(a)) F.Ec[a] = Ein[a * pl + id];
+    if (b_present<DIM>(a)) {
+      F.Bc[a] = Bin[a * pl + id];
+      if (axis_present<DIM>(a)) F.Bm[a] = Bin[a * pl + id + nb_offset<EDGE>(P, e[a], a, -1)];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!e_present<DIM>(a)) continue;
+    const int b = (a + 1) % 3, d = (a + 2) % 3;
+    if (axis_present<DIM>(b) && b_present<DIM>(d)) F.Bp[d][b] = Bin[d * pl + id + nb_offset<EDGE>(P, e[b], b, +1)];
+    if (axis_present<DIM>(d) && b_present<DIM>(b)) F.Bp[b][d] = Bin[b * pl + id + nb_offset<EDGE>(P, e[d], d, +1)];
+  }
+}
+
+// Driver current n_b at the E_z slot of node e: L(z - z0 - t) at the node's
+// z, times the transverse Gaussians half a cell up along x and y.
+template <int DIM, typename real>
+__device__ __forceinline__ real driver_at(const StepParams& P, const StepConst<real>& S, int e0, int e1, int e2) {
+  real nbv = driver_long<real>(P, S, real(e0) * S.dx - S.zeta0);
+  if (DIM >= 2) {
+    const real x = (real(e1) - S.xoff + real(0.5)) * S.dx;
+    real r2 = x * x;
+    if (DIM >= 3) {
+      const real y = (real(e2) - S.yoff + real(0.5)) * S.dx;
+      r2 += y * y;
+    }
+    nbv *= exp(-r2 * S.inv2sr2);
+  }
+  return nbv;
+}
+
+// E_a^{n+1/2} at the slot of node e (region index r): dual-grid curl of B^n,
+// n u_a averaged over the nodes around the slot, driver current for a = z.
+template <int DIM, int CL, int PR, int TZ, int TX, int TY, bool EDGE>
+__device__ __forceinline__ void e_slot(const StepParams& P, const StepConst<typename Prec<PR>::real>& S,
+                                       const typename Prec<PR>::real* smac, typename Prec<PR>::real* sE,
+                                       const typename Prec<PR>::real* sdrv, int oz, int ox, int oy,
+                                       int r, int e0, int e1, int e2,
+                                       const FieldPF<typename Prec<PR>::real>& F) {
+  using C = StepCfg<DIM, CL, PR, TZ, TX, TY>;
+  using M = Model<DIM, CL>;
+  using real = typename Prec<PR>::real;
+  constexpr int NR = C::NR;
+  const int e[3] = {e0, e1, e2};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!e_present<DIM>(a)) continue;
+    const int b = (a + 1) % 3, d = (a + 2) % 3;
+    if (EDGE && !P.periodic) {
+      bool wall = false;
+      if (b >= 1 && axis_present<DIM>(b) && e[b] == P.n[b] - 1) wall = true;
+      if (d >= 1 && axis_present<DIM>(d) && e[d] == P.n[d] - 1) wall = true;
+      if (wall) { sE[a * NR + r] = real(0); continue; }
+    }
+    real curl = 0;
+    if (axis_present<DIM>(b) && b_present<DIM>(d)) curl += (F.Bp[d][b] - F.Bc[d]) * S.idx;
+    if (axis_present<DIM>(d) && b_present<DIM>(b)) curl -= (F.Bp[b][d] - F.Bc[b]) * S.idx;
+    real J = 0;
+    if (a < DIM) {
+      const bool ob = axis_present<DIM>(b), od = axis_present<DIM>(d);
+      const int sb = ob ? C::stride(b) : 0, sd = od ? C::stride(d) : 0;
+      const int nb = ob ? 2 : 1, nd = od ? 2 : 1;
+#pragma unroll
+      for (int jb = 0; jb < 2; ++jb)
+#pragma unroll
+        for (int jd = 0; jd < 2; ++jd) {
+          if (jb < nb && jd < nd) {
+            const int rr = r + jb * sb + jd * sd;
+            J += smac[M::R_N * NR + rr] * smac[(M::R_U + a) * NR + rr];
+          }
+        }
+      J *= real(1) / real(nb * nd);
+    }
+    if (a == 0) {
+      real nbv;
+      if (!EDGE) {
+        // separable driver n_b = L(zeta) T(x) T(y) from the tile's tables
+        nbv = sdrv[e0 - oz];
+        if (DIM >= 2) nbv *= sdrv[(TZ + 1) + (e1 - ox)];
+        if (DIM >= 3) nbv *= sdrv[(TZ + 1) + (TX + 1) + (e2 - oy)];
+      } else {
+        nbv = driver_at<DIM, real>(P, S, e0, e1, e2);
+      }
+      J += nbv;
+    }
+    sE[a * NR + r] = F.Ec[a] + S.dt * (curl + J);
+  }
+}
+
+// Decode one region node (z, x, y already inside the domain) into its record.
+template <int DIM, int CL, int PR, bool EDGE, class Pull>
+__device__ __forceinline__ void decode_node(const StepParams& P, const StepConst<typename Prec<PR>::real>& S,
+                                            const Pull& pull, int z, int x, int y, typename Prec<PR>::real* smac,
+                                            int NR, int r) {
+  using M = Model<DIM, CL>;
+  using real = typename Prec<PR>::real;
+  constexpr int K = M::K, Q = Lattice<DIM>::Q;
+  real dA[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    real df[Q];
+    pull.template get<EDGE>(z, x, y, k, df);
+    real s = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) s += df[i];
+    dA[k] = s;
+  }
+  real rec[M::NM];
+  decode_record<DIM, CL, real>(P, S, dA, rec);
+#pragma unroll
+  for (int m = 0; m < M::NM; ++m) smac[m * NR + r] = rec[m];
+}
+
 // The three phases of one step for the CTA's tile; `pull` supplies the
 // deviations of the pulled populations of a node (global memory or a staged
 // shared-memory box).  `smem` holds the records and the E^{n+1/2} slots.
-template <int DIM, int CL, int PR, int TZ, int TX, int TY, class Pull>
-__device__ __forceinline__ void step_body(const StepParams& P, unsigned char* smem, const Pull& pull) {
+// EDGE = false promises that the tile and its halo lie in the bulk
+// (1 <= index <= n-2 on every axis), so no boundary rule applies.
+// In 1D and 2D the caller loads the own node's fields (FieldPF) before the
+// populations arrive; in 3D, where registers are scarce, they are loaded here
+// just before they are used.
+template <int DIM> struct EarlyFields { static constexpr bool value = DIM <= 2; };
+
+template <int DIM, int CL, int PR, int TZ, int TX, int TY, bool EDGE, class Pull>
+__device__ __forceinline__ void step_body(const StepParams& P, unsigned char* smem, const Pull& pull,
+                                          FieldPF<typename Prec<PR>::real>& F, int tile_z, int tile_x,
+                                          int tile_y) {
   using C = StepCfg<DIM, CL, PR, TZ, TX, TY>;
   using M = Model<DIM, CL>;
   using L = Lattice<DIM>;
   using real = typename Prec<PR>::real;
   using store = typename Prec<PR>::store;
-  constexpr int NT = C::NT, RZ = C::RZ, RX = C::RX, NR = C::NR;
+  constexpr int NT = C::NT, RZ = C::RZ, RX = C::RX, RY = C::RY, NR = C::NR;
   constexpr int K = M::K, Q = L::Q;
   constexpr bool KEEP = K * Q <= 32;  // own node's pulled populations stay in registers
 
   const StepConst<real>& S = consts<real>(P);
   real* smac = reinterpret_cast<real*>(smem);  // [NM][NR]
   real* sE = smac + M::NM * NR;                 // [3][NR]
+  real* sdrv = sE + 3 * NR;                     // [TZ+1 | TX+1 | TY+1] driver factors
 
   const int tid = threadIdx.x;
   const int tz = tid % TZ, tx = (tid / TZ) % TX, ty = tid / (TZ * TX);
-  const int gz0 = blockIdx.x * TZ, gx0 = blockIdx.y * TX, gy0 = blockIdx.z * TY;
+  const int gz0 = tile_z * TZ, gx0 = tile_x * TX, gy0 = tile_y * TY;
   const int oz = gz0 - 1, ox = gx0 - (DIM >= 2 ? 1 : 0), oy = gy0 - (DIM >= 3 ? 1 : 0);
-  const real dt = S.dt, idx_ = S.idx, i2dx = S.i2dx;
   const int pl = (int)P.plane;
-  const real* Ein = reinterpret_cast<const real*>(P.Ein);
-  const real* Bin = reinterpret_cast<const real*>(P.Bin);
 
-  // own node (ragged tiles: nodes past the domain still decode a clamped copy)
+  if (!EDGE) {
+    // separable driver factors of the slots [oz, oz + TZ] x [ox, ox + TX] x [oy, oy + TY]
+    for (int t = tid; t < C::NDRV; t += NT) {
+      real v;
+      if (t <= TZ) {
+        v = driver_long<real>(P, S, real(oz + t) * S.dx - S.zeta0);
+      } else if (t <= TZ + 1 + TX) {
+        const real x = (real(ox + t - (TZ + 1)) - S.xoff + real(0.5)) * S.dx;
+        v = DIM >= 2 ? exp(-x * x * S.inv2sr2) : real(1);
+      } else {
+        const real y = (real(oy + t - (TZ + 1) - (TX + 1)) - S.yoff + real(0.5)) * S.dx;
+        v = DIM >= 3 ? exp(-y * y * S.inv2sr2) : real(1);
+      }
+      sdrv[t] = v;
+    }
+  }
+
   const int gz = gz0 + tz, gx = DIM >= 2 ? gx0 + tx : 0, gy = DIM >= 3 ? gy0 + ty : 0;
-  const bool own_inside = gz < P.n[0] && (DIM < 2 || gx < P.n[1]) && (DIM < 3 || gy < P.n[2]);
+  const bool own_inside = !EDGE || (gz < P.n[0] && (DIM < 2 || gx < P.n[1]) && (DIM < 3 || gy < P.n[2]));
   const int r_own = (tz + 1) + RZ * ((DIM >= 2 ? tx + 1 : 0) + RX * (DIM >= 3 ? ty + 1 : 0));
 
   // ---------------- A: pull + decode of the tile and its halo -------------
   real keep[KEEP ? K * Q : 1];
   real dA_own[K];
   {
-    const int ez = wrap_or_clamp(gz, P.n[0], P.periodic);
-    const int ex = DIM >= 2 ? wrap_or_clamp(gx, P.n[1], P.periodic) : 0;
-    const int ey = DIM >= 3 ? wrap_or_clamp(gy, P.n[2], P.periodic) : 0;
+    const int ez = EDGE ? wrap_or_clamp(gz, P.n[0], P.periodic) : gz;
+    const int ex = DIM >= 2 ? (EDGE ? wrap_or_clamp(gx, P.n[1], P.periodic) : gx) : 0;
+    const int ey = DIM >= 3 ? (EDGE ? wrap_or_clamp(gy, P.n[2], P.periodic) : gy) : 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       real df[Q];
-      pull(ez, ex, ey, k, df);
+      pull.template get<EDGE>(ez, ex, ey, k, df);
       real s = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -177,129 +353,100 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
 #pragma unroll
     for (int m = 0; m < M::NM; ++m) smac[m * NR + r_own] = rec[m];
   }
-  for (int r = tid; r < NR; r += NT) {
-    const int rz = r % RZ, rx = (r / RZ) % RX, ry = r / (RZ * RX);
-    const bool interior = rz >= 1 && rz <= TZ && (DIM < 2 || (rx >= 1 && rx <= TX)) &&
-                          (DIM < 3 || (ry >= 1 && ry <= TY));
-    if (interior) continue;
-    const int ez = wrap_or_clamp(oz + rz, P.n[0], P.periodic);
-    const int ex = DIM >= 2 ? wrap_or_clamp(ox + rx, P.n[1], P.periodic) : 0;
-    const int ey = DIM >= 3 ? wrap_or_clamp(oy + ry, P.n[2], P.periodic) : 0;
-    real dA[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      real df[Q];
-      pull(ez, ex, ey, k, df);
-      real s = 0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) s += df[i];
-      dA[k] = s;
+  // halo ring
+  if constexpr (DIM <= 2) {
+    constexpr int NRING = NR - NT;
+    for (int h = tid; h < NRING; h += NT) {
+      int rz, rx = 0;
+      if constexpr (DIM == 1) {
+        rz = h == 0 ? 0 : RZ - 1;
+      } else {
+        if (h < RZ) { rz = h; rx = 0; }
+        else if (h < 2 * RZ) { rz = h - RZ; rx = RX - 1; }
+        else { const int j = h - 2 * RZ; rz = (j & 1) ? RZ - 1 : 0; rx = 1 + (j >> 1); }
+      }
+      const int r = rz + RZ * rx;
+      int z = oz + rz, x = ox + rx;
+      if (EDGE) {
+        z = wrap_or_clamp(z, P.n[0], P.periodic);
+        if (DIM >= 2) x = wrap_or_clamp(x, P.n[1], P.periodic);
+      }
+      decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, 0, smac, NR, r);
     }
-    real rec[M::NM];
-    decode_record<DIM, CL, real>(P, S, dA, rec);
-#pragma unroll
-    for (int m = 0; m < M::NM; ++m) smac[m * NR + r] = rec[m];
+  } else {
+    // 3D: stride over the region and skip the interior
+    for (int r = tid; r < NR; r += NT) {
+      const int rz = r % RZ, rx = (r / RZ) % RX, ry = r / (RZ * RX);
+      if (rz >= 1 && rz <= TZ && rx >= 1 && rx <= TX && ry >= 1 && ry <= TY) continue;
+      int z = oz + rz, x = ox + rx, y = oy + ry;
+      if (EDGE) {
+        z = wrap_or_clamp(z, P.n[0], P.periodic);
+        x = wrap_or_clamp(x, P.n[1], P.periodic);
+        y = wrap_or_clamp(y, P.n[2], P.periodic);
+      }
+      decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, y, smac, NR, r);
+    }
   }
   __syncthreads();
 
   // ---------------- B: E^{n+1/2} on the slots of tile + low halo ----------
+  if constexpr (!EarlyFields<DIM>::value) {
+    if (own_inside) load_fields<DIM, real, EDGE>(P, gz, gx, gy, cell_index32(P, gz, gx, gy), F);
+  }
+  if (own_inside) e_slot<DIM, CL, PR, TZ, TX, TY, EDGE>(P, S, smac, sE, sdrv, oz, ox, oy, r_own, gz, gx, gy, F);
   {
+    // low-side halo slots: region cells with rz = 0 (or rx = 0, ry = 0) in
+    // [0, TZ] x [0, TX] x [0, TY]
     constexpr int SZ = TZ + 1, SX = DIM >= 2 ? TX + 1 : 1, SY = DIM >= 3 ? TY + 1 : 1;
-    for (int q = tid; q < SZ * SX * SY; q += NT) {
-      const int rz = q % SZ, rx = (q / SZ) % SX, ry = q / (SZ * SX);
+    constexpr int NHALO = DIM == 3 ? SZ * SX * SY : SZ * SX * SY - TZ * (DIM >= 2 ? TX : 1);
+    for (int h = tid; h < NHALO; h += NT) {
+      int rz = 0, rx = 0, ry = 0;
+      if constexpr (DIM == 1) {
+        rz = 0;
+      } else if constexpr (DIM == 2) {
+        if (h < SZ) { rz = h; rx = 0; } else { rz = 0; rx = h - SZ + 1; }
+      } else {
+        // 3D: stride over the slot box and skip everything but the low faces
+        rz = h % SZ; rx = (h / SZ) % SX; ry = h / (SZ * SX);
+        if (rz != 0 && rx != 0 && ry != 0) continue;
+      }
       const int r = rz + RZ * (rx + RX * ry);
-      const int g0 = oz + rz, g1 = ox + rx, g2 = oy + ry;
-      const bool inside = g0 >= 0 && g0 < P.n[0] && (DIM < 2 || (g1 >= 0 && g1 < P.n[1])) &&
-                          (DIM < 3 || (g2 >= 0 && g2 < P.n[2]));
-      if (!inside && !P.periodic) continue;  // ghost, filled below
-      const int e0 = wrap_or_clamp(g0, P.n[0], 1);
-      const int e1 = DIM >= 2 ? wrap_or_clamp(g1, P.n[1], 1) : 0;
-      const int e2 = DIM >= 3 ? wrap_or_clamp(g2, P.n[2], 1) : 0;
-      const int e[3] = {e0, e1, e2};
-      const int id = cell_index32(P, e0, e1, e2);
+      int e0 = oz + rz, e1 = ox + rx, e2 = oy + ry;
+      int r_eff = r;
+      if (EDGE) {
+        if (P.periodic) {
+          e0 = wrap_or_clamp(e0, P.n[0], 1);
+          if (DIM >= 2) e1 = wrap_or_clamp(e1, P.n[1], 1);
+          if (DIM >= 3) e2 = wrap_or_clamp(e2, P.n[2], 1);
+        } else {
+          // transverse ghost: conducting wall; z ghost: the nearest slot
+          const bool trans_out = (DIM >= 2 && (e1 < 0 || e1 >= P.n[1])) || (DIM >= 3 && (e2 < 0 || e2 >= P.n[2]));
+          if (trans_out) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (!e_present<DIM>(a)) continue;
-        const int b = (a + 1) % 3, d = (a + 2) % 3;
-        bool wall = false;
-        if (!P.periodic) {
-          if (b >= 1 && axis_present<DIM>(b) && e[b] == P.n[b] - 1) wall = true;
-          if (d >= 1 && axis_present<DIM>(d) && e[d] == P.n[d] - 1) wall = true;
-        }
-        if (wall) { sE[a * NR + r] = real(0); continue; }
-        real curl = 0;
-        if (axis_present<DIM>(b) && b_present<DIM>(d)) {
-          const int nb = wrap_or_clamp(e[b] + 1, P.n[b], P.periodic);
-          const int id2 = id + (nb - e[b]) * P.axis_stride[b];
-          curl += (Bin[d * pl + id2] - Bin[d * pl + id]) * idx_;
-        }
-        if (axis_present<DIM>(d) && b_present<DIM>(b)) {
-          const int nb = wrap_or_clamp(e[d] + 1, P.n[d], P.periodic);
-          const int id2 = id + (nb - e[d]) * P.axis_stride[d];
-          curl -= (Bin[b * pl + id2] - Bin[b * pl + id]) * idx_;
-        }
-        // n u_a averaged over the nodes around the slot
-        real J = 0;
-        if (a < DIM) {
-          const bool ob = axis_present<DIM>(b), od = axis_present<DIM>(d);
-          const int sb = ob ? C::stride(b) : 0, sd = od ? C::stride(d) : 0;
-          const int nb = ob ? 2 : 1, nd = od ? 2 : 1;
-#pragma unroll
-          for (int jb = 0; jb < 2; ++jb)
-#pragma unroll
-            for (int jd = 0; jd < 2; ++jd) {
-              if (jb < nb && jd < nd) {
-                const int rr = r + jb * sb + jd * sd;
-                J += smac[M::R_N * NR + rr] * smac[(M::R_U + a) * NR + rr];
-              }
-            }
-          J *= real(1) / real(nb * nd);
-        }
-        if (a == 0) {
-          const real zeta = real(e0) * S.dx - S.zeta0;
-          real nbv = driver_long<real>(P, S, zeta);
-          if (DIM >= 2) {
-            const real x = (real(e1) - S.xoff + real(0.5)) * S.dx;
-            real r2 = x * x;
-            if (DIM >= 3) {
-              const real y = (real(e2) - S.yoff + real(0.5)) * S.dx;
-              r2 += y * y;
-            }
-            nbv *= exp(-r2 * S.inv2sr2);
+            for (int a = 0; a < 3; ++a) if (e_present<DIM>(a)) sE[a * NR + r] = real(0);
+            continue;
           }
-          J += nbv;
+          if (e0 < 0) { r_eff = r + 1; e0 = 0; }
+          if (e0 >= P.n[0]) continue;  // never read
         }
-        sE[a * NR + r] = Ein[a * pl + id] + dt * (curl + J);
+      }
+      const int id = cell_index32(P, e0, e1, e2);
+      FieldPF<real> G;
+      load_fields<DIM, real, EDGE>(P, e0, e1, e2, id, G);
+      e_slot<DIM, CL, PR, TZ, TX, TY, EDGE>(P, S, smac, sE, sdrv, oz, ox, oy, r_eff, e0, e1, e2, G);
+      if (r_eff != r) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) if (e_present<DIM>(a)) sE[a * NR + r] = sE[a * NR + r_eff];
       }
     }
   }
   __syncthreads();
-  if (!P.periodic) {
-    // low-side ghosts: transverse -> conducting wall (0); z -> nearest slot
-    constexpr int SZ = TZ + 1, SX = DIM >= 2 ? TX + 1 : 1, SY = DIM >= 3 ? TY + 1 : 1;
-    for (int q = tid; q < SZ * SX * SY; q += NT) {
-      const int rz = q % SZ, rx = (q / SZ) % SX, ry = q / (SZ * SX);
-      const int r = rz + RZ * (rx + RX * ry);
-      const int g0 = oz + rz, g1 = ox + rx, g2 = oy + ry;
-      bool trans_out = false;
-      if (DIM >= 2) trans_out = trans_out || g1 < 0 || g1 >= P.n[1];
-      if (DIM >= 3) trans_out = trans_out || g2 < 0 || g2 >= P.n[2];
-      if (trans_out) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) if (e_present<DIM>(a)) sE[a * NR + r] = real(0);
-      } else if (g0 < 0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) if (e_present<DIM>(a)) sE[a * NR + r] = sE[a * NR + r + 1];
-      }
-    }
-    __syncthreads();
-  }
 
   // ---------------- C: per tile node ------------------------------------
   if (!own_inside) return;
   const int r = r_own;
   const int id = cell_index32(P, gz, gx, gy);
-  const int e[3] = {gz, gx, gy};
+  const real dt = S.dt;
 
   real* Eout = reinterpret_cast<real*>(P.Eout);
   real* Bout = reinterpret_cast<real*>(P.Bout);
@@ -321,19 +468,14 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       En[a] = s * (real(1) / real(nb * nd));
     }
     if (b_present<DIM>(a)) {
-      const real bo = Bin[a * pl + id];
-      if (axis_present<DIM>(a)) {
-        const int nm = wrap_or_clamp(e[a] - 1, P.n[a], P.periodic);
-        Bn[a] = real(0.5) * (bo + Bin[a * pl + id + (nm - e[a]) * P.axis_stride[a]]);
-      } else {
-        Bn[a] = bo;
-      }
+      const real bo = F.Bc[a];
+      Bn[a] = axis_present<DIM>(a) ? real(0.5) * (bo + F.Bm[a]) : bo;
       const int b = (a + 1) % 3, d = (a + 2) % 3;
       real curl = 0;
       if (axis_present<DIM>(b) && e_present<DIM>(d))
-        curl += (sE[d * NR + r] - sE[d * NR + r - C::stride(b)]) * idx_;
+        curl += (sE[d * NR + r] - sE[d * NR + r - C::stride(b)]) * S.idx;
       if (axis_present<DIM>(d) && e_present<DIM>(b))
-        curl -= (sE[b * NR + r] - sE[b * NR + r - C::stride(d)]) * idx_;
+        curl -= (sE[b * NR + r] - sE[b * NR + r - C::stride(d)]) * S.idx;
       Bout[a * pl + id] = bo - dt * curl;
     }
   }
@@ -354,17 +496,13 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
     uxB[a] = s;
   }
 
-  real F[K];
-  if constexpr (CL == CL_LEC) {
-    F[0] = 0;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      const real gPi = (smac[M::R_PI * NR + r + C::stride(a)] - smac[M::R_PI * NR + r - C::stride(a)]) * i2dx;
-      F[1 + a] = -S.mu * gPi - n * (En[a] + uxB[a]);
-    }
-  } else {
+  // Sources of each advected scalar (Eq. lb-ade-lec-comps-F,
+  // lb-ade-warmc-comps-F with App. A), evaluated per set inside the collide
+  // loop so that only their inputs stay live.
+  real th[3][3], th0[3] = {0, 0, 0}, gw[3][3], divth[3] = {0, 0, 0};
+  real dth00 = 0, dth0[3] = {0, 0, 0}, dw[3] = {0, 0, 0}, divth0 = 0, Eu = 0;
+  if constexpr (CL == CL_WARMC) {
     real* prev = reinterpret_cast<real*>(P.prev);
-    real th[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -372,7 +510,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
         const int j = M::thidx(a, b);
         th[a][b] = j >= 0 ? smac[(M::R_TH + j) * NR + r] : real(0);
       }
-    real th0[3] = {0, 0, 0}, w[3] = {0, 0, 0};
+    real w[3] = {0, 0, 0};
     const real lam = smac[M::R_LAM * NR + r];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { th0[a] = smac[(M::R_TH0 + a) * NR + r]; w[a] = lam * u[a]; }
@@ -380,7 +518,6 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
 #pragma unroll
     for (int a = 0; a < DIM; ++a) th00 += u[a] * th0[a];
     // backward time differences (zero on the first step after a reset)
-    real dth00 = 0, dth0[3] = {0, 0, 0}, dw[3] = {0, 0, 0};
     if (P.have_prev) {
       const real idt = S.idt;
       dth00 = (th00 - prev[id]) * idt;
@@ -396,58 +533,68 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       prev[(1 + a) * pl + id] = th0[a];
       prev[(1 + DIM + a) * pl + id] = w[a];
     }
-    // spatial gradients from the neighbours' records
-    real gw[3][3];  // gw[a][k] = d_k w^a
+    // spatial gradients from the neighbours' records; gw[a][k] = d_k w^a
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int k = 0; k < 3; ++k) gw[a][k] = 0;
-    real divth[3] = {0, 0, 0}, divth0 = 0;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       const int rp = r + C::stride(k), rm = r - C::stride(k);
       const real lp = smac[M::R_LAM * NR + rp], lm = smac[M::R_LAM * NR + rm];
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
-        gw[a][k] = (lp * smac[(M::R_U + a) * NR + rp] - lm * smac[(M::R_U + a) * NR + rm]) * i2dx;
-      divth0 += (smac[(M::R_TH0 + k) * NR + rp] - smac[(M::R_TH0 + k) * NR + rm]) * i2dx;
+        gw[a][k] = (lp * smac[(M::R_U + a) * NR + rp] - lm * smac[(M::R_U + a) * NR + rm]) * S.i2dx;
+      divth0 += (smac[(M::R_TH0 + k) * NR + rp] - smac[(M::R_TH0 + k) * NR + rm]) * S.i2dx;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int j = M::thidx(a, k);
-        if (j >= 0) divth[a] += (smac[(M::R_TH + j) * NR + rp] - smac[(M::R_TH + j) * NR + rm]) * i2dx;
+        if (j >= 0) divth[a] += (smac[(M::R_TH + j) * NR + rp] - smac[(M::R_TH + j) * NR + rm]) * S.i2dx;
       }
     }
-    real Eu = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) Eu += En[a] * u[a];
-    F[0] = 0;
-    F[1] = -dth00 - divth0 - n * Eu;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) F[2 + a] = -dth0[a] - divth[a] - n * (En[a] + uxB[a]);
-#pragma unroll
-    for (int j = 0; j < M::NTH; ++j) {
+  }
+  auto source = [&](int k) -> real {
+    if (k == 0) return real(0);
+    if constexpr (CL == CL_LEC) {
+      const int a = k - 1;
+      const real gPi = (smac[M::R_PI * NR + r + C::stride(a)] - smac[M::R_PI * NR + r - C::stride(a)]) * S.i2dx;
+      return -S.mu * gPi - n * (En[a] + uxB[a]);
+    } else {
+      if (k == 1) return -dth00 - divth0 - n * Eu;
+      if (k < 2 + DIM) {
+        const int a = k - 2;
+        return -dth0[a] - divth[a] - n * (En[a] + uxB[a]);
+      }
+      const int j = k - 2 - DIM;
       const int a = M::tha(j), b = M::thb(j);
-      real s = -th0[b] * dw[a] - th0[a] * dw[b];
+      real sv = -th0[b] * dw[a] - th0[a] * dw[b];
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) s -= th[b][k] * gw[a][k] + th[a][k] * gw[b][k];
+      for (int q = 0; q < DIM; ++q) sv -= th[b][q] * gw[a][q] + th[a][q] * gw[b][q];
       real em = En[a] * th0[b] + En[b] * th0[a];
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
+      for (int q = 0; q < 3; ++q)
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
-          if (levi(a, k, l) != 0) em += real(levi(a, k, l)) * th[b][k] * Bn[l];
-          if (levi(b, k, l) != 0) em += real(levi(b, k, l)) * th[a][k] * Bn[l];
+          if (levi(a, q, l) != 0) em += real(levi(a, q, l)) * th[b][q] * Bn[l];
+          if (levi(b, q, l) != 0) em += real(levi(b, q, l)) * th[a][q] * Bn[l];
         }
-      F[2 + DIM + j] = s - em;
+      return sv - em;
     }
-  }
+  };
 
   // ---------------- collide + store (deviation form) ----------------------
+  // f* - w A_rest = df (1 - 1/tau) + (f^eq - w A_rest)/tau + w dt F, with
+  // f^eq - w A_rest = w (dA + A P_i), P_i = 3 cu + 9/2 cu^2 - 3/2 u^2 split
+  // into its even and odd parts over each pair of opposite velocities.
+  static_assert(opposite_pairs<DIM>(), "lattice order must pair opposite velocities");
   real ul[3] = {0, 0, 0};
   real usq = 0;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) { ul[a] = S.courant * u[a]; usq += ul[a] * ul[a]; }
-  const real itau = S.inv_tau;
+  const real itau = S.inv_tau, omt = real(1) - S.inv_tau;
+  const real base = real(-1.5) * usq;
   store* fout = reinterpret_cast<store*>(P.fout);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -458,27 +605,61 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       for (int i = 0; i < Q; ++i) df[i] = keep[k * Q + i];
       dA = dA_own[k];
     } else {
-      pull(gz, gx, gy, k, df);
+      pull.template get<EDGE>(gz, gx, gy, k, df);
       dA = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) dA += df[i];
     }
     const real A = S.Arest[k] + dA;
-    const real dtF = dt * F[k];
-    const float s = P.scale[k];
+    const real dtF = dt * source(k);
+    const float sc = P.scale[k];
     store* fk = fout + (size_t)k * Q * (size_t)P.plane;
+    {
+      const real w0 = real(L::w(0));
+      const real dfeq = w0 * (dA + A * base);
+      Codec<PR>::store(fk, id, df[0] * omt + dfeq * itau + w0 * dtF, sc);
+    }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int q = 0; q < (Q - 1) / 2; ++q) {
+      const int i = 1 + 2 * q, j = i + 1;
       real cu = 0;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) cu += real(L::c(i, a)) * ul[a];
       const real wi = real(L::w(i));
-      const real Pi = real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq;
-      const real dfeq = wi * (dA + A * Pi);
-      const real v = df[i] - (df[i] - dfeq) * itau + wi * dtF;
-      Codec<PR>::store(fk, i * pl + id, v, s);
+      const real even = wi * (dA + A * (base + real(4.5) * cu * cu));
+      const real odd = (real(3) * wi) * A * cu;
+      const real wF = wi * dtF;
+      Codec<PR>::store(fk, i * pl + id, df[i] * omt + (even + odd) * itau + wF, sc);
+      Codec<PR>::store(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF, sc);
     }
   }
+}
+
+// Whether the tile and its one-node halo lie in the bulk on every axis.
+template <int DIM, int TZ, int TX, int TY>
+__device__ __forceinline__ bool tile_is_bulk(const StepParams& P, int tile_z, int tile_x, int tile_y) {
+  const int gz0 = tile_z * TZ, gx0 = tile_x * TX, gy0 = tile_y * TY;
+  bool bulk = gz0 - 1 >= 1 && gz0 + TZ <= P.n[0] - 2;
+  if (DIM >= 2) bulk = bulk && gx0 - 1 >= 1 && gx0 + TX <= P.n[1] - 2;
+  if (DIM >= 3) bulk = bulk && gy0 - 1 >= 1 && gy0 + TY <= P.n[2] - 2;
+  return bulk;
+}
+
+// Own node's field prefetch (coordinates of a ragged tile's idle threads are
+// clamped so every load stays inside the arrays).
+template <int DIM, typename real, bool EDGE, int TZ, int TX, int TY>
+__device__ __forceinline__ void prefetch_own(const StepParams& P, FieldPF<real>& F, int tile_z, int tile_x,
+                                             int tile_y) {
+  const int tid = threadIdx.x;
+  int gz = tile_z * TZ + tid % TZ;
+  int gx = DIM >= 2 ? tile_x * TX + (tid / TZ) % TX : 0;
+  int gy = DIM >= 3 ? tile_y * TY + tid / (TZ * TX) : 0;
+  if (EDGE) {
+    gz = min(gz, P.n[0] - 1);
+    if (DIM >= 2) gx = min(gx, P.n[1] - 1);
+    if (DIM >= 3) gy = min(gy, P.n[2] - 1);
+  }
+  load_fields<DIM, real, EDGE>(P, gz, gx, gy, cell_index32(P, gz, gx, gy), F);
 }
 
 // Plain variant: populations pulled straight from global memory (any
@@ -486,9 +667,18 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
 template <int DIM, int CL, int PR, int TZ, int TX, int TY>
 __global__ void __launch_bounds__(TZ* TX* TY)
 lb_step_kernel(const StepParams P) {
+  using real = typename Prec<PR>::real;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GlobalPull<DIM, CL, PR> pull{P};
-  step_body<DIM, CL, PR, TZ, TX, TY>(P, smem_raw, pull);
+  FieldPF<real> F;
+  const int bz = blockIdx.x, bx = blockIdx.y, by = blockIdx.z;
+  if (tile_is_bulk<DIM, TZ, TX, TY>(P, bz, bx, by)) {
+    if constexpr (EarlyFields<DIM>::value) prefetch_own<DIM, real, false, TZ, TX, TY>(P, F, bz, bx, by);
+    step_body<DIM, CL, PR, TZ, TX, TY, false>(P, smem_raw, pull, F, bz, bx, by);
+  } else {
+    if constexpr (EarlyFields<DIM>::value) prefetch_own<DIM, real, true, TZ, TX, TY>(P, F, bz, bx, by);
+    step_body<DIM, CL, PR, TZ, TX, TY, true>(P, smem_raw, pull, F, bz, bx, by);
+  }
 }
 
 }  // namespace lbp

@@ -78,10 +78,11 @@ struct SmemPull2D {
   const StepParams& P;
   const store* box;
   int oz, ox;
-  __device__ __forceinline__ void operator()(int z, int x, int, int k, real* df) const {
+  template <bool EDGE>
+  __device__ __forceinline__ void get(int z, int x, int, int k, real* df) const {
     using L = Lattice<2>;
-    const int bz = min(max(z, 1), P.n[0] - 2) - oz;
-    const int bx = min(max(x, 1), P.n[1] - 2) - ox;
+    const int bz = (EDGE ? min(max(z, 1), P.n[0] - 2) : z) - oz;
+    const int bx = (EDGE ? min(max(x, 1), P.n[1] - 2) : x) - ox;
     const float is = P.inv_scale[k];
     const store* bk = box + (size_t)k * L::Q * T::BX * T::BZ;
 #pragma unroll
@@ -103,8 +104,10 @@ lb_step_tma2d_kernel(const StepParams P, const __grid_constant__ CUtensorMap tma
   store* box = reinterpret_cast<store*>(base);
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + T::box_pad);
   unsigned char* body = base + T::box_pad + 16;
+  using real = typename Prec<PR>::real;
   const int oz = blockIdx.x * T::TZ - T::HZ;
   const int ox = blockIdx.y * T::TX - 2;
+  const bool bulk = tile_is_bulk<2, T::TZ, T::TX, 1>(P, blockIdx.x, blockIdx.y, 0);
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
@@ -112,6 +115,10 @@ lb_step_tma2d_kernel(const StepParams P, const __grid_constant__ CUtensorMap tma
     tma_load_3d(box, &tmap, bar, oz, ox, 0);
   }
   __syncthreads();
+  // the own node's fields load while the box is in flight
+  FieldPF<real> F;
+  if (bulk) prefetch_own<2, real, false, T::TZ, T::TX, 1>(P, F, blockIdx.x, blockIdx.y, 0);
+  else prefetch_own<2, real, true, T::TZ, T::TX, 1>(P, F, blockIdx.x, blockIdx.y, 0);
   // bounded wait for the box; on timeout flag the error and leave
   bool done = false;
   for (uint32_t spin = 0; spin < (1u << 24) && !(done = mbar_try_wait(bar, 0)); ++spin) {
@@ -121,7 +128,111 @@ lb_step_tma2d_kernel(const StepParams P, const __grid_constant__ CUtensorMap tma
     return;
   }
   SmemPull2D<CL, PR> pull{P, box, oz, ox};
-  step_body<2, CL, PR, T::TZ, T::TX, 1>(P, body, pull);
+  if (bulk) step_body<2, CL, PR, T::TZ, T::TX, 1, false>(P, body, pull, F, blockIdx.x, blockIdx.y, 0);
+  else step_body<2, CL, PR, T::TZ, T::TX, 1, true>(P, body, pull, F, blockIdx.x, blockIdx.y, 0);
+}
+
+// Persistent form for the LEC closure: one CTA per SM walks the tiles
+// (t = blockIdx.x, + gridDim.x, ...) with two boxes in shared memory, so
+// the TMA load of the next tile streams in while the current one is
+// computed and the SM always has bytes in flight.
+template <int CL, int PR> struct PersistTile2D;
+template <> struct PersistTile2D<CL_LEC, PR_F32> { static constexpr int TZ = 64, TX = 8; };
+template <> struct PersistTile2D<CL_LEC, PR_F16S> { static constexpr int TZ = 64, TX = 16; };
+template <> struct PersistTile2D<CL_LEC, PR_F64> { static constexpr int TZ = 32, TX = 8; };
+template <> struct PersistTile2D<CL_WARMC, PR_F32> { static constexpr int TZ = 0, TX = 0; };
+template <> struct PersistTile2D<CL_WARMC, PR_F16S> { static constexpr int TZ = 0, TX = 0; };
+template <> struct PersistTile2D<CL_WARMC, PR_F64> { static constexpr int TZ = 0, TX = 0; };
+
+template <int CL, int PR>
+struct PersistCfg2D {
+  using M = Model<2, CL>;
+  using store = typename Prec<PR>::store;
+  static constexpr int TZ = PersistTile2D<CL, PR>::TZ, TX = PersistTile2D<CL, PR>::TX;
+  static constexpr bool enabled = TZ > 0;
+  static constexpr int HZ = 16 / (int)sizeof(store);
+  static constexpr int BZ = TZ + 2 * HZ, BX = TX + 4, BK = M::K * M::Q;
+  static constexpr size_t box_bytes = (size_t)BZ * BX * BK * sizeof(store);
+  static constexpr size_t box_pad = (box_bytes + 127) / 128 * 128;
+  using Body = StepCfg<2, CL, PR, (TZ > 0 ? TZ : 1), (TX > 0 ? TX : 1), 1>;
+  static constexpr size_t smem_bytes = 128 + 2 * box_pad + 32 + Body::smem_bytes;
+};
+
+template <int CL, int PR>
+struct SmemPullBox2D {
+  using T = PersistCfg2D<CL, PR>;
+  using real = typename Prec<PR>::real;
+  using store = typename Prec<PR>::store;
+  const StepParams& P;
+  const store* box;
+  int oz, ox;
+  template <bool EDGE>
+  __device__ __forceinline__ void get(int z, int x, int, int k, real* df) const {
+    using L = Lattice<2>;
+    const int bz = (EDGE ? min(max(z, 1), P.n[0] - 2) : z) - oz;
+    const int bx = (EDGE ? min(max(x, 1), P.n[1] - 2) : x) - ox;
+    const float is = P.inv_scale[k];
+    const store* bk = box + (size_t)k * L::Q * T::BX * T::BZ;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const store v = bk[(i * T::BX + (bx - L::c(i, 1))) * T::BZ + (bz - L::c(i, 0))];
+      if constexpr (PR == PR_F16S) df[i] = __half2float(v) * is;
+      else df[i] = v;
+    }
+  }
+};
+
+template <int CL, int PR>
+__global__ void __launch_bounds__(PersistCfg2D<CL, PR>::TZ* PersistCfg2D<CL, PR>::TX, 1)
+lb_step_persist2d_kernel(const StepParams P, const __grid_constant__ CUtensorMap tmap, int ntz, int ntiles) {
+  using T = PersistCfg2D<CL, PR>;
+  using store = typename Prec<PR>::store;
+  using real = typename Prec<PR>::real;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  auto box = [&](int b) { return reinterpret_cast<store*>(base + (size_t)b * T::box_pad); };
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * T::box_pad);
+  unsigned char* body = base + 2 * T::box_pad + 32;
+  const int G = gridDim.x;
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+    mbar_arrive_expect_tx(&bar[0], (uint32_t)T::box_bytes);
+    tma_load_3d(box(0), &tmap, &bar[0], (t % ntz) * T::TZ - T::HZ, (t / ntz) * T::TX - 2, 0);
+  }
+  __syncthreads();
+  for (int j = 0; t < ntiles; ++j, t += G) {
+    const int b = j & 1;
+    const int tz = t % ntz, tx = t / ntz;
+    const int tn = t + G;
+    if (threadIdx.x == 0 && tn < ntiles) {
+      // the other box was released by the barrier that ended tile j - 1; order
+      // those generic-proxy reads before the async-proxy writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(&bar[b ^ 1], (uint32_t)T::box_bytes);
+      tma_load_3d(box(b ^ 1), &tmap, &bar[b ^ 1], (tn % ntz) * T::TZ - T::HZ, (tn / ntz) * T::TX - 2, 0);
+    }
+    const bool bulk = tile_is_bulk<2, T::TZ, T::TX, 1>(P, tz, tx, 0);
+    FieldPF<real> F;
+    if (bulk) prefetch_own<2, real, false, T::TZ, T::TX, 1>(P, F, tz, tx, 0);
+    else prefetch_own<2, real, true, T::TZ, T::TX, 1>(P, F, tz, tx, 0);
+    // bounded wait for this tile's box; on timeout flag the error and leave
+    bool done = false;
+    const uint32_t parity = (uint32_t)((j >> 1) & 1);
+    for (uint32_t spin = 0; spin < (1u << 24) && !(done = mbar_try_wait(&bar[b], parity)); ++spin) {
+    }
+    if (!__syncthreads_and(done)) {
+      if (threadIdx.x == 0 && P.err) atomicOr(P.err, 1);
+      return;
+    }
+    SmemPullBox2D<CL, PR> pull{P, box(b), tz * T::TZ - T::HZ, tx * T::TX - 2};
+    if (bulk) step_body<2, CL, PR, T::TZ, T::TX, 1, false>(P, body, pull, F, tz, tx, 0);
+    else step_body<2, CL, PR, T::TZ, T::TX, 1, true>(P, body, pull, F, tz, tx, 0);
+    __syncthreads();  // box[b] and the records are free for the next tiles
+  }
 }
 
 }  // namespace lbp

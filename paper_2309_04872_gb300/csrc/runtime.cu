@@ -55,6 +55,8 @@ struct lbpwfa_s {
   size_t device_bytes = 0;
   std::string err;
   bool use_tma = false;
+  bool use_persist = false;
+  int num_sms = 0;
   alignas(64) CUtensorMap maps[2];
   int* err_d = nullptr;  // device error word written by bounded waits
 };
@@ -130,7 +132,7 @@ int validate(const lbpwfa_params* p) {
   if (p->dim >= 2 && !(p->sigma_r > 0.0)) return LBPWFA_ERR_INVALID;
   if (p->precision < LBPWFA_FP64 || p->precision > LBPWFA_FP16S) return LBPWFA_ERR_INVALID;
   if (p->boundary != LBPWFA_OPEN && p->boundary != LBPWFA_PERIODIC) return LBPWFA_ERR_INVALID;
-  if (p->kernel_variant != 0 && p->kernel_variant != 1) return LBPWFA_ERR_INVALID;
+  if (p->kernel_variant < 0 || p->kernel_variant > 3) return LBPWFA_ERR_INVALID;
   long long cells = 1;
   for (int a = 0; a < p->dim; ++a) cells *= p->n[a];
   if (cells > (1LL << 34)) return LBPWFA_ERR_INVALID;
@@ -250,7 +252,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // Tensor map of one population buffer viewed as [K*Q planes][nx rows][nzp]:
 // the step's box is (z, x, planes) = ks.tma_box.
-bool make_pop_map(lbpwfa_s* h, void* base, CUtensorMap* map) {
+bool make_pop_map(lbpwfa_s* h, void* base, CUtensorMap* map, const int* boxdim) {
   auto enc = encode_fn();
   if (!enc) return false;
   const cuuint64_t es = (cuuint64_t)h->ks.tma_elem_bytes;
@@ -258,7 +260,7 @@ bool make_pop_map(lbpwfa_s* h, void* base, CUtensorMap* map) {
                                : (es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
   cuuint64_t dims[3] = {(cuuint64_t)h->nzp, (cuuint64_t)h->n[1], (cuuint64_t)h->K * h->Q};
   cuuint64_t strides[2] = {(cuuint64_t)h->nzp * es, (cuuint64_t)h->plane * es};
-  cuuint32_t box[3] = {(cuuint32_t)h->ks.tma_box[0], (cuuint32_t)h->ks.tma_box[1], (cuuint32_t)h->ks.tma_box[2]};
+  cuuint32_t box[3] = {(cuuint32_t)boxdim[0], (cuuint32_t)boxdim[1], (cuuint32_t)boxdim[2]};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -404,10 +406,27 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err_d, 0, sizeof(int), h->stream);
     if (e != cudaSuccess) { int rr = fail_cuda(h, e, "error word"); lbpwfa_destroy(h); return rr; }
   }
-  h->use_tma = p->kernel_variant == 0 && h->ks.has_tma && dim == 2 && p->boundary == LBPWFA_OPEN;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const bool tma_ok = dim == 2 && p->boundary == LBPWFA_OPEN;
+  h->use_persist = p->kernel_variant == 3 && tma_ok && h->ks.has_persist && h->num_sms > 0;
+  if (h->use_persist) {
+    cudaError_t e = h->ks.prepare_persist();
+    bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0], h->ks.per_box) &&
+              make_pop_map(h, h->f[1].p, &h->maps[1], h->ks.per_box);
+    if (!ok) {
+      cudaGetLastError();
+      h->use_persist = false;
+    }
+  }
+  h->use_tma = !h->use_persist && (p->kernel_variant == 0 || p->kernel_variant == 2) && tma_ok && h->ks.has_tma;
   if (h->use_tma) {
     cudaError_t e = h->ks.prepare_tma();
-    bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0]) && make_pop_map(h, h->f[1].p, &h->maps[1]);
+    bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0], h->ks.tma_box) &&
+              make_pop_map(h, h->f[1].p, &h->maps[1], h->ks.tma_box);
     if (!ok) {
       cudaGetLastError();
       h->use_tma = false;  // the plain kernel computes the same step
@@ -447,9 +466,13 @@ int lbpwfa_step(lbpwfa_t h, int64_t nsteps) {
   const dim3 grid = h->use_tma ? dim3((unsigned)((h->n[0] + h->ks.tma_tz - 1) / h->ks.tma_tz),
                                       (unsigned)((h->n[1] + h->ks.tma_tx - 1) / h->ks.tma_tx), 1)
                                : step_grid(h);
+  const int ntz = (h->n[0] + h->ks.per_tz - 1) / (h->ks.per_tz > 0 ? h->ks.per_tz : 1);
+  const int ntiles = ntz * ((h->n[1] + h->ks.per_tx - 1) / (h->ks.per_tx > 0 ? h->ks.per_tx : 1));
+  const int pgrid = ntiles < h->num_sms ? ntiles : h->num_sms;
   for (int64_t s = 0; s < nsteps; ++s) {
     StepParams P = step_params(h);
-    if (h->use_tma) h->ks.step_tma(P, &h->maps[h->cur], grid, h->stream);
+    if (h->use_persist) h->ks.step_persist(P, &h->maps[h->cur], pgrid, ntz, ntiles, h->stream);
+    else if (h->use_tma) h->ks.step_tma(P, &h->maps[h->cur], grid, h->stream);
     else h->ks.step(P, grid, h->stream);
     CK_LAUNCH(h, "lb_step_kernel launch");
     h->cur = 1 - h->cur;
@@ -624,7 +647,7 @@ int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info) {
   const int ne = dim == 1 ? 1 : (dim == 2 ? 2 : 3);
   const int nbf = dim == 1 ? 0 : (dim == 2 ? 1 : 3);
   info->bytes_per_update = 2.0 * h->K * h->Q * h->store_sz + 2.0 * (ne + nbf + h->NPREV) * h->real_sz;
-  info->kernel_variant = h->use_tma ? 0 : 1;
+  info->kernel_variant = h->use_persist ? 3 : (h->use_tma ? 2 : 1);
   return LBPWFA_OK;
 }
 

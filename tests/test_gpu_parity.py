@@ -294,24 +294,28 @@ def test_zero_steps_and_edge_sizes():
 
 
 # ---------------------------------------------------------------------------
-# The TMA-staged 2D kernel and the plain kernel compute the same step
+# The 2D kernels (persistent TMA, TMA box per CTA, plain) compute the same step
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("closure", ["lec", "warmc"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
-def test_tma_and_plain_kernels_agree_bitwise(closure, prec):
-    cfg = _cfg(2, closure, "open", n=(131, 37))
+@pytest.mark.parametrize("n", [(131, 37), (300, 70)])
+def test_2d_kernel_variants_agree_bitwise(closure, prec, n):
+    cfg = _cfg(2, closure, "open", n=n)
     orc = O.Oracle(cfg)
     f, E, B = _random_state(orc, 77, cfg["mu"])
+    staged = not (closure == "warmc" and prec == "fp64")
+    expect = {0: 2 if staged else 1, 1: 1, 2: 2 if staged else 1,
+              3: 3 if closure == "lec" else 1}
     out = []
-    for variant in (0, 1):
+    for variant in (0, 1, 2, 3):
         with lb.Run(cfg, prec, variant=variant) as run:
-            expect_tma = variant == 0 and not (closure == "warmc" and prec == "fp64")
-            assert run.info().kernel_variant == (0 if expect_tma else 1)
+            assert run.info().kernel_variant == expect[variant]
             run.set_state(f, E, B)
             run.step(17)
             out.append((run.advected(), run.fields()))
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1])
+    for v in (1, 2, 3):
+        assert np.array_equal(out[0][0], out[v][0])
+        assert np.array_equal(out[0][1], out[v][1])
 
 
 @pytest.mark.parametrize("prec,tol,floor", [("fp64", 1e-12, 1e-13), ("fp32", 1e-4, 1e-7)])
