@@ -180,16 +180,19 @@ def _time_steps(run, stream, steps, warmup, flush):
 
 
 def _traffic_for(kernel_key):
-    """Per-launch DRAM bytes of the step kernel from a committed ncu capture,
-    valid only while the kernel sources are unchanged."""
+    """Per-launch DRAM bytes of the step kernel from a committed ncu summary
+    (a `traffic <kernel:workload> <bytes> sources_sha256=<digest>` line under
+    profiles/), valid only while the kernel sources are unchanged."""
+    import glob
+    import re
     try:
         from paper_2309_04872_gb300 import build as B
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            tab = json.load(f)
-        ent = tab.get(kernel_key)
-        if ent and ent.get("sources_sha256") == B._sources_digest():
-            return ent.get("dram_bytes_per_launch")
-    except (OSError, ValueError):
+        digest = B._sources_digest()
+        for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+            for m in re.finditer(r"traffic (\S+) (\d+) sources_sha256=([0-9a-f]+)", open(fn).read()):
+                if m.group(1) == kernel_key and m.group(3) == digest:
+                    return int(m.group(2))
+    except OSError:
         pass
     return None
 
