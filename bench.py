@@ -24,6 +24,8 @@ from __future__ import annotations
 import argparse
 import json
 import os
+
+import numpy as np
 import statistics
 import subprocess
 import sys
@@ -187,7 +189,7 @@ def _traffic_for(kernel_key):
     import re
     try:
         from paper_2309_04872_gb300 import build as B
-        digest = B._sources_digest()
+        digest = B.step_kernel_digest()
         for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
             for m in re.finditer(r"traffic (\S+) (\d+) sources_sha256=([0-9a-f]+)", open(fn).read()):
                 if m.group(1) == kernel_key and m.group(3) == digest:
@@ -238,10 +240,12 @@ def run_ours(a):
     peaks, peak_kind = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
 
-    def measure(prec, steps, warmup, mu=None, variant=None):
+    def measure(prec, steps, warmup, mu=None, variant=None, closure=None):
         c = dict(cfg)
         if mu is not None:
             c["mu"] = mu
+        if closure is not None:
+            c["closure"] = closure
         v = a.variant if variant is None else variant
         with lb.Run(c, prec, stream=stream.cuda_stream, variant=v) as run:
             info = run.info()
@@ -304,7 +308,16 @@ def run_ours(a):
                     modes[key] = {"mlups": round(r["mlups"], 2), "ms_per_step": round(r["ms"], 5),
                                   "achieved_gbs": round(r["gbs"], 1), "frac_of_measured_hbm": round(r["frac"], 4),
                                   "bytes_per_update": r["bytes_per_update"], "steps": steps, "kernel": r["kernel"]}
+        for prec in ("fp64", "fp32", "fp16s"):
+            steps = 200 if prec == "fp64" else 600
+            r = measure(prec, steps, 5, mu=1e-2, variant=0, closure="warmc")
+            modes[f"warmc_{prec}_mu0.01"] = {"mlups": round(r["mlups"], 2), "ms_per_step": round(r["ms"], 5),
+                                             "achieved_gbs": round(r["gbs"], 1),
+                                             "frac_of_measured_hbm": round(r["frac"], 4),
+                                             "bytes_per_update": r["bytes_per_update"], "steps": steps,
+                                             "kernel": r["kernel"]}
         out["modes"] = modes
+        out["precision_vs_fp64"] = _precision_table(cfg, stream)
 
     if rank == 0 and not a.no_configs and a.workload == "2d_lec":
         out["configs_measured"] = _configs(stream, flush, hbm)
@@ -322,6 +335,28 @@ def run_ours(a):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def _precision_table(cfg, stream, nsteps=2000):
+    """Reduced-precision storage against the FP64 GPU path on the same
+    workload after nsteps: relative L2 error of E_z and of n - 1."""
+    from paper_2309_04872_gb300 import lbpwfa as lb
+    res = {}
+    for closure in ("lec", "warmc"):
+        c = dict(cfg, closure=closure)
+        out = {}
+        for prec in ("fp64", "fp32", "fp16s"):
+            with lb.Run(c, prec, stream=stream.cuda_stream) as run:
+                run.step(nsteps)
+                out[prec] = (run.moments(lb.M_N)[0] - 1.0, run.fields(lb.F_EZ)[0])
+        ref_n, ref_e = out["fp64"]
+        for prec in ("fp32", "fp16s"):
+            n1, ez = out[prec]
+            res[f"{closure}_{prec}"] = {
+                "rel_err_n_minus_1": float(np.linalg.norm(n1 - ref_n) / np.linalg.norm(ref_n)),
+                "rel_err_Ez": float(np.linalg.norm(ez - ref_e) / np.linalg.norm(ref_e)),
+                "steps": nsteps}
+    return res
 
 
 def _configs(stream, flush, hbm):
@@ -343,6 +378,31 @@ def _configs(stream, flush, hbm):
         res["1d_lec_fp64_2048"] = {"steps": 4000, "ms_total": round(ms, 3), "steps_per_s": round(4000 / ms * 1e3, 1),
                                    "mlups": round(2048 * 4000 / ms / 1e3, 2),
                                    "note": "state is L2-resident and launch-bound; no flush"}
+    # the batched sweep: 64 uneven 2D runs, both closures, one launch per step
+    from tests import inputs
+    draws = inputs.batch_draws(64, seed=2309)
+    cfgs = [dict(dim=2, n=(d["nz"], d["nx"]), dx=0.05, courant=0.1, tau=0.53, closure=d["closure"], dv=3,
+                 mu=d["mu"], alpha=d["alpha"], sigma_z=d["sigma_z"], sigma_r=0.5, z0=4.0 * d["sigma_z"],
+                 boundary="open", init_fields=True) for d in draws]
+    with lb.Batch(cfgs, "fp32", stream=stream.cuda_stream, tune=True) as b:
+        info = b.info()
+        b.step(32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(96)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 96
+        gbs = info.bytes_per_step / (ms * 1e-3) / 1e9
+        nlec = sum(1 for d in draws if d["closure"] == "lec")
+        res["batch_64x2d_fp32"] = {
+            "mlups": round(info.ncell / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
+            "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
+            "nodes": int(info.ncell), "runs": 64, "lec_runs": nlec, "warmc_runs": 64 - nlec,
+            "tile": list(info.tile), "tuned_ms": [round(v, 4) for v in info.tuned_ms if v > 0],
+            "graph_steps": info.graph_steps, "steps": 96, "kernel": "lb_step_batch_kernel",
+            "l2": "state larger than L2 (no flush)"}
     for prec in ("fp32", "fp64"):
         try:
             with lb.Run(CONFIG_3D, prec, stream=stream.cuda_stream) as run:

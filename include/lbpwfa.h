@@ -210,6 +210,52 @@ int lbpwfa_set_stream(lbpwfa_t h, void* stream);
  * wait gave up (the step is then incomplete). */
 int lbpwfa_synchronize(lbpwfa_t h);
 
+/* ------------------------------------------------------------------------
+ * Batched sweeps (uneven 2D grids, mixed closures, one launch per step).
+ * The paper runs each parameter point as a separate simulation (Sec. 6:
+ * temperature and driver scans, Figs. 3 and 6); a batch advances many such
+ * runs together: every step is one persistent kernel over a work list of
+ * (run, tile) items, and runs of lbpwfa_batch_step are replayed from a
+ * captured CUDA graph.  A device-side step counter supplies each step's time
+ * and buffer parity, so the graph is valid from any step.
+ * ------------------------------------------------------------------------ */
+typedef struct lbpwfa_batch_s* lbpwfa_batch_t;
+
+typedef struct {
+  int nruns;
+  int64_t ncell;           /* nodes over all runs */
+  int64_t nitems;          /* (run, tile) work items per step */
+  int tile[2];             /* tile (z, x) chosen by the autotuner */
+  int grid;                /* CTAs of the persistent launch */
+  int graph_steps;         /* steps per captured graph */
+  int64_t step;
+  size_t device_bytes;
+  double bytes_per_step;   /* algorithmic HBM bytes of one batch step */
+  double tuned_ms[4];      /* autotuner timing per candidate tile (-1 unused) */
+} lbpwfa_batch_info_t;
+
+/* Create nruns >= 1 runs from p[0..nruns-1], each validated as by
+ * lbpwfa_create.  Every run must be 2D with the same precision; closures,
+ * grids and driver parameters may differ.  flags bit 0: skip the autotuner
+ * (use the first candidate tile).  The autotuner times each candidate tile
+ * over a few steps and restores the rest state; when the environment
+ * variable LBPWFA_TUNE_CACHE names a JSON file, choices are read from and
+ * written to it.  p[i].stream of run 0 is the batch's stream.
+ * Errors: INVALID, OOM, CUDA. */
+int lbpwfa_batch_create(const lbpwfa_params* p, int nruns, int flags, lbpwfa_batch_t* out);
+
+/* Advance every run by nsteps >= 0 steps. */
+int lbpwfa_batch_step(lbpwfa_batch_t b, int64_t nsteps);
+
+/* Handle of run i for lbpwfa_moments, lbpwfa_fields, lbpwfa_advected,
+ * lbpwfa_get_state, lbpwfa_set_state, lbpwfa_reduce, lbpwfa_info and
+ * lbpwfa_save.  It stays owned by the batch; lbpwfa_step on it returns
+ * LBPWFA_ERR_STATE, and lbpwfa_destroy on it does nothing. */
+int lbpwfa_batch_member(lbpwfa_batch_t b, int i, lbpwfa_t* run);
+
+int lbpwfa_batch_info(lbpwfa_batch_t b, lbpwfa_batch_info_t* info);
+void lbpwfa_batch_destroy(lbpwfa_batch_t b);
+
 void lbpwfa_destroy(lbpwfa_t h);
 const char* lbpwfa_status_string(int status);
 /* Text of the last CUDA error seen by this handle ("" if none). */

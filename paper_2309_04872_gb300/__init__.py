@@ -1,4 +1,4 @@
 """GB300-native lattice Boltzmann warm-plasma wakefield solver
 (arXiv 2309.04872): CUDA library liblbpwfa.so and its thin binding."""
-from .lbpwfa import (FP16S, FP32, FP64, LEC, OPEN, PERIODIC, WARMC, LbpwfaError, Run,  # noqa: F401
+from .lbpwfa import (FP16S, FP32, FP64, LEC, OPEN, PERIODIC, WARMC, Batch, LbpwfaError, Run,  # noqa: F401
                      library_path, load_library, make_params)

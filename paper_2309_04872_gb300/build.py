@@ -19,7 +19,7 @@ LIB = os.path.join(OUT, "liblbpwfa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo", "-Xcompiler", "-fPIC",
               "-diag-suppress", "177", "-I", INCLUDE]
-UNITS = ["lb_inst_f64.cu", "lb_inst_f32.cu", "lb_inst_f16s.cu", "runtime.cu"]
+UNITS = ["lb_inst_f64.cu", "lb_inst_f32.cu", "lb_inst_f16s.cu", "lb_batch.cu", "runtime.cu"]
 
 
 def _nvcc() -> str:
@@ -35,6 +35,21 @@ def _sources_digest() -> str:
                 with open(os.path.join(d, name), "rb") as f:
                     h.update(name.encode())
                     h.update(f.read())
+    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    return h.hexdigest()
+
+
+# sources that define the single-run step kernels (their ncu figures stay
+# valid while these and the compile flags are unchanged)
+STEP_KERNEL_SOURCES = ["lb_common.cuh", "lb_step.cuh", "lb_step_tma.cuh", "lb_inst.cuh", "lb_dispatch.h"]
+
+
+def step_kernel_digest() -> str:
+    h = hashlib.sha256()
+    for name in STEP_KERNEL_SOURCES:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
     h.update(" ".join(ARCH + NVCC_FLAGS).encode())
     return h.hexdigest()
 

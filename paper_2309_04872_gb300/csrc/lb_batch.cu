@@ -1,0 +1,52 @@
+// Instances of the batched step kernel: FP32 and FP64 storage, three
+// candidate tiles for the autotuner.
+#include "lb_batch.cuh"
+#include "lb_batch_dispatch.h"
+
+namespace lbp {
+
+namespace {
+template <int PR, int TZ, int TX>
+struct BatchImpl {
+  using Cfg = BatchCfg<PR, TZ, TX>;
+  static cudaError_t prepare() {
+    return cudaFuncSetAttribute(lb_step_batch_kernel<PR, TZ, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg::smem_bytes);
+  }
+  static void launch(const BatchArgs& A, int grid, cudaStream_t s) {
+    lb_step_batch_kernel<PR, TZ, TX><<<grid, TZ * TX, Cfg::smem_bytes, s>>>(A);
+  }
+  static int occupancy() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lb_step_batch_kernel<PR, TZ, TX>, TZ * TX, Cfg::smem_bytes);
+    return n;
+  }
+};
+
+template <int PR>
+void fill(BatchKernelSet* ks) {
+  ks->ncand = 3;
+  ks->tz[0] = 32; ks->tx[0] = 8;
+  ks->tz[1] = 64; ks->tx[1] = 4;
+  ks->tz[2] = 16; ks->tx[2] = 16;
+  ks->prepare[0] = &BatchImpl<PR, 32, 8>::prepare;
+  ks->prepare[1] = &BatchImpl<PR, 64, 4>::prepare;
+  ks->prepare[2] = &BatchImpl<PR, 16, 16>::prepare;
+  ks->launch[0] = &BatchImpl<PR, 32, 8>::launch;
+  ks->launch[1] = &BatchImpl<PR, 64, 4>::launch;
+  ks->launch[2] = &BatchImpl<PR, 16, 16>::launch;
+  ks->occupancy[0] = &BatchImpl<PR, 32, 8>::occupancy;
+  ks->occupancy[1] = &BatchImpl<PR, 64, 4>::occupancy;
+  ks->occupancy[2] = &BatchImpl<PR, 16, 16>::occupancy;
+}
+}  // namespace
+
+bool batch_kernels(int precision, BatchKernelSet* ks) {
+  if (precision == PR_F32) { fill<PR_F32>(ks); return true; }
+  if (precision == PR_F64) { fill<PR_F64>(ks); return true; }
+  return false;
+}
+
+void batch_advance(long long* step, cudaStream_t s) { batch_advance_kernel<<<1, 32, 0, s>>>(step); }
+
+}  // namespace lbp

@@ -17,6 +17,8 @@
 
 #include "../../include/lbpwfa.h"
 #include "lb_aux.cuh"
+#include "lb_batch_dispatch.h"
+#include "lb_batch_types.cuh"
 #include "lb_dispatch.h"
 
 using namespace lbp;
@@ -56,6 +58,7 @@ struct lbpwfa_s {
   std::string err;
   bool use_tma = false;
   bool use_persist = false;
+  bool in_batch = false;  // owned by a batch: stepped only through lbpwfa_batch_step
   int num_sms = 0;
   alignas(64) CUtensorMap maps[2];
   int* err_d = nullptr;  // device error word written by bounded waits
@@ -169,6 +172,13 @@ AuxParams aux_params(const lbpwfa_s* h) {
   return A;
 }
 
+// Driver centre z0 + step dt, rounded like the batched kernel computes it
+// (product, then sum; no fused multiply-add).
+double zeta0_of(double z0, long long step, double dt) {
+  volatile double t = (double)step * dt;
+  return z0 + t;
+}
+
 template <typename real>
 void fill_consts(const lbpwfa_s* h, StepConst<real>& c) {
   const double dx = h->prm.dx, dt = h->dt;
@@ -181,7 +191,7 @@ void fill_consts(const lbpwfa_s* h, StepConst<real>& c) {
   c.inv_tau = (real)(1.0 / h->prm.tau);
   c.mu = (real)h->prm.mu;
   c.cH = (real)((1.0 + 0.5 * h->prm.dv) * h->prm.mu);
-  c.zeta0 = (real)(h->prm.z0 + h->step * dt);
+  c.zeta0 = (real)zeta0_of(h->prm.z0, h->step, dt);
   c.alpha = (real)h->prm.alpha;
   c.inv2sz2 = (real)(h->prm.sigma_z > 0 ? 1.0 / (2.0 * h->prm.sigma_z * h->prm.sigma_z) : 0.0);
   c.inv2sr2 = (real)(h->prm.sigma_r > 0 ? 1.0 / (2.0 * h->prm.sigma_r * h->prm.sigma_r) : 0.0);
@@ -278,6 +288,28 @@ int check_err_word(lbpwfa_s* h) {
   return LBPWFA_OK;
 }
 
+// Rest state n = 1, u = 0 (all stored deviations zero: every storage format
+// encodes 0 as zero bits), the initial driver field, step 0.
+int init_rest_state(lbpwfa_s* h) {
+  const size_t pop_bytes = h->f[0].bytes, fld_bytes = h->E[0].bytes;
+  for (int j = 0; j < 2; ++j) {
+    CK(h, cudaMemsetAsync(h->f[j].p, 0, pop_bytes, h->stream));
+    CK(h, cudaMemsetAsync(h->E[j].p, 0, fld_bytes, h->stream));
+    CK(h, cudaMemsetAsync(h->B[j].p, 0, fld_bytes, h->stream));
+  }
+  if (h->prev.p) CK(h, cudaMemsetAsync(h->prev.p, 0, h->prev.bytes, h->stream));
+  if (h->prm.init_fields && h->prm.dim >= 2) {
+    AuxParams A = aux_params(h);
+    A.t = 0.0;
+    h->ks.init_fields(A, h->E[0].p, h->B[0].p, h->stream);
+    CK_LAUNCH(h, "init_fields");
+  }
+  h->cur = 0;
+  h->step = 0;
+  h->have_prev = 0;
+  return LBPWFA_OK;
+}
+
 uint32_t crc32_update(uint32_t crc, const void* data, size_t len) {
   static uint32_t table[256];
   static bool init = false;
@@ -315,7 +347,7 @@ const char* lbpwfa_status_string(int s) {
 
 const char* lbpwfa_last_error(lbpwfa_t h) { return h ? h->err.c_str() : ""; }
 
-void lbpwfa_destroy(lbpwfa_t h) {
+static void destroy_run(lbpwfa_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (int j = 0; j < 2; ++j) { release(h->f[j]); release(h->E[j]); release(h->B[j]); }
@@ -327,6 +359,11 @@ void lbpwfa_destroy(lbpwfa_t h) {
   if (h->profile_d) cudaFree(h->profile_d);
   if (h->owns_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+void lbpwfa_destroy(lbpwfa_t h) {
+  if (!h || h->in_batch) return;
+  destroy_run(h);
 }
 
 int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
@@ -439,21 +476,8 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
                         cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) { int rr = fail_cuda(h, e, "profile upload"); lbpwfa_destroy(h); return rr; }
   }
-  // rest state: all deviations zero (every storage format encodes 0 as zero bits)
-  cudaError_t e = cudaSuccess;
-  for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
-    e = cudaMemsetAsync(h->f[j].p, 0, pop_bytes, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->E[j].p, 0, fld_bytes, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->B[j].p, 0, fld_bytes, h->stream);
-  }
-  if (e == cudaSuccess && h->prev.p) e = cudaMemsetAsync(h->prev.p, 0, h->prev.bytes, h->stream);
-  if (e != cudaSuccess) { int rr = fail_cuda(h, e, "cudaMemsetAsync"); lbpwfa_destroy(h); return rr; }
-  if (p->init_fields && dim >= 2) {
-    AuxParams A = aux_params(h);
-    h->ks.init_fields(A, h->E[0].p, h->B[0].p, h->stream);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) { int rr = fail_cuda(h, e, "init_fields"); lbpwfa_destroy(h); return rr; }
-  }
+  r = init_rest_state(h);
+  if (r != LBPWFA_OK) { lbpwfa_destroy(h); return r; }
   h->cur = 0;
   h->step = 0;
   h->have_prev = 0;
@@ -463,6 +487,10 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
 
 int lbpwfa_step(lbpwfa_t h, int64_t nsteps) {
   if (!h || nsteps < 0) return LBPWFA_ERR_INVALID;
+  if (h->in_batch) {
+    h->err = "lbpwfa_step: this run belongs to a batch; use lbpwfa_batch_step";
+    return LBPWFA_ERR_STATE;
+  }
   const dim3 grid = h->use_tma ? dim3((unsigned)((h->n[0] + h->ks.tma_tz - 1) / h->ks.tma_tz),
                                       (unsigned)((h->n[1] + h->ks.tma_tx - 1) / h->ks.tma_tx), 1)
                                : step_grid(h);
@@ -826,3 +854,335 @@ extern "C" int lbpwfa_reduce_noalloc(lbpwfa_t h, double* out, int out_is_device)
   CK(h, cudaStreamSynchronize(h->stream));
   return out[2] > 0 ? LBPWFA_ERR_NONFINITE : LBPWFA_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched sweeps.
+// ---------------------------------------------------------------------------
+struct lbpwfa_batch_s {
+  std::vector<lbpwfa_s*> runs;
+  BatchKernelSet bk{};
+  int cand = 0;
+  int grid = 0;
+  int precision = 0;
+  std::vector<BatchRun> runs_h;
+  BatchRun* runs_d = nullptr;
+  int2* items_d = nullptr;
+  long long* step_d = nullptr;
+  long long nitems = 0;
+  long long step = 0;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_steps = 32;
+  double tuned_ms[4] = {-1, -1, -1, -1};
+  size_t device_bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+int batch_fail(lbpwfa_batch_s* b, cudaError_t e, const char* what) {
+  b->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return LBPWFA_ERR_CUDA;
+}
+#define BCK(b, call)                                            \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return batch_fail((b), e_, #call);   \
+  } while (0)
+
+void batch_free_lists(lbpwfa_batch_s* b) {
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->graph_exec = nullptr;
+  b->graph = nullptr;
+  if (b->runs_d) cudaFree(b->runs_d);
+  if (b->items_d) cudaFree(b->items_d);
+  b->runs_d = nullptr;
+  b->items_d = nullptr;
+}
+
+// Launch records and the (run, tile) work list for candidate tile c.
+int batch_build(lbpwfa_batch_s* b, int c) {
+  batch_free_lists(b);
+  const int tz = b->bk.tz[c], tx = b->bk.tx[c];
+  b->runs_h.assign(b->runs.size(), BatchRun{});
+  std::vector<int2> items;
+  for (size_t i = 0; i < b->runs.size(); ++i) {
+    lbpwfa_s* h = b->runs[i];
+    BatchRun& R = b->runs_h[i];
+    const int cur = h->cur;
+    for (int par = 0; par < 2; ++par) {
+      h->cur = par;
+      R.P[par] = step_params(h);
+    }
+    h->cur = cur;
+    R.z0 = h->prm.z0;
+    R.dt = h->dt;
+    R.prev_from = h->have_prev ? -1 : b->step;
+    R.closure = h->prm.closure;
+    R.ntz = (h->n[0] + tz - 1) / tz;
+    R.ntx = (h->n[1] + tx - 1) / tx;
+    for (int t = 0; t < R.ntz * R.ntx; ++t) items.push_back(make_int2((int)i, t));
+  }
+  b->nitems = (long long)items.size();
+  BCK(b, cudaMalloc(&b->runs_d, sizeof(BatchRun) * b->runs_h.size()));
+  BCK(b, cudaMalloc(&b->items_d, sizeof(int2) * items.size()));
+  BCK(b, cudaMemcpyAsync(b->runs_d, b->runs_h.data(), sizeof(BatchRun) * b->runs_h.size(),
+                         cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemcpyAsync(b->items_d, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
+                         b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  BCK(b, b->bk.prepare[c]());
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int occ = b->bk.occupancy[c]();
+  long long g = (long long)sms * (occ > 0 ? occ : 1);
+  b->grid = (int)(g < b->nitems ? g : b->nitems);
+  b->cand = c;
+  return LBPWFA_OK;
+}
+
+int batch_launch_one(lbpwfa_batch_s* b) {
+  BatchArgs A{};
+  A.runs = b->runs_d;
+  A.items = b->items_d;
+  A.nitems = (int)b->nitems;
+  A.step = b->step_d;
+  b->bk.launch[b->cand](A, b->grid, b->stream);
+  BCK(b, cudaGetLastError());
+  batch_advance(b->step_d, b->stream);
+  BCK(b, cudaGetLastError());
+  return LBPWFA_OK;
+}
+
+// Restart from the rest state at step 0 (used after tuning).
+int batch_reset(lbpwfa_batch_s* b) {
+  for (lbpwfa_s* h : b->runs) {
+    int r = init_rest_state(h);
+    if (r != LBPWFA_OK) { b->err = h->err; return r; }
+  }
+  BCK(b, cudaMemsetAsync(b->step_d, 0, sizeof(long long), b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  b->step = 0;
+  return LBPWFA_OK;
+}
+
+std::string batch_key(const lbpwfa_batch_s* b) {
+  cudaDeviceProp prop{};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  std::string k = std::string(prop.name) + "|p" + std::to_string(b->precision);
+  for (const lbpwfa_s* h : b->runs)
+    k += "|" + std::to_string(h->prm.closure) + ":" + std::to_string(h->n[0]) + "x" + std::to_string(h->n[1]);
+  char buf[32];
+  std::snprintf(buf, sizeof(buf), "%016zx", std::hash<std::string>{}(k));
+  return buf;
+}
+
+// Tuning cache: one line per entry, `"<key>": <candidate>`, inside a JSON object.
+int cache_lookup(const std::string& key) {
+  const char* path = std::getenv("LBPWFA_TUNE_CACHE");
+  if (!path) return -1;
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return -1;
+  char line[256];
+  int found = -1;
+  while (std::fgets(line, sizeof(line), fp)) {
+    char k[64];
+    int c;
+    if (std::sscanf(line, " \"%63[0-9a-f]\": %d", k, &c) == 2 && key == k) found = c;
+  }
+  std::fclose(fp);
+  return found;
+}
+
+void cache_store(const std::string& key, int c) {
+  const char* path = std::getenv("LBPWFA_TUNE_CACHE");
+  if (!path) return;
+  std::vector<std::string> entries;
+  if (FILE* fp = std::fopen(path, "r")) {
+    char line[256];
+    while (std::fgets(line, sizeof(line), fp)) {
+      char k[64];
+      int v;
+      if (std::sscanf(line, " \"%63[0-9a-f]\": %d", k, &v) == 2 && key != k)
+        entries.push_back(std::string("\"") + k + "\": " + std::to_string(v));
+    }
+    std::fclose(fp);
+  }
+  entries.push_back("\"" + key + "\": " + std::to_string(c));
+  if (FILE* fp = std::fopen(path, "w")) {
+    std::fprintf(fp, "{\n");
+    for (size_t i = 0; i < entries.size(); ++i)
+      std::fprintf(fp, "  %s%s\n", entries[i].c_str(), i + 1 < entries.size() ? "," : "");
+    std::fprintf(fp, "}\n");
+    std::fclose(fp);
+  }
+}
+
+// Time each candidate tile over a few steps of the real batch, keep the
+// fastest, and return to the rest state.
+int batch_autotune(lbpwfa_batch_s* b) {
+  const std::string key = batch_key(b);
+  const int cached = cache_lookup(key);
+  if (cached >= 0 && cached < b->bk.ncand) return batch_build(b, cached);
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0));
+  BCK(b, cudaEventCreate(&e1));
+  int best = 0;
+  double best_ms = 1e30;
+  for (int c = 0; c < b->bk.ncand; ++c) {
+    int r = batch_build(b, c);
+    if (r != LBPWFA_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+    for (int w = 0; w < 2 && r == LBPWFA_OK; ++w) r = batch_launch_one(b);
+    cudaEventRecord(e0, b->stream);
+    for (int w = 0; w < 4 && r == LBPWFA_OK; ++w) r = batch_launch_one(b);
+    cudaEventRecord(e1, b->stream);
+    if (r != LBPWFA_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+    BCK(b, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    b->tuned_ms[c] = ms / 4.0;
+    if (b->tuned_ms[c] < best_ms) { best_ms = b->tuned_ms[c]; best = c; }
+    r = batch_reset(b);
+    if (r != LBPWFA_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cache_store(key, best);
+  return batch_build(b, best);
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbpwfa_batch_destroy(lbpwfa_batch_t b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_free_lists(b);
+  if (b->step_d) cudaFree(b->step_d);
+  for (lbpwfa_s* h : b->runs) destroy_run(h);
+  if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int lbpwfa_batch_create(const lbpwfa_params* p, int nruns, int flags, lbpwfa_batch_t* out) {
+  if (!out || !p || nruns < 1) return LBPWFA_ERR_INVALID;
+  *out = nullptr;
+  for (int i = 0; i < nruns; ++i) {
+    int st = validate(&p[i]);
+    if (st != LBPWFA_OK) return st;
+    if (p[i].dim != 2 || p[i].precision != p[0].precision) return LBPWFA_ERR_INVALID;
+  }
+  lbpwfa_batch_s* b = new lbpwfa_batch_s();
+  b->precision = p[0].precision;
+  if (!batch_kernels(b->precision == LBPWFA_FP64 ? PR_F64 : (b->precision == LBPWFA_FP32 ? PR_F32 : -1), &b->bk)) {
+    delete b;
+    return LBPWFA_ERR_INVALID;  // batched FP16S storage is not built
+  }
+  if (p[0].stream) {
+    b->stream = (cudaStream_t)p[0].stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return LBPWFA_ERR_CUDA; }
+    b->owns_stream = true;
+  }
+  for (int i = 0; i < nruns; ++i) {
+    lbpwfa_params q = p[i];
+    q.stream = b->stream;
+    q.kernel_variant = 1;
+    lbpwfa_t h = nullptr;
+    int st = lbpwfa_create(&q, &h);
+    if (st != LBPWFA_OK) { lbpwfa_batch_destroy(b); return st; }
+    h->in_batch = true;
+    b->runs.push_back(h);
+    b->device_bytes += h->device_bytes;
+  }
+  if (cudaMalloc(&b->step_d, sizeof(long long)) != cudaSuccess) { lbpwfa_batch_destroy(b); return LBPWFA_ERR_OOM; }
+  if (cudaMemsetAsync(b->step_d, 0, sizeof(long long), b->stream) != cudaSuccess) {
+    lbpwfa_batch_destroy(b);
+    return LBPWFA_ERR_CUDA;
+  }
+  int st = (flags & 1) ? batch_build(b, 0) : batch_autotune(b);
+  if (st != LBPWFA_OK) { lbpwfa_batch_destroy(b); return st; }
+  *out = b;
+  return LBPWFA_OK;
+}
+
+int lbpwfa_batch_step(lbpwfa_batch_t b, int64_t nsteps) {
+  if (!b || nsteps < 0) return LBPWFA_ERR_INVALID;
+  if (nsteps == 0) return LBPWFA_OK;
+  // a member whose state was replaced restarts its WARMC backward differences
+  bool dirty = false;
+  for (size_t i = 0; i < b->runs.size(); ++i) {
+    lbpwfa_s* h = b->runs[i];
+    if (h->prm.closure == LBPWFA_WARMC && !h->have_prev && b->runs_h[i].prev_from != b->step) {
+      b->runs_h[i].prev_from = b->step;
+      dirty = true;
+    }
+  }
+  if (dirty)
+    BCK(b, cudaMemcpyAsync(b->runs_d, b->runs_h.data(), sizeof(BatchRun) * b->runs_h.size(),
+                           cudaMemcpyHostToDevice, b->stream));
+  int64_t left = nsteps;
+  if (left >= b->graph_steps && !b->graph_exec) {
+    BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int r = LBPWFA_OK;
+    for (int s = 0; s < b->graph_steps && r == LBPWFA_OK; ++s) r = batch_launch_one(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (r != LBPWFA_OK) return r;
+    if (e != cudaSuccess) return batch_fail(b, e, "cudaStreamEndCapture");
+    b->graph = g;
+    BCK(b, cudaGraphInstantiate(&b->graph_exec, b->graph, 0));
+  }
+  while (b->graph_exec && left >= b->graph_steps) {
+    BCK(b, cudaGraphLaunch(b->graph_exec, b->stream));
+    left -= b->graph_steps;
+  }
+  for (; left > 0; --left) {
+    int r = batch_launch_one(b);
+    if (r != LBPWFA_OK) return r;
+  }
+  b->step += nsteps;
+  for (lbpwfa_s* h : b->runs) {
+    h->step = b->step;
+    h->cur = (int)(b->step & 1);
+    if (h->NPREV) h->have_prev = 1;
+  }
+  return LBPWFA_OK;
+}
+
+int lbpwfa_batch_member(lbpwfa_batch_t b, int i, lbpwfa_t* run) {
+  if (!b || !run || i < 0 || i >= (int)b->runs.size()) return LBPWFA_ERR_INVALID;
+  *run = b->runs[i];
+  return LBPWFA_OK;
+}
+
+int lbpwfa_batch_info(lbpwfa_batch_t b, lbpwfa_batch_info_t* info) {
+  if (!b || !info) return LBPWFA_ERR_INVALID;
+  info->nruns = (int)b->runs.size();
+  info->ncell = 0;
+  info->bytes_per_step = 0.0;
+  for (lbpwfa_s* h : b->runs) {
+    lbpwfa_info_t ri{};
+    lbpwfa_info(h, &ri);
+    info->ncell += ri.ncell;
+    info->bytes_per_step += ri.bytes_per_update * (double)ri.ncell;
+  }
+  info->nitems = b->nitems;
+  info->tile[0] = b->bk.tz[b->cand];
+  info->tile[1] = b->bk.tx[b->cand];
+  info->grid = b->grid;
+  info->graph_steps = b->graph_steps;
+  info->step = b->step;
+  info->device_bytes = b->device_bytes;
+  for (int c = 0; c < 4; ++c) info->tuned_ms[c] = b->tuned_ms[c];
+  return LBPWFA_OK;
+}
+
+}  // extern "C"

@@ -55,12 +55,21 @@ class Info(ctypes.Structure):
                 ("kernel_variant", ctypes.c_int)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("nruns", ctypes.c_int), ("ncell", ctypes.c_int64), ("nitems", ctypes.c_int64),
+                ("tile", ctypes.c_int * 2), ("grid", ctypes.c_int), ("graph_steps", ctypes.c_int),
+                ("step", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("bytes_per_step", ctypes.c_double),
+                ("tuned_ms", ctypes.c_double * 4)]
+
+
 _lib = None
 _DP = ctypes.POINTER(ctypes.c_double)
 EXPORTED = ["lbpwfa_create", "lbpwfa_step", "lbpwfa_moments", "lbpwfa_fields", "lbpwfa_advected",
             "lbpwfa_set_state", "lbpwfa_get_state", "lbpwfa_reduce", "lbpwfa_info", "lbpwfa_save",
             "lbpwfa_load", "lbpwfa_set_stream", "lbpwfa_synchronize", "lbpwfa_destroy",
-            "lbpwfa_status_string", "lbpwfa_last_error", "lbpwfa_reduce_noalloc"]
+            "lbpwfa_status_string", "lbpwfa_last_error", "lbpwfa_reduce_noalloc",
+            "lbpwfa_batch_create", "lbpwfa_batch_step", "lbpwfa_batch_member", "lbpwfa_batch_info",
+            "lbpwfa_batch_destroy"]
 
 
 def library_path() -> str:
@@ -99,6 +108,12 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbpwfa_status_string.restype = ctypes.c_char_p
     L.lbpwfa_last_error.argtypes = [vp]
     L.lbpwfa_last_error.restype = ctypes.c_char_p
+    L.lbpwfa_batch_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+    L.lbpwfa_batch_step.argtypes = [vp, ctypes.c_int64]
+    L.lbpwfa_batch_member.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+    L.lbpwfa_batch_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+    L.lbpwfa_batch_destroy.argtypes = [vp]
+    L.lbpwfa_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -264,3 +279,80 @@ class Run:
 
     def load(self, path: str):
         self._check(load_library().lbpwfa_load(self._h, path.encode()), "lbpwfa_load")
+
+
+class _Member(Run):
+    """View of one run of a batch (outputs and state; stepping goes through
+    the batch)."""
+
+    def __init__(self, batch, handle, cfg, precision):
+        self.cfg = dict(cfg)
+        self.precision = precision
+        self._batch = batch  # keeps the batch alive
+        self._h = handle
+        inf = self.info()
+        self.K, self.Q, self.ncell = inf.K, inf.Q, inf.ncell
+
+    def close(self):
+        self._h = None  # owned by the batch
+
+
+class Batch:
+    """Many 2D runs advanced together by one persistent launch per step."""
+
+    def __init__(self, cfgs, precision="fp32", stream=None, tune=True):
+        L = load_library()
+        self.cfgs = [dict(c) for c in cfgs]
+        arr = (Params * len(cfgs))()
+        self._keep = []
+        for i, c in enumerate(cfgs):
+            p, keep = make_params(c, precision, stream if i == 0 else None)
+            arr[i] = p
+            self._keep.append(keep)
+        h = ctypes.c_void_p()
+        st = L.lbpwfa_batch_create(arr, len(cfgs), 0 if tune else 1, ctypes.byref(h))
+        if st != 0:
+            raise LbpwfaError(st, "lbpwfa_batch_create")
+        self._h = h
+        self.members = []
+        for i, c in enumerate(cfgs):
+            m = ctypes.c_void_p()
+            st = L.lbpwfa_batch_member(self._h, i, ctypes.byref(m))
+            if st != 0:
+                raise LbpwfaError(st, "lbpwfa_batch_member")
+            self.members.append(_Member(self, m, c, precision))
+
+    def step(self, nsteps: int = 1):
+        st = load_library().lbpwfa_batch_step(self._h, int(nsteps))
+        if st != 0:
+            raise LbpwfaError(st, "lbpwfa_batch_step")
+
+    def info(self) -> BatchInfo:
+        inf = BatchInfo()
+        st = load_library().lbpwfa_batch_info(self._h, ctypes.byref(inf))
+        if st != 0:
+            raise LbpwfaError(st, "lbpwfa_batch_info")
+        return inf
+
+    def synchronize(self):
+        self.members[0].synchronize()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            for m in self.members:
+                m._h = None
+            load_library().lbpwfa_batch_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

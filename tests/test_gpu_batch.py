@@ -1,0 +1,116 @@
+"""Batched sweeps: many 2D runs of uneven grids and both closures advanced
+by one persistent launch per step (CUDA-graph replays of 32 steps plus
+single launches for the rest)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+lb = pytest.importorskip("paper_2309_04872_gb300.lbpwfa")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lb.load_library()
+
+
+def _runs():
+    base = dict(dim=2, dx=0.05, courant=0.1, tau=0.53, dv=3, sigma_r=0.4, boundary="open", init_fields=True)
+    return [
+        dict(base, n=(96, 40), closure="lec", mu=1e-2, alpha=0.3, sigma_z=0.7, z0=1.5),
+        dict(base, n=(131, 37), closure="warmc", mu=5e-3, alpha=0.5, sigma_z=0.5, z0=2.0),
+        dict(base, n=(64, 64), closure="warmc", mu=2e-2, alpha=0.1, sigma_z=1.0, z0=1.0),
+        dict(base, n=(200, 24), closure="lec", mu=1e-3, alpha=0.8, sigma_z=0.6, z0=3.0),
+    ]
+
+
+@pytest.mark.parametrize("tune", [False, True])
+def test_batch_members_match_single_runs_bitwise(tune):
+    runs = _runs()
+    nsteps = 70  # two graph replays of 32 steps and 6 single launches
+    with lb.Batch(runs, "fp32", tune=tune) as b:
+        b.step(nsteps)
+        got = [(m.advected(), m.fields()) for m in b.members]
+        assert b.info().step == nsteps
+    for cfg, (A, F) in zip(runs, got):
+        with lb.Run(cfg, "fp32", variant=1) as r:
+            r.step(nsteps)
+            assert np.array_equal(r.advected(), A)
+            assert np.array_equal(r.fields(), F)
+
+
+def test_batch_fp64_matches_oracle():
+    runs = _runs()[:3]
+    with lb.Batch(runs, "fp64", tune=False) as b:
+        b.step(40)
+        for cfg, m in zip(runs, b.members):
+            o = O.Oracle(cfg)
+            o.step(40)
+            A = m.advected()
+            Ao = o.advected()
+            rest = o.rest_advected()
+            for k in range(o.K):
+                d = np.linalg.norm(A[k] - Ao[k])
+                assert d <= 1e-12 * np.linalg.norm(Ao[k]) + 1e-13 * np.sqrt(Ao[k].size)
+                if rest[k] != 0:
+                    assert d <= 1e-9 * np.linalg.norm(Ao[k] - rest[k]) + 1e-13 * abs(rest[k]) * np.sqrt(Ao[k].size)
+
+
+def test_batch_member_state_reset_matches_single_run():
+    """Replacing a WARMC member's state restarts its backward time
+    differences exactly as lbpwfa_set_state does for a single run."""
+    runs = _runs()
+    o = O.Oracle(runs[1])
+    base = o.rest_advected()
+    f = inputs.random_populations(12, o.K, o.Q, o.ncell, base, np.abs(base) * 0.03 + 1e-3)
+    with lb.Batch(runs, "fp32", tune=False) as b:
+        b.step(5)
+        b.members[1].set_state(f)
+        b.step(9)
+        A = b.members[1].advected()
+    with lb.Run(runs[1], "fp32", variant=1) as r:
+        r.step(5)
+        r.set_state(f)
+        r.step(9)
+        assert np.array_equal(r.advected(), A)
+
+
+def test_batch_member_cannot_step_alone():
+    with lb.Batch(_runs()[:2], "fp32", tune=False) as b:
+        with pytest.raises(lb.LbpwfaError) as ei:
+            b.members[0].step(1)
+        assert ei.value.status == -6
+
+
+def test_batch_autotune_cache(tmp_path, monkeypatch):
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("LBPWFA_TUNE_CACHE", str(path))
+    runs = _runs()
+    with lb.Batch(runs, "fp32", tune=True) as b:
+        first = b.info()
+        assert all(first.tuned_ms[c] > 0 for c in range(3))
+    entries = json.loads(path.read_text())
+    assert len(entries) == 1
+    (choice,) = entries.values()
+    with lb.Batch(runs, "fp32", tune=True) as b:
+        again = b.info()
+        assert all(again.tuned_ms[c] < 0 for c in range(4))  # read from the cache
+        assert list(again.tile) == list(first.tile)
+    assert choice in (0, 1, 2)
+
+
+def test_batch_rejects_mixed_inputs():
+    runs = _runs()
+    with pytest.raises(lb.LbpwfaError):
+        lb.Batch([runs[0], dict(runs[1], dim=3, n=(16, 16, 16))], "fp32")
+    with pytest.raises(lb.LbpwfaError):
+        lb.Batch(runs, "fp16s")
