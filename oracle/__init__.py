@@ -93,6 +93,9 @@ def lib():
         L.orc_driver_density.restype = ctypes.c_double
         L.orc_driver_density.argtypes = [ctypes.POINTER(_Params), ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double]
+        L.orc_adjoint_run.restype = ctypes.c_double
+        L.orc_adjoint_run.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, _DP, _DP,
+                                      _DP, _DP, _DP]
         _lib = L
     return _lib
 
@@ -232,6 +235,26 @@ class Oracle:
     def reduce(self) -> np.ndarray:
         out = np.zeros(3)
         lib().orc_reduce(self._h, _ptr(out))
+        return out
+
+    def adjoint(self, nsteps: int, witness: int, state_grad: bool = False):
+        """Run ``nsteps`` steps and return (J, dJ/d(alpha, sigma_z, sigma_r),
+        dJ/d(profile samples)) with J = E.flat[witness] at the end (the
+        discrete adjoint of the whole run; 1D and 2D).  With ``state_grad``
+        a fourth item (dJ/df, dJ/dE, dJ/dB) of the starting state follows."""
+        g3 = np.zeros(3)
+        npr = self._prof.size if self._prof is not None else 0
+        gp = np.zeros(max(1, npr))
+        lf = np.zeros(self.K * self.Q * self.ncell) if state_grad else None
+        lE = np.zeros(3 * self.ncell) if state_grad else None
+        lB = np.zeros(3 * self.ncell) if state_grad else None
+        J = lib().orc_adjoint_run(self._h, int(nsteps), int(witness), _ptr(g3), _ptr(gp),
+                                  _ptr(lf) if state_grad else None,
+                                  _ptr(lE) if state_grad else None,
+                                  _ptr(lB) if state_grad else None)
+        out = (float(J), g3, gp[:npr])
+        if state_grad:
+            out = out + ((lf, lE.reshape(3, self.ncell), lB.reshape(3, self.ncell)),)
         return out
 
 

@@ -70,6 +70,7 @@ struct orc_state {
   double *E, *B;      /* [3][ncell]: E at t_{n-1/2}, B at t_n */
   double *prev;       /* [7][ncell]: theta00, theta0[3], w[3] of the previous step */
   int have_prev;
+  int fields_from_driver;  /* E, B still the driver's initial fields */
   long step;
   /* stage arrays */
   orc_macro *mac;
@@ -478,6 +479,7 @@ orc_state* orc_create(const orc_params* p, int* status)
       for (long c = 0; c < nc; ++c)
         S->f[((size_t)k * S->Q + i) * nc + c] = S->w[i] * S->Arest[k];
   if (p->init_fields) init_fields(S);
+  S->fields_from_driver = p->init_fields && p->dim >= 2;
   S->have_prev = 0;
   S->step = 0;
   *status = 0;
@@ -585,6 +587,7 @@ void orc_set_state(orc_state* S, const double* f, const double* E, const double*
           S->f[base + c] = f[base + bulk_of(S, c)];
         }
   }
+  if (E || B) S->fields_from_driver = 0;
   if (E) {
     memcpy(S->E, E, sizeof(double) * 3 * nc);
     for (long c = 0; c < nc; ++c)
@@ -646,7 +649,39 @@ static void decode_node(const orc_state* S, long c, orc_macro* m)
   }
 }
 
-static void step_once(orc_state* S)
+/* E^{n+1/2} (S->En) and B^n (S->B) averaged to node c. */
+static void node_fields(const orc_state* S, long c, double* En, double* Bn)
+{
+  long nc = S->ncell;
+  for (int a = 0; a < 3; ++a) {
+    En[a] = 0.0;
+    Bn[a] = 0.0;
+    if (E_present(S, a)) {
+      int b = (a + 1) % 3, d = (a + 2) % 3;
+      int off[2], no = 0;
+      if (present(S, b)) off[no++] = b;
+      if (present(S, d)) off[no++] = d;
+      double s = 0.0;
+      for (int q = 0; q < (1 << no); ++q) {
+        long cc = c;
+        for (int j = 0; j < no && cc >= 0; ++j)
+          if (q & (1 << j)) cc = nb_E(S, cc, off[j], -1);
+        s += Eget(S, S->En, a, cc);
+      }
+      En[a] = s / (double)(1 << no);
+    }
+    if (B_present(S, a)) {
+      if (present(S, a))
+        Bn[a] = 0.5 * (S->B[(long)a * nc + c] + S->B[(long)a * nc + nb_node(S, c, a, -1)]);
+      else
+        Bn[a] = S->B[(long)a * nc + c];
+    }
+  }
+}
+
+/* Stages (1)-(5a) of a step: decoded macros, E^{n+1/2} (En), B^{n+1} (Bn),
+ * sources (F) and post-collision populations (fs); the state is unchanged. */
+static void forward_stages(orc_state* S)
 {
   const orc_params* p = &S->p;
   long nc = S->ncell;
@@ -716,30 +751,8 @@ static void step_once(orc_state* S)
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; ++c) {
     const orc_macro* m = &S->mac[c];
-    /* node-centred E^{n+1/2} and B^n */
-    double En[3] = {0, 0, 0}, Bn[3] = {0, 0, 0};
-    for (int a = 0; a < 3; ++a) {
-      if (E_present(S, a)) {
-        int b = (a + 1) % 3, d = (a + 2) % 3;
-        int off[2], no = 0;
-        if (present(S, b)) off[no++] = b;
-        if (present(S, d)) off[no++] = d;
-        double s = 0.0;
-        for (int q = 0; q < (1 << no); ++q) {
-          long cc = c;
-          for (int j = 0; j < no && cc >= 0; ++j)
-            if (q & (1 << j)) cc = nb_E(S, cc, off[j], -1);
-          s += Eget(S, S->En, a, cc);
-        }
-        En[a] = s / (double)(1 << no);
-      }
-      if (B_present(S, a)) {
-        if (present(S, a))
-          Bn[a] = 0.5 * (S->B[(long)a * nc + c] + S->B[(long)a * nc + nb_node(S, c, a, -1)]);
-        else
-          Bn[a] = S->B[(long)a * nc + c];
-      }
-    }
+    double En[3], Bn[3];
+    node_fields(S, c, En, Bn);
     double Fk[11] = {0};
     if (p->closure == ORC_LEC) {
       double gPi[3] = {0, 0, 0};
@@ -799,6 +812,14 @@ static void step_once(orc_state* S)
     }
   }
 
+}
+
+/* Stages (5b) and (6): pull streaming into the state and the time advance. */
+static void finish_step(orc_state* S)
+{
+  const orc_params* p = &S->p;
+  long nc = S->ncell;
+  int K = S->K, Q = S->Q;
   /* (5b) pull streaming with the open-boundary copy */
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; ++c) {
@@ -832,6 +853,12 @@ static void step_once(orc_state* S)
   memcpy(S->E, S->En, sizeof(double) * 3 * nc);
   memcpy(S->B, S->Bn, sizeof(double) * 3 * nc);
   S->step += 1;
+}
+
+static void step_once(orc_state* S)
+{
+  forward_stages(S);
+  finish_step(S);
 }
 
 void orc_step(orc_state* S, long nsteps)
@@ -912,4 +939,500 @@ void orc_reduce(const orc_state* S, double* out)
   for (size_t j = 0; j < (size_t)S->K * S->Q * nc; ++j)
     if (!isfinite(S->f[j])) bad += 1.0;
   out[0] = sn; out[1] = sb; out[2] = bad;
+}
+
+/* ======================================================================== */
+/* Discrete adjoint (FP64), 1D and 2D.                                        */
+/*                                                                          */
+/* J = E_z at one slot after N steps from the current state.  The driver     */
+/* parameters enter a step only through n_b in the E_z update (step 2) and  */
+/* the initial fields; every other stage is transposed one by one, in       */
+/* reverse order: streaming (a push), collision, sources (their gradient     */
+/* stencils become scatters to the neighbours), the node averages of E and  */
+/* B, the B and E updates, and the closure decode (LEC: implicit            */
+/* differentiation of the converged fixed point, Sec. 4.1; WARMC: chain     */
+/* rule through Eq. lb-ade-warmc-comps-A and the mass-shell components).    */
+/* ======================================================================== */
+typedef struct {
+  double *lf, *lE, *lB, *lprev;     /* adjoint of the state (f^n, E, B, prev) */
+  double *lfs, *lA, *lF, *lEn;      /* adjoint of stage quantities */
+  orc_macro *lm;                    /* adjoint of the decoded quantities */
+} orc_adj;
+
+/* ∂n_b/∂theta at (z, x, y, t): theta = (alpha, sigma_z, sigma_r) Gaussian, or
+ * the profile samples (gp, weights added) and sigma_r. */
+static void driver_grad(const orc_params* p, double z, double x, double y, double t, double scale,
+                        double* g3, double* gp)
+{
+  double zeta = z - p->z0 - t;
+  double T = 1.0, r2 = 0.0;
+  if (p->dim >= 2) {
+    r2 = x * x + (p->dim >= 3 ? y * y : 0.0);
+    T = exp(-r2 / (2.0 * p->sigma_r * p->sigma_r));
+  }
+  double L = driver_long(p, zeta);
+  if (p->profile && p->profile_len >= 2) {
+    double s = zeta / p->profile_dz + 0.5 * (p->profile_len - 1);
+    if (!(s < 0.0 || s > (double)(p->profile_len - 1))) {
+      int j = (int)floor(s);
+      if (j >= p->profile_len - 1) gp[p->profile_len - 1] += scale * T;
+      else {
+        double fr = s - j;
+        gp[j] += scale * T * (1.0 - fr);
+        gp[j + 1] += scale * T * fr;
+      }
+    }
+  } else {
+    double sz = p->sigma_z;
+    g3[0] += scale * T * exp(-zeta * zeta / (2.0 * sz * sz));
+    g3[1] += scale * L * T * zeta * zeta / (sz * sz * sz);
+  }
+  if (p->dim >= 2) {
+    double sr = p->sigma_r;
+    g3[2] += scale * L * T * r2 / (sr * sr * sr);
+  }
+}
+
+/* LEC decode transposed (implicit function theorem at the fixed point
+ * n H(n, gamma(p)) p = A_p; H = 1 + (1 + D/2) mu (n/gamma)^(2/D)). */
+static void adj_decode_lec(const orc_state* S, long c, const double* A, const orc_macro* m,
+                           const orc_macro* lm, double* lA)
+{
+  int Ds = S->Ds;
+  double D = S->p.dv, e = 2.0 / D, cH = (1.0 + 0.5 * D) * S->p.mu;
+  double n = A[0], g = m->gamma, x = n / g;
+  double p[3] = {0, 0, 0};
+  for (int a = 0; a < Ds; ++a) p[a] = g * m->u[a];
+  double xe = pow(x, e), H = 1.0 + cH * xe;
+  double lp[3] = {0, 0, 0};
+  for (int b = 0; b < Ds; ++b) {
+    double s = 0.0;
+    for (int a = 0; a < Ds; ++a) s += lm->u[a] * ((a == b ? 1.0 / g : 0.0) - p[a] * p[b] / (g * g * g));
+    lp[b] = s - lm->Pi * (1.0 + e) * m->Pi * p[b] / (g * g);
+  }
+  double ln = lm->n + lm->Pi * (1.0 + e) * xe / g;
+  double beta = cH * e * xe / (g * g), pp = 0.0, pl = 0.0;
+  for (int a = 0; a < Ds; ++a) { pp += p[a] * p[a]; pl += p[a] * lp[a]; }
+  for (int a = 0; a < Ds; ++a) {
+    double mu_a = (lp[a] + beta * p[a] * pl / (H - beta * pp)) / (n * H);
+    lA[(long)(1 + a) * S->ncell + c] += mu_a;
+    ln -= mu_a * p[a] * (H + cH * e * xe);
+  }
+  lA[c] += ln;
+}
+
+/* WARMC decode transposed (Eq. lb-ade-warmc-comps-A, traces4). */
+static void adj_decode_warmc(const orc_state* S, long c, const double* A, const orc_macro* m,
+                             orc_macro* lm, double* lA)
+{
+  long nc = S->ncell;
+  int Ds = S->Ds;
+  double n = A[0], nl = A[1];
+  /* theta00 = u . theta0 */
+  for (int a = 0; a < 3; ++a) { lm->u[a] += lm->th00 * m->th0[a]; lm->th0[a] += lm->th00 * m->u[a]; }
+  /* theta0_a = sum_b u_b theta_ab */
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      lm->u[b] += lm->th0[a] * m->th[a][b];
+      lm->th[a][b] += lm->th0[a] * m->u[b];
+    }
+  /* w_a = A_{2+a} / n */
+  for (int a = 0; a < Ds; ++a) {
+    lA[(long)(2 + a) * nc + c] += lm->w[a] / n;
+    lA[c] -= lm->w[a] * A[2 + a] / (n * n);
+  }
+  /* u_a = A_{2+a} / A_1 */
+  for (int a = 0; a < Ds; ++a) {
+    lA[(long)(2 + a) * nc + c] += lm->u[a] / nl;
+    lA[1 * nc + c] -= lm->u[a] * A[2 + a] / (nl * nl);
+  }
+  /* theta_pair = A_theta n / A_1 */
+  for (int j = 0; j < S->ntheta; ++j) {
+    int a = S->thpair[j][0], b = S->thpair[j][1];
+    double l = lm->th[a][b] + (a != b ? lm->th[b][a] : 0.0);
+    double At = A[2 + Ds + j];
+    lA[(long)(2 + Ds + j) * nc + c] += l * n / nl;
+    lA[c] += l * At / nl;
+    lA[1 * nc + c] -= l * At * n / (nl * nl);
+  }
+  /* lambda = A_1 / n */
+  lA[1 * nc + c] += lm->lam / n;
+  lA[c] -= lm->lam * nl / (n * n);
+  lA[c] += lm->n;
+}
+
+/* One reverse step.  On entry S holds the forward state X_n with its stage
+ * arrays recomputed (forward_stages) and J holds the adjoint of X_{n+1}; on
+ * exit J holds the adjoint of X_n; g3/gp accumulate dJ/dtheta of step n. */
+static void adj_step(orc_state* S, orc_adj* J, double* g3, double* gp)
+{
+  const orc_params* p = &S->p;
+  long nc = S->ncell;
+  int K = S->K, Q = S->Q, Ds = S->Ds;
+  double dt = S->dt, dx = p->dx, C = p->courant, tau = p->tau;
+  double t = S->step * dt;
+  size_t fsz = (size_t)K * Q * nc;
+  memset(J->lfs, 0, sizeof(double) * fsz);
+  memset(J->lA, 0, sizeof(double) * (size_t)K * nc);
+  memset(J->lF, 0, sizeof(double) * (size_t)K * nc);
+  memset(J->lEn, 0, sizeof(double) * 3 * nc);
+  memset(J->lm, 0, sizeof(orc_macro) * (size_t)nc);
+  double* lf_old = (double*)calloc(fsz, sizeof(double));
+  double* lE_old = (double*)calloc(3 * (size_t)nc, sizeof(double));
+  double* lB_old = (double*)calloc(3 * (size_t)nc, sizeof(double));
+  double* lprev_old = (double*)calloc(7 * (size_t)nc, sizeof(double));
+
+  /* (6)^T prev_{n+1} = (th00, th0, w) of this step */
+  if (p->closure == ORC_WARMC) {
+    for (long c = 0; c < nc; ++c) {
+      J->lm[c].th00 += J->lprev[c];
+      for (int a = 0; a < 3; ++a) {
+        J->lm[c].th0[a] += J->lprev[(long)(1 + a) * nc + c];
+        J->lm[c].w[a] += J->lprev[(long)(4 + a) * nc + c];
+      }
+    }
+  }
+  /* (5b)^T streaming: f_new(x)_i = fs(bulk(x) - xi_i)_i */
+  for (long c = 0; c < nc; ++c) {
+    long cb = bulk_of(S, c);
+    int ib[3]; coords(S, cb, ib);
+    for (int i = 0; i < Q; ++i) {
+      int src[3] = {ib[0], ib[1], ib[2]};
+      for (int a = 0; a < p->dim; ++a) {
+        int v = src[a] - S->xi[i][a], n = S->n[a];
+        if (p->boundary == ORC_PERIODIC) v = ((v % n) + n) % n;
+        src[a] = v;
+      }
+      long cs = index_of(S, src);
+      for (int k = 0; k < K; ++k)
+        J->lfs[((size_t)k * Q + i) * nc + cs] += J->lf[((size_t)k * Q + i) * nc + c];
+    }
+  }
+  /* (5a)^T collision: fs = f (1 - 1/tau) + feq(A, u)/tau + w dt F */
+  for (long c = 0; c < nc; ++c) {
+    const orc_macro* m = &S->mac[c];
+    double ul[3] = {0, 0, 0};
+    for (int a = 0; a < Ds; ++a) ul[a] = C * m->u[a];
+    for (int k = 0; k < K; ++k) {
+      double A = 0.0;
+      for (int i = 0; i < Q; ++i) A += S->f[((size_t)k * Q + i) * nc + c];
+      for (int i = 0; i < Q; ++i) {
+        size_t ix = ((size_t)k * Q + i) * nc + c;
+        double l = J->lfs[ix];
+        if (l == 0.0) continue;
+        double cu = S->xi[i][0] * ul[0] + S->xi[i][1] * ul[1] + S->xi[i][2] * ul[2];
+        double usq = ul[0] * ul[0] + ul[1] * ul[1] + ul[2] * ul[2];
+        double P = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
+        lf_old[ix] += (1.0 - 1.0 / tau) * l;
+        J->lA[(long)k * nc + c] += S->w[i] * (1.0 + P) / tau * l;
+        for (int a = 0; a < Ds; ++a)
+          J->lm[c].u[a] += S->w[i] * A / tau * C * (3.0 * S->xi[i][a] + 9.0 * cu * S->xi[i][a] - 3.0 * ul[a]) * l;
+        J->lF[(long)k * nc + c] += S->w[i] * dt * l;
+      }
+    }
+  }
+  /* (4)^T sources */
+  for (long c = 0; c < nc; ++c) {
+    const orc_macro* m = &S->mac[c];
+    orc_macro* lm = &J->lm[c];
+    double En[3], Bn[3], lEn[3] = {0, 0, 0}, lBn[3] = {0, 0, 0};
+    node_fields(S, c, En, Bn);
+    if (p->closure == ORC_LEC) {
+      for (int a = 0; a < Ds; ++a) {
+        double l = J->lF[(long)(1 + a) * nc + c];
+        if (l == 0.0) continue;
+        long cp = nb_node(S, c, a, +1), cm = nb_node(S, c, a, -1);
+        J->lm[cp].Pi -= p->mu * l / (2.0 * dx);
+        J->lm[cm].Pi += p->mu * l / (2.0 * dx);
+        double uxB = 0.0;
+        for (int k = 0; k < 3; ++k)
+          for (int q = 0; q < 3; ++q) {
+            int e3 = eps3(a, k, q);
+            if (!e3) continue;
+            uxB += e3 * m->u[k] * Bn[q];
+            lm->u[k] -= m->n * e3 * Bn[q] * l;
+            lBn[q] -= m->n * e3 * m->u[k] * l;
+          }
+        lm->n -= (En[a] + uxB) * l;
+        lEn[a] -= m->n * l;
+      }
+    } else {
+      double lnl = J->lF[1 * nc + c];
+      double hp = S->have_prev ? 1.0 : 0.0;
+      double lnlu[3] = {0, 0, 0}, lth[3][3] = {{0}};
+      for (int a = 0; a < Ds; ++a) lnlu[a] = J->lF[(long)(2 + a) * nc + c];
+      for (int j = 0; j < S->ntheta; ++j) {
+        int a = S->thpair[j][0], b = S->thpair[j][1];
+        lth[a][b] = J->lF[(long)(2 + Ds + j) * nc + c];
+      }
+      /* F_nl = -d_t th00 - d_k th0_k - n E.u */
+      if (lnl != 0.0) {
+        lm->th00 -= hp * lnl / dt;
+        lprev_old[c] += hp * lnl / dt;
+        for (int k = 0; k < Ds; ++k) {
+          J->lm[nb_node(S, c, k, +1)].th0[k] -= lnl / (2.0 * dx);
+          J->lm[nb_node(S, c, k, -1)].th0[k] += lnl / (2.0 * dx);
+        }
+        for (int a = 0; a < 3; ++a) {
+          lm->n -= En[a] * m->u[a] * lnl;
+          lEn[a] -= m->n * m->u[a] * lnl;
+          lm->u[a] -= m->n * En[a] * lnl;
+        }
+      }
+      /* F_nlu_a = -d_t th0_a - d_b th_ab - n (E + u x B)_a */
+      for (int a = 0; a < Ds; ++a) {
+        double l = lnlu[a];
+        if (l == 0.0) continue;
+        lm->th0[a] -= hp * l / dt;
+        lprev_old[(long)(1 + a) * nc + c] += hp * l / dt;
+        for (int b = 0; b < Ds; ++b) {
+          J->lm[nb_node(S, c, b, +1)].th[a][b] -= l / (2.0 * dx);
+          J->lm[nb_node(S, c, b, -1)].th[a][b] += l / (2.0 * dx);
+        }
+        double uxB = 0.0;
+        for (int k = 0; k < 3; ++k)
+          for (int q = 0; q < 3; ++q) {
+            int e3 = eps3(a, k, q);
+            if (!e3) continue;
+            uxB += e3 * m->u[k] * Bn[q];
+            lm->u[k] -= m->n * e3 * Bn[q] * l;
+            lBn[q] -= m->n * e3 * m->u[k] * l;
+          }
+        lm->n -= (En[a] + uxB) * l;
+        lEn[a] -= m->n * l;
+      }
+      /* F_th_ab; time derivatives of w against prev */
+      double dw_dt[3] = {0, 0, 0};
+      if (S->have_prev)
+        for (int a = 0; a < 3; ++a) dw_dt[a] = (m->w[a] - S->prev[(long)(4 + a) * nc + c]) / dt;
+      double gw[3][3] = {{0}};
+      for (int k = 0; k < Ds; ++k) {
+        const orc_macro* mp = &S->mac[nb_node(S, c, k, +1)];
+        const orc_macro* mm = &S->mac[nb_node(S, c, k, -1)];
+        for (int a = 0; a < 3; ++a) gw[a][k] = (mp->w[a] - mm->w[a]) / (2.0 * dx);
+      }
+      double ldw[3] = {0, 0, 0}, lgw[3][3] = {{0}};
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double l = lth[a][b];
+          if (l == 0.0) continue;
+          /* s = -th0_b dw_a - th0_a dw_b - th_bk gw_ak - th_ak gw_bk */
+          lm->th0[b] -= dw_dt[a] * l;
+          ldw[a] -= m->th0[b] * l;
+          lm->th0[a] -= dw_dt[b] * l;
+          ldw[b] -= m->th0[a] * l;
+          for (int k = 0; k < 3; ++k) {
+            lm->th[b][k] -= gw[a][k] * l;
+            lgw[a][k] -= m->th[b][k] * l;
+            lm->th[a][k] -= gw[b][k] * l;
+            lgw[b][k] -= m->th[a][k] * l;
+          }
+          /* em = E_a th0_b + E_b th0_a + eps_akq th_bk B_q + eps_bkq th_ak B_q */
+          lEn[a] -= m->th0[b] * l;
+          lm->th0[b] -= En[a] * l;
+          lEn[b] -= m->th0[a] * l;
+          lm->th0[a] -= En[b] * l;
+          for (int k = 0; k < 3; ++k)
+            for (int q = 0; q < 3; ++q) {
+              int ea = eps3(a, k, q), eb = eps3(b, k, q);
+              if (ea) { lm->th[b][k] -= ea * Bn[q] * l; lBn[q] -= ea * m->th[b][k] * l; }
+              if (eb) { lm->th[a][k] -= eb * Bn[q] * l; lBn[q] -= eb * m->th[a][k] * l; }
+            }
+        }
+      for (int a = 0; a < 3; ++a) {
+        lm->w[a] += hp * ldw[a] / dt;
+        lprev_old[(long)(4 + a) * nc + c] -= hp * ldw[a] / dt;
+        for (int k = 0; k < Ds; ++k) {
+          J->lm[nb_node(S, c, k, +1)].w[a] += lgw[a][k] / (2.0 * dx);
+          J->lm[nb_node(S, c, k, -1)].w[a] -= lgw[a][k] / (2.0 * dx);
+        }
+      }
+    }
+    /* node averages of E^{n+1/2} and B^n */
+    for (int a = 0; a < 3; ++a) {
+      if (E_present(S, a) && lEn[a] != 0.0) {
+        int b = (a + 1) % 3, d = (a + 2) % 3;
+        int off[2], no = 0;
+        if (present(S, b)) off[no++] = b;
+        if (present(S, d)) off[no++] = d;
+        for (int q = 0; q < (1 << no); ++q) {
+          long cc = c;
+          for (int j = 0; j < no && cc >= 0; ++j)
+            if (q & (1 << j)) cc = nb_E(S, cc, off[j], -1);
+          if (cc >= 0) J->lEn[(long)a * nc + cc] += lEn[a] / (double)(1 << no);
+        }
+      }
+      if (B_present(S, a) && lBn[a] != 0.0) {
+        if (present(S, a)) {
+          lB_old[(long)a * nc + c] += 0.5 * lBn[a];
+          lB_old[(long)a * nc + nb_node(S, c, a, -1)] += 0.5 * lBn[a];
+        } else {
+          lB_old[(long)a * nc + c] += lBn[a];
+        }
+      }
+    }
+  }
+  /* lambda of E^{n+1/2}: as next state's E, through the sources, through B^{n+1} */
+  for (size_t q = 0; q < 3 * (size_t)nc; ++q) J->lEn[q] += J->lE[q];
+  for (long c = 0; c < nc; ++c)
+    for (int a = 0; a < 3; ++a) {
+      if (!B_present(S, a)) continue;
+      double l = J->lB[(long)a * nc + c];
+      lB_old[(long)a * nc + c] += l;
+      int b = (a + 1) % 3, d = (a + 2) % 3;
+      if (present(S, b) && E_present(S, d)) {
+        J->lEn[(long)d * nc + c] -= dt * l / dx;
+        long cm = nb_E(S, c, b, -1);
+        if (cm >= 0) J->lEn[(long)d * nc + cm] += dt * l / dx;
+      }
+      if (present(S, d) && E_present(S, b)) {
+        J->lEn[(long)b * nc + c] += dt * l / dx;
+        long cm = nb_E(S, c, d, -1);
+        if (cm >= 0) J->lEn[(long)b * nc + cm] -= dt * l / dx;
+      }
+    }
+  /* (2)^T E^{n+1/2} = E + dt (curl B + avg(n u) + n_b) */
+  for (long c = 0; c < nc; ++c) {
+    int i[3]; coords(S, c, i);
+    double pos[3]; node_pos(S, i, pos);
+    for (int a = 0; a < 3; ++a) {
+      if (!E_present(S, a) || E_wall(S, c, a)) continue;
+      double l = J->lEn[(long)a * nc + c];
+      if (l == 0.0) continue;
+      lE_old[(long)a * nc + c] += l;
+      int b = (a + 1) % 3, d = (a + 2) % 3;
+      if (present(S, b) && B_present(S, d)) {
+        lB_old[(long)d * nc + nb_node(S, c, b, +1)] += dt * l / dx;
+        lB_old[(long)d * nc + c] -= dt * l / dx;
+      }
+      if (present(S, d) && B_present(S, b)) {
+        lB_old[(long)b * nc + nb_node(S, c, d, +1)] -= dt * l / dx;
+        lB_old[(long)b * nc + c] += dt * l / dx;
+      }
+      int off[2], no = 0;
+      if (present(S, b)) off[no++] = b;
+      if (present(S, d)) off[no++] = d;
+      for (int s = 0; s < (1 << no); ++s) {
+        long cc = c;
+        for (int j = 0; j < no; ++j)
+          if (s & (1 << j)) cc = nb_node(S, cc, off[j], +1);
+        double w = dt * l / (double)(1 << no);
+        J->lm[cc].n += w * S->mac[cc].u[a];
+        J->lm[cc].u[a] += w * S->mac[cc].n;
+      }
+      if (a == 0) {
+        double q[3] = {pos[0], pos[1], pos[2]};
+        for (int j = 0; j < no; ++j) q[off[j]] += 0.5 * dx;
+        driver_grad(p, q[0], q[1], q[2], t, dt * l, g3, gp);
+      }
+    }
+  }
+  /* (1)^T decode, then moments */
+  for (long c = 0; c < nc; ++c) {
+    double A[11];
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < Q; ++i) s += S->f[((size_t)k * Q + i) * nc + c];
+      A[k] = s;
+    }
+    if (p->closure == ORC_LEC) adj_decode_lec(S, c, A, &S->mac[c], &J->lm[c], J->lA);
+    else adj_decode_warmc(S, c, A, &S->mac[c], &J->lm[c], J->lA);
+    for (int k = 0; k < K; ++k)
+      for (int i = 0; i < Q; ++i) lf_old[((size_t)k * Q + i) * nc + c] += J->lA[(long)k * nc + c];
+  }
+  memcpy(J->lf, lf_old, sizeof(double) * fsz);
+  memcpy(J->lE, lE_old, sizeof(double) * 3 * nc);
+  memcpy(J->lB, lB_old, sizeof(double) * 3 * nc);
+  memcpy(J->lprev, lprev_old, sizeof(double) * 7 * nc);
+  free(lf_old); free(lE_old); free(lB_old); free(lprev_old);
+}
+
+/* Initial driver field (init_fields) differentiated with respect to theta,
+ * contracted with the adjoint of E^{-1/2} and B^0. */
+static void adj_init_fields(const orc_state* S, const double* lE, const double* lB, double* g3, double* gp)
+{
+  const orc_params* p = &S->p;
+  if (p->dim != 2 || !p->init_fields) return;
+  long nc = S->ncell;
+  double sr = p->sigma_r, dx = p->dx;
+  for (long c = 0; c < nc; ++c) {
+    int i[3]; coords(S, c, i);
+    double pos[3]; node_pos(S, i, pos);
+    double x = pos[1];
+    double er = erf(x / (sqrt(2.0) * sr));
+    double k = sr * sqrt(M_PI / 2.0) * er;
+    double dk_dsr = sqrt(M_PI / 2.0) * er - x / sr * exp(-x * x / (2.0 * sr * sr));
+    for (int which = 0; which < 2; ++which) {
+      double l = which == 0 ? (E_wall(S, c, 1) ? 0.0 : lE[1 * nc + c]) : lB[2 * nc + c];
+      if (l == 0.0) continue;
+      double z = which == 0 ? pos[0] + 0.5 * dx : pos[0];
+      double t = which == 0 ? -0.5 * S->dt : 0.0;
+      double zeta = z - p->z0 - t;
+      /* field = -L(zeta) k(x): d/dL = -k, d/dsr = -L dk/dsr */
+      orc_params q = *p;
+      q.dim = 1;  /* longitudinal factor only */
+      driver_grad(&q, z, 0.0, 0.0, t, -k * l, g3, gp);
+      g3[2] += -driver_long(p, zeta) * dk_dsr * l;
+    }
+  }
+}
+
+double orc_adjoint_run(orc_state* S, long N, long witness, double* g3, double* gp,
+                       double* lf0, double* lE0, double* lB0)
+{
+  if (S->p.dim > 2) return NAN;
+  long nc = S->ncell;
+  int K = S->K, Q = S->Q;
+  size_t fsz = (size_t)K * Q * nc, esz = 3 * (size_t)nc, psz = 7 * (size_t)nc;
+  size_t ssz = fsz + 2 * esz + psz;
+  double* X = (double*)malloc(sizeof(double) * ssz * (size_t)(N + 1));
+  int* hp = (int*)malloc(sizeof(int) * (size_t)(N + 1));
+  long step0 = S->step;
+  for (long n = 0; n <= N; ++n) {
+    double* x = X + ssz * (size_t)n;
+    memcpy(x, S->f, sizeof(double) * fsz);
+    memcpy(x + fsz, S->E, sizeof(double) * esz);
+    memcpy(x + fsz + esz, S->B, sizeof(double) * esz);
+    memcpy(x + fsz + 2 * esz, S->prev, sizeof(double) * psz);
+    hp[n] = S->have_prev;
+    if (n < N) step_once(S);
+  }
+  double Jv = S->E[witness];
+  orc_adj J;
+  J.lf = (double*)calloc(fsz, sizeof(double));
+  J.lE = (double*)calloc(esz, sizeof(double));
+  J.lB = (double*)calloc(esz, sizeof(double));
+  J.lprev = (double*)calloc(psz, sizeof(double));
+  J.lfs = (double*)calloc(fsz, sizeof(double));
+  J.lA = (double*)calloc((size_t)K * nc, sizeof(double));
+  J.lF = (double*)calloc((size_t)K * nc, sizeof(double));
+  J.lEn = (double*)calloc(esz, sizeof(double));
+  J.lm = (orc_macro*)calloc((size_t)nc, sizeof(orc_macro));
+  J.lE[witness] = 1.0;
+  for (long n = N - 1; n >= 0; --n) {
+    double* x = X + ssz * (size_t)n;
+    memcpy(S->f, x, sizeof(double) * fsz);
+    memcpy(S->E, x + fsz, sizeof(double) * esz);
+    memcpy(S->B, x + fsz + esz, sizeof(double) * esz);
+    memcpy(S->prev, x + fsz + 2 * esz, sizeof(double) * psz);
+    S->have_prev = hp[n];
+    S->step = step0 + n;
+    forward_stages(S);
+    adj_step(S, &J, g3, gp);
+  }
+  if (step0 == 0 && S->fields_from_driver) adj_init_fields(S, J.lE, J.lB, g3, gp);
+  if (lf0) memcpy(lf0, J.lf, sizeof(double) * fsz);
+  if (lE0) memcpy(lE0, J.lE, sizeof(double) * esz);
+  if (lB0) memcpy(lB0, J.lB, sizeof(double) * esz);
+  /* leave the final state in S */
+  double* x = X + ssz * (size_t)N;
+  memcpy(S->f, x, sizeof(double) * fsz);
+  memcpy(S->E, x + fsz, sizeof(double) * esz);
+  memcpy(S->B, x + fsz + esz, sizeof(double) * esz);
+  memcpy(S->prev, x + fsz + 2 * esz, sizeof(double) * psz);
+  S->have_prev = hp[N];
+  S->step = step0 + N;
+  free(J.lf); free(J.lE); free(J.lB); free(J.lprev); free(J.lfs); free(J.lA); free(J.lF); free(J.lEn); free(J.lm);
+  free(X); free(hp);
+  return Jv;
 }

@@ -69,6 +69,17 @@ void orc_warmc_source(double n, const double* u, const double* th, const double*
                       double* F_nl, double* F_nlu, double* F_th);
 double orc_driver_density(const orc_params* p, double z, double x, double y, double t);
 
+/* Discrete adjoint (1D, 2D): runs N steps from the current state, returns
+ * J = E[witness] after them (an index into E[3][ncell]; the E_z slot of cell c
+ * is c), and adds dJ/d(alpha, sigma_z, sigma_r) to g3 (Gaussian driver; with a
+ * profile g3[0..1] stay 0) and dJ/d(profile samples) to gp.  When the run
+ * starts at step 0 from the driver's initial fields, their dependence on the
+ * driver parameters is included.  S is left in the final state.  Returns NaN
+ * for 3D.  Memory: N + 1 stored states.  lf0, lE0, lB0 (each may be NULL)
+ * receive dJ/d(f, E, B) of the starting state, layouts as orc_get_state. */
+double orc_adjoint_run(orc_state* S, long N, long witness, double* g3, double* gp,
+                       double* lf0, double* lE0, double* lB0);
+
 #ifdef __cplusplus
 }
 #endif
