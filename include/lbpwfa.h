@@ -86,8 +86,10 @@ typedef struct {
   double z0;               /* driver centre at t = 0, k_p^-1 */
   const double* profile;   /* optional longitudinal profile L(zeta) sampled at
                               zeta_j = (j - (len-1)/2) profile_dz about the
-                              driver centre, linearly interpolated, 0 outside;
-                              replaces alpha exp(-zeta^2/2 sigma_z^2).
+                              driver centre, linearly interpolated with zero
+                              samples just outside both ends (continuous,
+                              0 from one sample beyond the ends); replaces
+                              alpha exp(-zeta^2/2 sigma_z^2).
                               Copied at create; NULL for the Gaussian. */
   int profile_len;         /* >= 2 when profile != NULL */
   double profile_dz;       /* > 0 when profile != NULL */
@@ -209,6 +211,53 @@ int lbpwfa_set_stream(lbpwfa_t h, void* stream);
 /* Wait for the handle's queued work; returns TIMEOUT when a bounded device
  * wait gave up (the step is then incomplete). */
 int lbpwfa_synchronize(lbpwfa_t h);
+
+/* ------------------------------------------------------------------------
+ * Gradients by the discrete adjoint (1D and 2D; FP64 or FP32 storage).
+ * The quantity differentiated is J = E_z at one slot after a window of steps
+ * (the accelerating field at a witness position behind the driver, Sec. 6);
+ * the parameters are those of the driver in Eq. (bunch-density): alpha,
+ * sigma_z, sigma_r, or the sampled profile values.  The reverse sweep
+ * applies, per step and in reverse order, the transpose of every stage of
+ * lbpwfa_step (streaming with the open-boundary copy, BGK collision, the
+ * LEC / WARMC sources with their central differences, the closure decode by
+ * implicit differentiation, the Yee updates and the driver current), on the
+ * forward values the step kernel saved while recording.  The paper has no
+ * adjoint; this is the exact gradient of the discrete scheme it defines.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t max_steps;        /* steps the window may hold (>= 1) */
+  int64_t checkpoint_every; /* C > 0: keep the full state every C steps and
+                               recompute each C-step segment (recording its
+                               tape) during the reverse sweep; 0: keep the
+                               tape of every step (no recomputation):
+                               (K + dim + (dim == 2)) values per node per step */
+} lbpwfa_record_params;
+
+/* Start recording at the current step: the next up-to-max_steps calls of
+ * lbpwfa_step form the window.  Replaces an earlier recording.  Stepping past
+ * max_steps returns STATE; lbpwfa_set_state and lbpwfa_load end the
+ * recording.  Errors: INVALID (3D, FP16S storage, a batch member, bad
+ * arguments), OOM, CUDA. */
+int lbpwfa_record(lbpwfa_t h, const lbpwfa_record_params* rp);
+
+typedef struct {
+  int witness[3];           /* node (z, x, y) of the E_z slot defining J */
+  double seed;              /* dL/dJ; the outputs are dL/dtheta = seed dJ/dtheta */
+  double J;                 /* out: E_z at the witness slot after the window */
+  double grad_driver[3];    /* out: dL/d(alpha, sigma_z, sigma_r); with a
+                               profile the first two are 0 */
+  double* grad_profile;     /* out: dL/d(profile sample j), profile_len host
+                               doubles, or NULL */
+} lbpwfa_adjoint_io;
+
+/* Reverse sweep over the recorded window (at least one step).  When the
+ * window starts at step 0 from the driver's initial fields
+ * (init_fields = 1, 2D), their dependence on the parameters is included.
+ * The run's state stays (or is put back) at the end of the window and the
+ * recording ends.  Synchronises.  Errors: INVALID (witness outside the grid),
+ * STATE (nothing recorded), OOM, CUDA. */
+int lbpwfa_adjoint_step(lbpwfa_t h, lbpwfa_adjoint_io* io);
 
 /* ------------------------------------------------------------------------
  * Batched sweeps (uneven 2D grids, mixed closures, one launch per step).

@@ -285,15 +285,22 @@ void orc_warmc_source(double n, const double* u, const double* th /*[3][3]*/,
  * zeta = z - z0 - t (moves towards +z at c), L = alpha exp(-zeta^2/2sz^2)
  * or a sampled profile with linear interpolation, T = exp(-r^2 / 2 sr^2).  */
 /* ------------------------------------------------------------------------ */
+/* Sampled profile: sample j sits at zeta_j = (j - (len-1)/2) dz; linear
+ * interpolation between samples, with zero samples just outside both ends
+ * (so L is continuous and falls to 0 one sample beyond the ends). */
+static double profile_sample(const orc_params* p, int j)
+{
+  return (j >= 0 && j < p->profile_len) ? p->profile[j] : 0.0;
+}
+
 static double driver_long(const orc_params* p, double zeta)
 {
   if (p->profile && p->profile_len >= 2) {
     double s = zeta / p->profile_dz + 0.5 * (p->profile_len - 1);
-    if (s < 0.0 || s > (double)(p->profile_len - 1)) return 0.0;
+    if (!(s > -1.0 && s < (double)p->profile_len)) return 0.0;
     int j = (int)floor(s);
-    if (j >= p->profile_len - 1) return p->profile[p->profile_len - 1];
     double fr = s - j;
-    return (1.0 - fr) * p->profile[j] + fr * p->profile[j + 1];
+    return (1.0 - fr) * profile_sample(p, j) + fr * profile_sample(p, j + 1);
   }
   return p->alpha * exp(-zeta * zeta / (2.0 * p->sigma_z * p->sigma_z));
 }
@@ -973,14 +980,11 @@ static void driver_grad(const orc_params* p, double z, double x, double y, doubl
   double L = driver_long(p, zeta);
   if (p->profile && p->profile_len >= 2) {
     double s = zeta / p->profile_dz + 0.5 * (p->profile_len - 1);
-    if (!(s < 0.0 || s > (double)(p->profile_len - 1))) {
+    if (s > -1.0 && s < (double)p->profile_len) {
       int j = (int)floor(s);
-      if (j >= p->profile_len - 1) gp[p->profile_len - 1] += scale * T;
-      else {
-        double fr = s - j;
-        gp[j] += scale * T * (1.0 - fr);
-        gp[j + 1] += scale * T * fr;
-      }
+      double fr = s - j;
+      if (j >= 0) gp[j] += scale * T * (1.0 - fr);
+      if (j + 1 < p->profile_len) gp[j + 1] += scale * T * fr;
     }
   } else {
     double sz = p->sigma_z;

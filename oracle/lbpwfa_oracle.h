@@ -32,7 +32,10 @@ typedef struct {
   double alpha;            /* driver peak n_b / n_i */
   double sigma_z, sigma_r; /* rms sizes, k_p^-1 */
   double z0;               /* driver centre at t = 0 */
-  const double* profile;   /* optional longitudinal profile samples (copied) */
+  const double* profile;   /* optional longitudinal profile samples (copied):
+                              sample j at zeta_j = (j - (len-1)/2) profile_dz,
+                              linear between samples, zero samples just
+                              outside both ends */
   int profile_len;
   double profile_dz;
   int boundary;            /* ORC_OPEN or ORC_PERIODIC */

@@ -1,0 +1,75 @@
+// Instantiation of the adjoint kernels (lb_adjoint.cuh).
+#include "lb_adjoint.cuh"
+#include "lb_adjoint_dispatch.h"
+
+namespace lbp {
+
+namespace {
+
+template <int DIM> struct AdjTile;
+template <> struct AdjTile<1> { static constexpr int TZ = 128, TX = 1; };
+template <> struct AdjTile<2> { static constexpr int TZ = 32, TX = 8; };
+
+template <int DIM, int CL, int PR>
+struct AdjImpl {
+  using real = typename Prec<PR>::real;
+  using T = AdjTile<DIM>;
+  static void local(const AdjParams& A, dim3 g, cudaStream_t s) {
+    adj_local_kernel<DIM, CL, real, T::TZ, T::TX><<<g, T::TZ * T::TX, 0, s>>>(A);
+  }
+  static void field(const AdjParams& A, dim3 g, cudaStream_t s) {
+    adj_field_kernel<DIM, CL, real, T::TZ, T::TX><<<g, T::TZ * T::TX, 0, s>>>(A);
+  }
+  static void init_rows(const StepParams& P, const void* lE, const void* lB, const double* Kx, double* rows,
+                        dim3 g, cudaStream_t s) {
+    if constexpr (DIM == 2)
+      adj_init_rows_kernel<real, T::TZ, T::TX><<<g, T::TZ * T::TX, 0, s>>>(P, (const real*)lE, (const real*)lB, Kx,
+                                                                            rows);
+  }
+  static void seed(void* lE, long long idx, double v, cudaStream_t s) {
+    adj_seed_kernel<real><<<1, 32, 0, s>>>((real*)lE, idx, v);
+  }
+  static void read_slot(const void* E, long long idx, double* out, cudaStream_t s) {
+    read_slot_kernel<real><<<1, 32, 0, s>>>((const real*)E, idx, out);
+  }
+  static void fill(AdjKernelSet* k) {
+    using AM = AdjModel<DIM, CL>;
+    k->K = AM::K;
+    k->NG = AM::NG;
+    k->NPREV = AM::NPREV;
+    k->NTAPE = AM::NTAPE;
+    k->tz = T::TZ;
+    k->tx = T::TX;
+    k->local = &local;
+    k->field = &field;
+    k->init_rows = &init_rows;
+    k->seed = &seed;
+    k->read_slot = &read_slot;
+  }
+};
+
+template <int PR>
+bool pick(int dim, int closure, AdjKernelSet* k) {
+  if (dim == 1 && closure == CL_LEC) { AdjImpl<1, CL_LEC, PR>::fill(k); return true; }
+  if (dim == 1 && closure == CL_WARMC) { AdjImpl<1, CL_WARMC, PR>::fill(k); return true; }
+  if (dim == 2 && closure == CL_LEC) { AdjImpl<2, CL_LEC, PR>::fill(k); return true; }
+  if (dim == 2 && closure == CL_WARMC) { AdjImpl<2, CL_WARMC, PR>::fill(k); return true; }
+  return false;
+}
+
+}  // namespace
+
+bool adjoint_kernels(int dim, int closure, int precision, AdjKernelSet* k) {
+  if (precision == PR_F64) return pick<PR_F64>(dim, closure, k);
+  if (precision == PR_F32) return pick<PR_F32>(dim, closure, k);
+  return false;
+}
+
+void launch_grad(const GradParams& G, cudaStream_t s) {
+  if (G.nsets <= 0) return;
+  grad_sets_kernel<<<G.nsets, 256, 0, s>>>(G);
+  const int nout = G.plen > 3 ? G.plen : 3;
+  grad_accum_kernel<<<(nout + 127) / 128, 128, 0, s>>>(G);
+}
+
+}  // namespace lbp

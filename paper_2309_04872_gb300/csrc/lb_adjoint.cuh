@@ -1,0 +1,822 @@
+// Discrete adjoint of one coupled time step (1D and 2D), for gradients of a
+// field value with respect to the driver parameters (Eq. bunch-density:
+// alpha, sigma_z, sigma_r or the sampled profile).
+//
+// The forward step (lb_step.cuh) is, per node: moments and closure decode
+// (Eq. disc-moments-ade, Sec. 4.1 / 5.1), E^{n+1/2} = E^{n-1/2} + dt (curl B
+// + n u + n_b z), B^{n+1} = B^n - dt curl E^{n+1/2}, sources (Eq.
+// lb-ade-lec-comps-F / lb-ade-warmc-comps-F with App. A) from E^{n+1/2},
+// B^n and central differences of the neighbours, BGK + w_i dt F (Eq. lbe,
+// lsource), pull streaming with the open-boundary copy (Eq. open-bc).  The
+// reverse step applies the transpose of each stage in the opposite order.
+// Every transposed stencil is written in gather ("pull") form, so each node
+// computes its own adjoint without atomics:
+//   adj_local_kernel  - per node: adjoint of streaming (gather of the next
+//     state's population adjoints, folding the boundary copies), of the
+//     collision and of the sources' local terms; publishes small records
+//     for the neighbours: the decode adjoint of its local part, the
+//     coefficients of its gradient stencils, and the adjoints of its
+//     node-averaged E^{n+1/2} and B^n.
+//   adj_field_kernel  - per node: adjoint of E^{n+1/2} at the slots around
+//     the node (next-state E, B update, node averages), of B^n (E update,
+//     node average), of the decoded values (neighbours' gradient records,
+//     the current n u), the decode adjoint, and the population adjoint
+//     lambda_f^n = (1 - 1/tau) lambda_fs + lambda_A; plus per-row partial
+//     sums of dt lambda(E_z) times the driver's transverse factor, from
+//     which the driver-parameter gradients are formed.
+// The step's forward values come from the tape the step kernel wrote while
+// recording: its deviation moments dA^n (decoded here exactly as the step
+// decoded them), E^{n+1/2} and B^n; the previous step's values of the WARMC
+// backward differences come from the previous tape entry.
+#pragma once
+
+#include "lb_adjoint_types.cuh"
+#include "lb_step.cuh"
+
+namespace lbp {
+
+template <int DIM, int CL>
+struct AdjModel {
+  using M = Model<DIM, CL>;
+  static constexpr int K = M::K;
+  static constexpr int NE = DIM;                                // present E components z[, x]
+  static constexpr int NB = DIM == 2 ? 1 : 0;                   // present B components [y]
+  static constexpr int NTAPE = K + NE + NB;
+  static constexpr int NG = CL == CL_LEC ? DIM : 1 + DIM + DIM * DIM;
+  static constexpr int NPREV = M::NPREV;
+};
+
+
+// ---------------------------------------------------------------------------
+// Index helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int aidx(const StepParams& P, int z, int x) { return z + x * P.nzp; }
+
+// Nodes m with wrap_or_clamp(m + delta) == c along an axis of n nodes.
+struct Pre {
+  int v[2];
+  int cnt;
+};
+__device__ __forceinline__ Pre preimage(int c, int n, int delta, int periodic) {
+  Pre r;
+  r.cnt = 0;
+  const int m = c - delta;
+  if (periodic) {
+    r.v[r.cnt++] = m < 0 ? m + n : (m >= n ? m - n : m);
+  } else {
+    if (m >= 0 && m < n) r.v[r.cnt++] = m;
+    if ((delta > 0 && c == n - 1) || (delta < 0 && c == 0)) r.v[r.cnt++] = c;
+  }
+  return r;
+}
+
+// Adjoint of the post-collision population (k, i) of node (z, x): the sum of
+// the next state's population adjoints of every node that pulls it.  Node y
+// pulls f*_i(bulk(y) - xi_i); with open boundaries the boundary nodes copy
+// their nearest bulk node, so a bulk target also collects their adjoints.
+template <int DIM, typename real>
+__device__ __forceinline__ real lfs_get(const StepParams& P, const real* lfk, int i, int z, int x, bool edge) {
+  using L = Lattice<DIM>;
+  const int pl = (int)P.plane;
+  const real* b = lfk + (size_t)i * pl;
+  int yz = z + L::c(i, 0), yx = DIM >= 2 ? x + L::c(i, 1) : 0;
+  if (!edge) return b[aidx(P, yz, yx)];
+  if (P.periodic) {
+    yz = wrap_or_clamp(yz, P.n[0], 1);
+    if (DIM >= 2) yx = wrap_or_clamp(yx, P.n[1], 1);
+    return b[aidx(P, yz, yx)];
+  }
+  if (yz < 1 || yz > P.n[0] - 2) return real(0);
+  if (DIM >= 2 && (yx < 1 || yx > P.n[1] - 2)) return real(0);
+  int cz[3] = {yz, -1, -1}, cx[3] = {yx, -1, -1};
+  if (yz == 1) cz[1] = 0;
+  if (yz == P.n[0] - 2) cz[2] = P.n[0] - 1;
+  if (DIM >= 2) {
+    if (yx == 1) cx[1] = 0;
+    if (yx == P.n[1] - 2) cx[2] = P.n[1] - 1;
+  }
+  real s = 0;
+#pragma unroll
+  for (int qz = 0; qz < 3; ++qz) {
+    if (cz[qz] < 0) continue;
+#pragma unroll
+    for (int qx = 0; qx < (DIM >= 2 ? 3 : 1); ++qx) {
+      if (cx[qx] < 0) continue;
+      s += b[aidx(P, cz[qz], cx[qx])];
+    }
+  }
+  return s;
+}
+
+// Node not within reach of a boundary rule for the population gather.
+template <int DIM>
+__device__ __forceinline__ bool gather_interior(const StepParams& P, int z, int x) {
+  bool in = z >= 3 && z <= P.n[0] - 4;
+  if (DIM >= 2) in = in && x >= 3 && x <= P.n[1] - 4;
+  return in;
+}
+
+// ---------------------------------------------------------------------------
+// Decoded values of a node, from its tape moments (the step's decode).
+// ---------------------------------------------------------------------------
+template <int DIM, int CL, typename real>
+struct Node {
+  real dA[Model<DIM, CL>::K];
+  real rec[Model<DIM, CL>::NM];
+};
+
+template <int DIM, int CL, typename real>
+__device__ __forceinline__ void load_node(const StepParams& P, const real* tp, int id, Node<DIM, CL, real>& N) {
+  constexpr int K = Model<DIM, CL>::K;
+  const int pl = (int)P.plane;
+#pragma unroll
+  for (int k = 0; k < K; ++k) N.dA[k] = tp[k * pl + id];
+  decode_record<DIM, CL, real>(P, consts<real>(P), N.dA, N.rec);
+}
+
+// WARMC theta^{ab} from the record (stored pairs, symmetric; 0 elsewhere).
+template <int DIM, typename real>
+__device__ __forceinline__ real th_of(const real* rec, int a, int b) {
+  using M = Model<DIM, CL_WARMC>;
+  const int j = M::thidx(a, b);
+  return j >= 0 ? rec[M::R_TH + j] : real(0);
+}
+
+// Adjoint of the decoded values of one node.
+template <typename real>
+struct LMac {
+  real n, lam, Pi, th00;
+  real u[3], th0[3], w[3];
+  real th[3][3];
+  __device__ __forceinline__ void zero() {
+    n = lam = Pi = th00 = real(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      u[a] = th0[a] = w[a] = real(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) th[a][b] = real(0);
+    }
+  }
+};
+
+// Transposed decode: adds d(decoded)/d(dA)^T lm to lA.
+//  LEC (Sec. 4.1): n = A_0; p solves n H(n/gamma) p = A_p with
+//    gamma = sqrt(1 + p^2), H = 1 + (1 + D/2) mu (n/gamma)^(2/D); u = p/gamma,
+//    Pi = (n/gamma)^(1+2/D).  At the fixed point the implicit function
+//    theorem gives dp = M^-1 (dA_p - p (H + cH e x^e) dn) with
+//    M = n (H I - beta p p^T), beta = cH e x^e / gamma^2 (x = n/gamma,
+//    e = 2/D), inverted by the Sherman-Morrison formula.
+//  WARMC (Eq. lb-ade-warmc-comps-A, traces4): the record n, lambda = nl/n,
+//    u = A_u / nl, theta_j = A_j n / nl, theta^{0a} = u_b theta^{ab}, and
+//    the step's theta^{00} = u_a theta^{0a}, w^a = lambda u^a.
+template <int DIM, int CL, typename real>
+__device__ __forceinline__ void decode_adjoint(const StepParams& P, const StepConst<real>& S,
+                                               const Node<DIM, CL, real>& N, LMac<real> lm, real* lA) {
+  using M = Model<DIM, CL>;
+  if constexpr (CL == CL_LEC) {
+    const real n = N.rec[M::R_N];
+    real u[DIM], p[DIM], uu = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { u[a] = N.rec[M::R_U + a]; uu += u[a] * u[a]; }
+    const real g = real(1) / sqrt(real(1) - uu);
+    const real ig = real(1) / g;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) p[a] = g * u[a];
+    const real D = real(P.D), e = real(2) / D;
+    const real x = n * ig;
+    const real xe = pow_2_over_D<real>(x, P.D);
+    const real Pi = x * xe;
+    const real H = real(1) + S.cH * xe;
+    real lp[DIM], pl = 0, pp = 0;
+    real ud = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) ud += lm.u[a] * p[a];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      lp[b] = lm.u[b] * ig - ud * p[b] * ig * ig * ig - lm.Pi * (real(1) + e) * Pi * p[b] * ig * ig;
+      pl += p[b] * lp[b];
+      pp += p[b] * p[b];
+    }
+    real ln = lm.n + lm.Pi * (real(1) + e) * xe * ig;
+    const real beta = S.cH * e * xe * ig * ig;
+    const real c = beta * pl / (H - beta * pp);
+    const real inH = real(1) / (n * H);
+    const real dn_coef = H + S.cH * e * xe;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const real mu_a = (lp[a] + c * p[a]) * inH;
+      lA[1 + a] += mu_a;
+      ln -= mu_a * p[a] * dn_coef;
+    }
+    lA[0] += ln;
+  } else {
+    const real n = real(1) + N.dA[0];
+    const real nl = S.Arest[1] + N.dA[1];
+    const real inl = real(1) / nl;
+    const real lam = N.rec[M::R_LAM];
+    real u[3] = {0, 0, 0}, th0[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { u[a] = N.rec[M::R_U + a]; th0[a] = N.rec[M::R_TH0 + a]; }
+    // theta^{00} = u_a theta^{0a}
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { lm.u[a] += lm.th00 * th0[a]; lm.th0[a] += lm.th00 * u[a]; }
+    // theta^{0a} = u_b theta^{ab}
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        if (M::thidx(a, b) < 0) continue;
+        lm.u[b] += lm.th0[a] * th_of<DIM>(N.rec, a, b);
+        lm.th[a][b] += lm.th0[a] * u[b];
+      }
+    // w^a = lambda u^a
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { lm.lam += lm.w[a] * u[a]; lm.u[a] += lm.w[a] * lam; }
+    // theta_j = A_j n / nl
+    real lilam = 0;
+    const real ilam = n * inl;
+#pragma unroll
+    for (int j = 0; j < M::NTH; ++j) {
+      const int a = M::tha(j), b = M::thb(j);
+      const real l = a == b ? lm.th[a][a] : lm.th[a][b] + lm.th[b][a];
+      lA[2 + DIM + j] += l * ilam;
+      lilam += l * (S.Arest[2 + DIM + j] + N.dA[2 + DIM + j]);
+    }
+    real ln = lm.n + lilam * inl;
+    real linl = lilam * n;
+    // u_a = A_{2+a} / nl
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { lA[2 + a] += lm.u[a] * inl; linl += lm.u[a] * N.dA[2 + a]; }
+    // lambda = nl / n
+    real lnl = lm.lam / n;
+    ln -= lm.lam * lam / n;
+    lnl -= linl * inl * inl;
+    lA[1] += lnl;
+    lA[0] += ln;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 1: streaming, collision and local source adjoints.
+// ---------------------------------------------------------------------------
+template <int DIM, int CL, typename real, int TZ, int TX>
+__global__ void __launch_bounds__(TZ* TX) adj_local_kernel(const AdjParams A) {
+  using M = Model<DIM, CL>;
+  using AM = AdjModel<DIM, CL>;
+  using L = Lattice<DIM>;
+  constexpr int K = M::K, Q = L::Q;
+  const StepParams& P = A.P;
+  const StepConst<real>& S = consts<real>(P);
+  const int z = blockIdx.x * TZ + threadIdx.x % TZ;
+  const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
+  if (z >= P.n[0] || (DIM >= 2 && x >= P.n[1])) return;
+  const int pl = (int)P.plane;
+  const int id = aidx(P, z, x);
+  const real* tp = reinterpret_cast<const real*>(A.tape);
+
+  Node<DIM, CL, real> N;
+  load_node<DIM, CL, real>(P, tp, id, N);
+  const real n = N.rec[M::R_N];
+  real u[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) u[a] = N.rec[M::R_U + a];
+
+  LMac<real> lm;
+  lm.zero();
+
+  // ---- streaming + collision adjoint --------------------------------------
+  // fs = f (1 - 1/tau) + f^eq(A, C u)/tau + w dt F with
+  // f^eq = w A (1 + 3 cu + 9/2 cu^2 - 3/2 u^2):
+  //   lambda_A += sum_i w_i (1 + P_i) lambda_fs / tau
+  //   lambda_u += sum_i w_i A C (3 xi + 9 cu xi - 3 u) lambda_fs / tau
+  //   lambda_F  = dt sum_i w_i lambda_fs
+  const bool edge = !gather_interior<DIM>(P, z, x);
+  real ul[3] = {0, 0, 0}, usq = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { ul[a] = S.courant * u[a]; usq += ul[a] * ul[a]; }
+  const real* lf = reinterpret_cast<const real*>(A.lf_in);
+  real lA[K], lF[K], lu_c[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const real* lfk = lf + (size_t)k * Q * pl;
+    real m0 = 0, mA = 0, mu_[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const real l = lfs_get<DIM, real>(P, lfk, i, z, x, edge);
+      const real wl = real(L::w(i)) * l;
+      real cu = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) cu += real(L::c(i, a)) * ul[a];
+      m0 += wl;
+      mA += wl * (real(1) + real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) mu_[a] += wl * (real(L::c(i, a)) * (real(3) + real(9) * cu) - real(3) * ul[a]);
+    }
+    const real Ak = S.Arest[k] + N.dA[k];
+    lA[k] = mA * S.inv_tau;
+    lF[k] = S.dt * m0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) lu_c[a] += Ak * mu_[a];
+  }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) lm.u[a] += lu_c[a] * S.courant * S.inv_tau;
+
+  // ---- fields at the node (E^{n+1/2}, B^n from the tape) -------------------
+  const real* tE = tp + K * pl;
+  real En[3] = {0, 0, 0}, Bn[3] = {0, 0, 0};
+  if constexpr (DIM == 1) {
+    En[0] = tE[id];
+  } else {
+    // E_z: slots (z, x) and (z, x - 1) (conducting-wall ghost below x = 0)
+    real ez = tE[id];
+    if (x >= 1) ez += tE[aidx(P, z, x - 1)];
+    else if (P.periodic) ez += tE[aidx(P, z, P.n[1] - 1)];
+    En[0] = real(0.5) * ez;
+    // E_x: slots (z, x) and (z - 1, x) (z clamps)
+    const int zm = z >= 1 ? z - 1 : (P.periodic ? P.n[0] - 1 : 0);
+    En[1] = real(0.5) * (tE[pl + id] + tE[pl + aidx(P, zm, x)]);
+    Bn[2] = tp[(K + DIM) * pl + id];
+  }
+
+  // ---- source adjoint, local terms ----------------------------------------
+  real lEn[3] = {0, 0, 0}, lBn[3] = {0, 0, 0};
+  real G[AM::NG];
+  real lpo[AM::NPREV > 0 ? AM::NPREV : 1];
+#pragma unroll
+  for (int j = 0; j < (AM::NPREV > 0 ? AM::NPREV : 1); ++j) lpo[j] = real(0);
+  // -n (E + u x B)_a and its adjoint, shared by both closures
+  auto lorentz = [&](int a, real l) {
+    real uxB = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int e3 = levi(a, k, q);
+        if (e3 == 0) continue;
+        uxB += real(e3) * u[k] * Bn[q];
+        lm.u[k] -= n * real(e3) * Bn[q] * l;
+        lBn[q] -= n * real(e3) * u[k] * l;
+      }
+    lm.n -= (En[a] + uxB) * l;
+    lEn[a] -= n * l;
+  };
+  if constexpr (CL == CL_LEC) {
+    // F_p = -mu grad Pi - n (E + u x B)
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      G[a] = lF[1 + a];
+      lorentz(a, lF[1 + a]);
+    }
+  } else {
+    const int hp = P.have_prev;
+    const real lam = N.rec[M::R_LAM];
+    real th0[3] = {0, 0, 0}, w[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { th0[a] = N.rec[M::R_TH0 + a]; w[a] = lam * u[a]; }
+    // previous-step w (backward time difference)
+    real dw[3] = {0, 0, 0};
+    if (hp) {
+      real wp[3] = {0, 0, 0};
+      if (A.tape_prev) {
+        Node<DIM, CL, real> Np;
+        load_node<DIM, CL, real>(P, reinterpret_cast<const real*>(A.tape_prev), id, Np);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) wp[a] = Np.rec[M::R_LAM] * Np.rec[M::R_U + a];
+      } else {
+        const real* p0 = reinterpret_cast<const real*>(A.prev0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) wp[a] = p0[(1 + DIM + a) * pl + id];
+      }
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) dw[a] = (w[a] - wp[a]) * S.idt;
+    }
+    // gradients of w from the neighbours' decode
+    real gw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const int ck = k == 0 ? z : x;
+      const int cp = wrap_or_clamp(ck + 1, P.n[k], P.periodic), cm = wrap_or_clamp(ck - 1, P.n[k], P.periodic);
+      const int idp = k == 0 ? aidx(P, cp, x) : aidx(P, z, cp);
+      const int idm = k == 0 ? aidx(P, cm, x) : aidx(P, z, cm);
+      Node<DIM, CL, real> Np, Nm;
+      load_node<DIM, CL, real>(P, tp, idp, Np);
+      load_node<DIM, CL, real>(P, tp, idm, Nm);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a)
+        gw[a][k] = (Np.rec[M::R_LAM] * Np.rec[M::R_U + a] - Nm.rec[M::R_LAM] * Nm.rec[M::R_U + a]) * S.i2dx;
+    }
+    // adjoints of the previous-step values this step wrote
+    if (A.lp_in) {
+      const real* lpi = reinterpret_cast<const real*>(A.lp_in);
+      lm.th00 += lpi[id];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        lm.th0[a] += lpi[(1 + a) * pl + id];
+        lm.w[a] += lpi[(1 + DIM + a) * pl + id];
+      }
+    }
+    // F_{n lambda} = -d_t th00 - d_k th0k - n E.u
+    {
+      const real l = lF[1];
+      G[0] = l;
+      if (hp) { lm.th00 -= l * S.idt; lpo[0] += l * S.idt; }
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        lm.n -= En[a] * u[a] * l;
+        lEn[a] -= n * u[a] * l;
+        lm.u[a] -= n * En[a] * l;
+      }
+    }
+    // F_{n lambda u_a} = -d_t th0a - d_b th_ab - n (E + u x B)_a
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const real l = lF[2 + a];
+      G[1 + a] = l;
+      if (hp) { lm.th0[a] -= l * S.idt; lpo[1 + a] += l * S.idt; }
+      lorentz(a, l);
+    }
+    // F_{lambda th_ab}: time and space derivatives of w, EM terms
+    real ldw[3] = {0, 0, 0}, lgw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int j = 0; j < M::NTH; ++j) {
+      const real l = lF[2 + DIM + j];
+      const int a = M::tha(j), b = M::thb(j);
+      lm.th0[b] -= dw[a] * l;
+      ldw[a] -= th0[b] * l;
+      lm.th0[a] -= dw[b] * l;
+      ldw[b] -= th0[a] * l;
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) {
+        lm.th[b][q] -= gw[a][q] * l;
+        lgw[a][q] -= th_of<DIM>(N.rec, b, q) * l;
+        lm.th[a][q] -= gw[b][q] * l;
+        lgw[b][q] -= th_of<DIM>(N.rec, a, q) * l;
+      }
+      lEn[a] -= th0[b] * l;
+      lm.th0[b] -= En[a] * l;
+      lEn[b] -= th0[a] * l;
+      lm.th0[a] -= En[b] * l;
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int ea = levi(a, q, r), eb = levi(b, q, r);
+          if (ea != 0) {
+            lm.th[b][q] -= real(ea) * Bn[r] * l;
+            lBn[r] -= real(ea) * th_of<DIM>(N.rec, b, q) * l;
+          }
+          if (eb != 0) {
+            lm.th[a][q] -= real(eb) * Bn[r] * l;
+            lBn[r] -= real(eb) * th_of<DIM>(N.rec, a, q) * l;
+          }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      if (hp) { lm.w[a] += ldw[a] * S.idt; lpo[1 + DIM + a] -= ldw[a] * S.idt; }
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) G[1 + DIM + a * DIM + k] = lgw[a][k];
+    }
+  }
+
+  decode_adjoint<DIM, CL, real>(P, S, N, lm, lA);
+
+  real* rA = reinterpret_cast<real*>(A.rA);
+#pragma unroll
+  for (int k = 0; k < K; ++k) rA[k * pl + id] = lA[k];
+  real* rG = reinterpret_cast<real*>(A.rG);
+#pragma unroll
+  for (int j = 0; j < AM::NG; ++j) rG[j * pl + id] = G[j];
+  real* rEn = reinterpret_cast<real*>(A.rEn);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) rEn[a * pl + id] = lEn[a];
+  if constexpr (DIM == 2) reinterpret_cast<real*>(A.rBn)[2 * pl + id] = lBn[2];
+  if constexpr (AM::NPREV > 0) {
+    real* lpo_g = reinterpret_cast<real*>(A.lp_out);
+#pragma unroll
+    for (int j = 0; j < AM::NPREV; ++j) lpo_g[j * pl + id] = lpo[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 2: field adjoints, gradient-stencil gathers, decode adjoint and the
+// population adjoint of the previous state.
+// ---------------------------------------------------------------------------
+
+// Adjoint of E_a^{n+1/2} at slot (sz, sx): as the next state's E, through
+// the node averages of the sources and through B^{n+1}; zero on walls.
+template <int DIM, typename real>
+__device__ __forceinline__ real lEn_slot(const AdjParams& A, int a, int sz, int sx) {
+  const StepParams& P = A.P;
+  const StepConst<real>& S = consts<real>(P);
+  const int pl = (int)P.plane;
+  const real* lE = reinterpret_cast<const real*>(A.lE_in);
+  const real* rEn = reinterpret_cast<const real*>(A.rEn);
+  const int id = aidx(P, sz, sx);
+  if constexpr (DIM == 1) {
+    return lE[id] + rEn[id];
+  } else {
+    const real* lB = reinterpret_cast<const real*>(A.lB_in) + 2 * pl;  // B_y
+    const real* rE = rEn + a * pl;
+    const real cdt = S.dt * S.idx;
+    if (a == 0) {
+      if (!P.periodic && sx == P.n[1] - 1) return real(0);  // conducting wall
+      real v = lE[id] + real(0.5) * rE[id] + cdt * lB[id];
+      int xp = sx + 1;
+      if (xp >= P.n[1]) xp = P.periodic ? 0 : -1;
+      if (xp >= 0) {
+        const int idp = aidx(P, sz, xp);
+        v += real(0.5) * rE[idp] - cdt * lB[idp];
+      }
+      return v;
+    } else {
+      real v = lE[pl + id] + real(0.5) * rE[id] - cdt * lB[id];
+      int zp = sz + 1;
+      if (zp >= P.n[0]) zp = P.periodic ? 0 : -1;
+      if (zp >= 0) {
+        const int idp = aidx(P, zp, sx);
+        v += real(0.5) * rE[idp] + cdt * lB[idp];
+      }
+      if (!P.periodic && sz == 0) v += real(0.5) * rE[id] + cdt * lB[id];
+      return v;
+    }
+  }
+}
+
+template <int DIM, int CL, typename real, int TZ, int TX>
+__global__ void __launch_bounds__(TZ* TX) adj_field_kernel(const AdjParams A) {
+  using M = Model<DIM, CL>;
+  using AM = AdjModel<DIM, CL>;
+  using L = Lattice<DIM>;
+  constexpr int K = M::K, Q = L::Q;
+  const StepParams& P = A.P;
+  const StepConst<real>& S = consts<real>(P);
+  __shared__ double red[2][TX][TZ];
+  const int tzi = threadIdx.x % TZ, txi = threadIdx.x / TZ;
+  const int z = blockIdx.x * TZ + tzi;
+  const int x = DIM >= 2 ? blockIdx.y * TX + txi : 0;
+  const bool inside = z < P.n[0] && (DIM < 2 || x < P.n[1]);
+  double r0 = 0.0, r2 = 0.0;
+  if (inside) {
+    const int pl = (int)P.plane;
+    const int id = aidx(P, z, x);
+    const real* tp = reinterpret_cast<const real*>(A.tape);
+    Node<DIM, CL, real> N;
+    load_node<DIM, CL, real>(P, tp, id, N);
+    const real n = N.rec[M::R_N];
+    real u[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) u[a] = N.rec[M::R_U + a];
+
+    LMac<real> lm;
+    lm.zero();
+    const real dt = S.dt;
+    // ---- E^{n+1/2} slots: own (E_a at this node) and the ones below --------
+    // J_a at slot s averages n u_a over s and s + e_b (b the slot's offset
+    // axis; 1D: the node itself); the B_y curl at this node reads the same
+    // slots.
+    real* lEo = reinterpret_cast<real*>(A.lE_out);
+    if constexpr (DIM == 1) {
+      const real l = lEn_slot<DIM, real>(A, 0, z, 0);
+      lEo[id] = l;
+      lm.n += dt * l * u[0];
+      lm.u[0] += dt * l * n;
+      r0 = (double)(dt * l);
+      r2 = 0.0;
+    } else {
+      const real cdt = dt * S.idx;
+      real lBy = reinterpret_cast<const real*>(A.lB_in)[2 * pl + id] +
+                 reinterpret_cast<const real*>(A.rBn)[2 * pl + id];
+      // E_z: offset axis x
+      {
+        const real lc = lEn_slot<DIM, real>(A, 0, z, x);
+        lEo[id] = lc;
+        r0 = (double)(dt * lc) * A.Tx[x];
+        r2 = (double)(dt * lc) * A.Tx[P.n[1] + x];
+        real jsum = real(0.5) * lc;   // slot s = this node
+        lBy -= cdt * lc;
+        const Pre pr = preimage(x, P.n[1], +1, P.periodic);
+        for (int q = 0; q < pr.cnt; ++q) {
+          const real ls = pr.v[q] == x ? lc : lEn_slot<DIM, real>(A, 0, z, pr.v[q]);
+          jsum += real(0.5) * ls;
+          lBy += cdt * ls;
+        }
+        lm.n += dt * jsum * u[0];
+        lm.u[0] += dt * jsum * n;
+      }
+      // E_x: offset axis z
+      {
+        const real lc = lEn_slot<DIM, real>(A, 1, z, x);
+        lEo[pl + id] = lc;
+        real jsum = real(0.5) * lc;
+        lBy += cdt * lc;
+        const Pre pr = preimage(z, P.n[0], +1, P.periodic);
+        for (int q = 0; q < pr.cnt; ++q) {
+          const real ls = pr.v[q] == z ? lc : lEn_slot<DIM, real>(A, 1, pr.v[q], x);
+          jsum += real(0.5) * ls;
+          lBy -= cdt * ls;
+        }
+        lm.n += dt * jsum * u[1];
+        lm.u[1] += dt * jsum * n;
+      }
+      reinterpret_cast<real*>(A.lB_out)[2 * pl + id] = lBy;
+    }
+
+    // ---- gradient stencils of the neighbours that read this node -----------
+    const real* rG = reinterpret_cast<const real*>(A.rG);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const int ck = k == 0 ? z : x;
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        // side 0: m + e_k = this node (coefficient -1/2dx); side 1: m - e_k
+        const Pre pr = preimage(ck, P.n[k], side == 0 ? +1 : -1, P.periodic);
+        const real sgn = side == 0 ? real(-1) : real(1);
+        for (int q = 0; q < pr.cnt; ++q) {
+          const int m = k == 0 ? aidx(P, pr.v[q], x) : aidx(P, z, pr.v[q]);
+          const real c = sgn * S.i2dx;
+          if constexpr (CL == CL_LEC) {
+            lm.Pi += c * S.mu * rG[k * pl + m];
+          } else {
+            lm.th0[k] += c * rG[m];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+              lm.th[a][k] += c * rG[(1 + a) * pl + m];
+              lm.w[a] -= c * rG[(1 + DIM + a * DIM + k) * pl + m];
+            }
+          }
+        }
+      }
+    }
+
+    real lA[K];
+    const real* rA = reinterpret_cast<const real*>(A.rA);
+#pragma unroll
+    for (int k = 0; k < K; ++k) lA[k] = rA[k * pl + id];
+    decode_adjoint<DIM, CL, real>(P, S, N, lm, lA);
+
+    // ---- population adjoint of the previous state ----------------------------
+    const bool edge = !gather_interior<DIM>(P, z, x);
+    const real* lf = reinterpret_cast<const real*>(A.lf_in);
+    real* lfo = reinterpret_cast<real*>(A.lf_out);
+    const real omt = real(1) - S.inv_tau;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const real* lfk = lf + (size_t)k * Q * pl;
+      real* lok = lfo + (size_t)k * Q * pl;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) lok[i * pl + id] = omt * lfs_get<DIM, real>(P, lfk, i, z, x, edge) + lA[k];
+    }
+  }
+  // ---- per-row partial sums of the driver-gradient weights ---------------
+  red[0][txi][tzi] = r0;
+  red[1][txi][tzi] = r2;
+  __syncthreads();
+  if (txi == 0 && z < P.n[0]) {
+    double s0 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int t = 0; t < TX; ++t) { s0 += red[0][t][tzi]; s2 += red[1][t][tzi]; }
+    const int ntx = gridDim.y;
+    A.rows[(size_t)blockIdx.y * P.n[0] + z] = s0;
+    A.rows[((size_t)ntx + blockIdx.y) * P.n[0] + z] = s2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Driver-parameter gradients from the row sums.
+//
+// A row set j holds, per z, R0 = sum_x c(x) and R2 = sum_x c2(x) for a
+// quantity whose forward value is n_b-like: v(z, x) = L(zeta) T(x) with
+// zeta = z dx + zoff_j - zeta0_j.  Then
+//   dJ/dalpha   += sum R0 exp(-zeta^2 / 2 sigma_z^2)      (Gaussian L)
+//   dJ/dsigma_z += sum R0 L zeta^2 / sigma_z^3           (Gaussian L)
+//   dJ/dsigma_r += sum R2 L
+//   dJ/dprofile_j += sum R0 (interpolation weight of sample j at zeta).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double row_sum(const GradParams& G, int j, int q, int z) {
+  const double* r = G.rows + ((size_t)j * 2 + q) * (size_t)G.ntx * G.n0;
+  double s = 0.0;
+  for (int t = 0; t < G.ntx; ++t) s += r[(size_t)t * G.n0 + z];
+  return s;
+}
+
+__device__ __forceinline__ double glong(const GradParams& G, double zeta) {
+  if (G.profile) {
+    const double s = zeta / G.pdz + 0.5 * (G.plen - 1);
+    if (!(s > -1.0 && s < (double)G.plen)) return 0.0;
+    const int j = (int)floor(s);
+    const double fr = s - j;
+    const double a = j >= 0 ? G.profile[j] : 0.0, b = j + 1 < G.plen ? G.profile[j + 1] : 0.0;
+    return (1.0 - fr) * a + fr * b;
+  }
+  return G.alpha * exp(-zeta * zeta * G.inv2sz2);
+}
+
+// one block of 256 threads per row set: fixed-order tree over z
+__global__ void __launch_bounds__(256) grad_sets_kernel(const GradParams G) {
+  __shared__ double red[3][256];
+  const int j = blockIdx.x;
+  const double zeta0 = G.setp[j].x, zoff = G.setp[j].y;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int z = threadIdx.x; z < G.n0; z += 256) {
+    const double R0 = row_sum(G, j, 0, z), R2 = row_sum(G, j, 1, z);
+    const double zeta = z * G.dx + zoff - zeta0;
+    const double L = glong(G, zeta);
+    if (!G.profile) {
+      const double g = exp(-zeta * zeta * G.inv2sz2);
+      a0 += R0 * g;
+      a1 += R0 * L * zeta * zeta / (G.sigma_z * G.sigma_z * G.sigma_z);
+    }
+    a2 += R2 * L;
+  }
+  red[0][threadIdx.x] = a0;
+  red[1][threadIdx.x] = a1;
+  red[2][threadIdx.x] = a2;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) G.gpart[j * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// sets summed in order into the running gradient (one thread per output)
+__global__ void grad_accum_kernel(const GradParams G) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < 3) {
+    double s = G.g3[q];
+    for (int j = 0; j < G.nsets; ++j) s += G.gpart[j * 3 + q];
+    G.g3[q] = s;
+  }
+  if (G.profile && q < G.plen) {
+    // sample q collects the rows whose zeta interpolates between q-1..q+1
+    double s = G.gp[q];
+    for (int j = 0; j < G.nsets; ++j) {
+      const double zeta0 = G.setp[j].x, zoff = G.setp[j].y;
+      const double zc = ((q - 0.5 * (G.plen - 1)) * G.pdz + zeta0 - zoff) / G.dx;
+      const double span = G.pdz / G.dx + 2.0;
+      int zlo = (int)floor(zc - span), zhi = (int)ceil(zc + span);
+      zlo = zlo < 0 ? 0 : zlo;
+      zhi = zhi > G.n0 - 1 ? G.n0 - 1 : zhi;
+      for (int z = zlo; z <= zhi; ++z) {
+        const double zeta = z * G.dx + zoff - zeta0;
+        const double sv = zeta / G.pdz + 0.5 * (G.plen - 1);
+        if (!(sv > -1.0 && sv < (double)G.plen)) continue;
+        const int jj = (int)floor(sv);
+        const double fr = sv - jj;
+        double wgt = 0.0;
+        if (jj == q) wgt = 1.0 - fr;
+        else if (jj + 1 == q) wgt = fr;
+        if (wgt != 0.0) s += row_sum(G, j, 0, z) * wgt;
+      }
+    }
+    G.gp[q] = s;
+  }
+}
+
+// Initial driver field (2D, v -> c limit): E_x = -L(zeta_E) k(x) at the E_x
+// slot (z + dx/2, t = -dt/2), B_y = -L(zeta_B) k(x) at the node (t = 0),
+// k(x) = sigma_r sqrt(pi/2) erf(x / (sqrt(2) sigma_r)).  Row sets 0 (E) and
+// 1 (B): R0 = sum_x lambda (-k), R2 = sum_x lambda (-dk/dsigma_r).
+template <typename real, int TZ, int TX>
+__global__ void __launch_bounds__(TZ* TX) adj_init_rows_kernel(StepParams P, const real* lE, const real* lB,
+                                                                const double* Kx, double* rows) {
+  __shared__ double red[4][TX][TZ];
+  const int tzi = threadIdx.x % TZ, txi = threadIdx.x / TZ;
+  const int z = blockIdx.x * TZ + tzi, x = blockIdx.y * TX + txi;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (z < P.n[0] && x < P.n[1]) {
+    const int pl = (int)P.plane;
+    const int id = aidx(P, z, x);
+    const double le = (double)lE[pl + id], lb = (double)lB[2 * pl + id];
+    v[0] = le * Kx[x];
+    v[1] = le * Kx[P.n[1] + x];
+    v[2] = lb * Kx[x];
+    v[3] = lb * Kx[P.n[1] + x];
+  }
+  for (int q = 0; q < 4; ++q) red[q][txi][tzi] = v[q];
+  __syncthreads();
+  if (txi == 0 && z < P.n[0]) {
+    const int ntx = gridDim.y;
+    for (int q = 0; q < 4; ++q) {
+      double s = 0.0;
+      for (int t = 0; t < TX; ++t) s += red[q][t][tzi];
+      // set (q / 2), component (q % 2)
+      rows[(((size_t)(q / 2) * 2 + (q % 2)) * ntx + blockIdx.y) * P.n[0] + z] = s;
+    }
+  }
+}
+
+template <typename real>
+__global__ void adj_seed_kernel(real* lE, long long idx, double v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) lE[idx] = real(v);
+}
+
+template <typename real>
+__global__ void read_slot_kernel(const real* E, long long idx, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = (double)E[idx];
+}
+
+}  // namespace lbp

@@ -35,12 +35,12 @@ __device__ __forceinline__ long long padded(const AuxParams& A, const int* e) {
 
 __device__ __forceinline__ double driver_long_d(const AuxParams& A, double zeta) {
   if (A.profile) {
-    double s = zeta / A.pdz + 0.5 * (A.plen - 1);
-    if (s < 0.0 || s > (double)(A.plen - 1)) return 0.0;
-    int j = (int)floor(s);
-    if (j >= A.plen - 1) return A.profile[A.plen - 1];
-    double fr = s - j;
-    return (1.0 - fr) * A.profile[j] + fr * A.profile[j + 1];
+    const double s = zeta / A.pdz + 0.5 * (A.plen - 1);
+    if (!(s > -1.0 && s < (double)A.plen)) return 0.0;
+    const int j = (int)floor(s);
+    const double fr = s - j;
+    const double a = j >= 0 ? A.profile[j] : 0.0, b = j + 1 < A.plen ? A.profile[j + 1] : 0.0;
+    return (1.0 - fr) * a + fr * b;
   }
   return A.alpha * exp(-zeta * zeta * A.inv2sz2);
 }

@@ -152,6 +152,9 @@ struct StepParams {
   float inv_scale[11];   // FP16S: 1/s_k
   float scale[11];       // FP16S: s_k
   int* err;              // device error word (bit 0: a bounded wait gave up)
+  void* tape;            // adjoint recording (1D/2D), or null: this step's
+                         // deviation moments dA [K], E^{n+1/2} [DIM] and
+                         // B^n [present B] as [K + DIM + NB][plane] of real
   StepConst<float> cf;
   StepConst<double> cd;
 };
@@ -283,16 +286,19 @@ __device__ __forceinline__ void decode_lec_f32(float n, const float* Ap, float c
   Pi = x * pow_2_over_D<float>(x, D);
 }
 
-// Driver longitudinal factor L(zeta) (Eq. bunch-density, rms reading).
+// Driver longitudinal factor L(zeta) (Eq. bunch-density, rms reading).  A
+// sampled profile is interpolated linearly with zero samples just outside
+// both ends, so L stays continuous.
 template <typename real>
 __device__ __forceinline__ real driver_long(const StepParams& P, const StepConst<real>& S, real zeta) {
   if (P.profile) {
     const real q = zeta * S.pdz_inv + S.phalf;
-    if (q < real(0) || q > real(P.plen - 1)) return real(0);
+    if (!(q > real(-1) && q < real(P.plen))) return real(0);
     const int j = (int)floor(q);
-    if (j >= P.plen - 1) return real(P.profile[P.plen - 1]);
     const real fr = q - real(j);
-    return (real(1) - fr) * real(P.profile[j]) + fr * real(P.profile[j + 1]);
+    const real a = j >= 0 ? real(P.profile[j]) : real(0);
+    const real b = j + 1 < P.plen ? real(P.profile[j + 1]) : real(0);
+    return (real(1) - fr) * a + fr * b;
   }
   return S.alpha * exp(-zeta * zeta * S.inv2sz2);
 }

@@ -352,6 +352,16 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
     decode_record<DIM, CL, real>(P, S, dA_own, rec);
 #pragma unroll
     for (int m = 0; m < M::NM; ++m) smac[m * NR + r_own] = rec[m];
+    if constexpr (DIM <= 2) {
+      // adjoint recording: the moments this step decodes and B^n
+      if (P.tape != nullptr && own_inside) {
+        real* tp = reinterpret_cast<real*>(P.tape);
+        const int id_own = cell_index32(P, gz, gx, gy);
+#pragma unroll
+        for (int k = 0; k < K; ++k) tp[k * pl + id_own] = dA_own[k];
+        if constexpr (DIM == 2) tp[(K + DIM) * pl + id_own] = F.Bc[2];
+      }
+    }
   }
   // halo ring
   if constexpr (DIM <= 2) {
@@ -451,10 +461,12 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   real* Eout = reinterpret_cast<real*>(P.Eout);
   real* Bout = reinterpret_cast<real*>(P.Bout);
   real En[3] = {0, 0, 0}, Bn[3] = {0, 0, 0};
+  real* tape = reinterpret_cast<real*>(P.tape);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (e_present<DIM>(a)) {
       Eout[a * pl + id] = sE[a * NR + r];
+      if (DIM <= 2 && tape != nullptr) tape[(K + a) * pl + id] = sE[a * NR + r];
       const int b = (a + 1) % 3, d = (a + 2) % 3;
       const bool ob = axis_present<DIM>(b), od = axis_present<DIM>(d);
       const int sb = ob ? C::stride(b) : 0, sd = od ? C::stride(d) : 0;

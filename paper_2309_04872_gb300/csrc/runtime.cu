@@ -20,51 +20,17 @@
 #include "lb_batch_dispatch.h"
 #include "lb_batch_types.cuh"
 #include "lb_dispatch.h"
+#include "lb_runtime.h"
 
 using namespace lbp;
+using namespace lbprt;
 
 namespace {
-
 constexpr int kReduceBlocks = 256;   // fixed: the FP64 sums do not depend on the GPU
 constexpr float kF16Scale = 1024.0f; // binary16 deviations are stored times 2^10
-
-struct Buf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
 }  // namespace
 
-struct lbpwfa_s {
-  lbpwfa_params prm{};
-  std::vector<double> profile_h;
-  double* profile_d = nullptr;
-  KernelSet ks{};
-  int K = 0, Q = 0, NPREV = 0;
-  int n[3] = {1, 1, 1};
-  int nzp = 0;
-  long long plane = 0, ncell = 0;
-  size_t store_sz = 0, real_sz = 0;
-  double dt = 0.0;
-  long long step = 0;
-  int cur = 0;  // index of the buffers holding the current state
-  Buf f[2], E[2], B[2], prev, partial, out3, scratch;
-  int have_prev = 0;
-  cudaStream_t stream = nullptr;
-  bool owns_stream = false;
-  double Arest[11] = {0};
-  float scale[11], inv_scale[11];
-  size_t device_bytes = 0;
-  std::string err;
-  bool use_tma = false;
-  bool use_persist = false;
-  bool in_batch = false;  // owned by a batch: stepped only through lbpwfa_batch_step
-  int num_sms = 0;
-  alignas(64) CUtensorMap maps[2];
-  int* err_d = nullptr;  // device error word written by bounded waits
-};
-
-namespace {
+namespace lbprt {
 
 int fail_cuda(lbpwfa_s* h, cudaError_t e, const char* what) {
   if (h) {
@@ -72,18 +38,6 @@ int fail_cuda(lbpwfa_s* h, cudaError_t e, const char* what) {
   }
   return LBPWFA_ERR_CUDA;
 }
-
-#define CK(h, call)                                       \
-  do {                                                    \
-    cudaError_t e_ = (call);                              \
-    if (e_ != cudaSuccess) return fail_cuda((h), e_, #call); \
-  } while (0)
-
-#define CK_LAUNCH(h, what)                                \
-  do {                                                    \
-    cudaError_t e_ = cudaGetLastError();                  \
-    if (e_ != cudaSuccess) return fail_cuda((h), e_, what); \
-  } while (0)
 
 int alloc(lbpwfa_s* h, Buf& b, size_t bytes) {
   if (bytes == 0) return LBPWFA_OK;
@@ -304,6 +258,7 @@ int init_rest_state(lbpwfa_s* h) {
     h->ks.init_fields(A, h->E[0].p, h->B[0].p, h->stream);
     CK_LAUNCH(h, "init_fields");
   }
+  h->fields_from_driver = h->prm.init_fields && h->prm.dim >= 2;
   h->cur = 0;
   h->step = 0;
   h->have_prev = 0;
@@ -327,7 +282,32 @@ uint32_t crc32_update(uint32_t crc, const void* data, size_t len) {
   return ~crc;
 }
 
-}  // namespace
+// One step of the single-run kernel in use; tape != null records the step's
+// adjoint inputs (lb_step.cuh).
+int launch_step(lbpwfa_s* h, void* tape) {
+  const dim3 grid = h->use_tma ? dim3((unsigned)((h->n[0] + h->ks.tma_tz - 1) / h->ks.tma_tz),
+                                      (unsigned)((h->n[1] + h->ks.tma_tx - 1) / h->ks.tma_tx), 1)
+                               : step_grid(h);
+  StepParams P = step_params(h);
+  P.tape = tape;
+  if (h->use_persist) {
+    const int ntz = (h->n[0] + h->ks.per_tz - 1) / h->ks.per_tz;
+    const int ntiles = ntz * ((h->n[1] + h->ks.per_tx - 1) / h->ks.per_tx);
+    const int pgrid = ntiles < h->num_sms ? ntiles : h->num_sms;
+    h->ks.step_persist(P, &h->maps[h->cur], pgrid, ntz, ntiles, h->stream);
+  } else if (h->use_tma) {
+    h->ks.step_tma(P, &h->maps[h->cur], grid, h->stream);
+  } else {
+    h->ks.step(P, grid, h->stream);
+  }
+  CK_LAUNCH(h, "lb_step_kernel launch");
+  h->cur = 1 - h->cur;
+  h->step += 1;
+  if (h->NPREV) h->have_prev = 1;
+  return LBPWFA_OK;
+}
+
+}  // namespace lbprt
 
 extern "C" {
 
@@ -350,6 +330,7 @@ const char* lbpwfa_last_error(lbpwfa_t h) { return h ? h->err.c_str() : ""; }
 static void destroy_run(lbpwfa_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  adj_free(h);
   for (int j = 0; j < 2; ++j) { release(h->f[j]); release(h->E[j]); release(h->B[j]); }
   release(h->prev);
   release(h->partial);
@@ -491,21 +472,12 @@ int lbpwfa_step(lbpwfa_t h, int64_t nsteps) {
     h->err = "lbpwfa_step: this run belongs to a batch; use lbpwfa_batch_step";
     return LBPWFA_ERR_STATE;
   }
-  const dim3 grid = h->use_tma ? dim3((unsigned)((h->n[0] + h->ks.tma_tz - 1) / h->ks.tma_tz),
-                                      (unsigned)((h->n[1] + h->ks.tma_tx - 1) / h->ks.tma_tx), 1)
-                               : step_grid(h);
-  const int ntz = (h->n[0] + h->ks.per_tz - 1) / (h->ks.per_tz > 0 ? h->ks.per_tz : 1);
-  const int ntiles = ntz * ((h->n[1] + h->ks.per_tx - 1) / (h->ks.per_tx > 0 ? h->ks.per_tx : 1));
-  const int pgrid = ntiles < h->num_sms ? ntiles : h->num_sms;
   for (int64_t s = 0; s < nsteps; ++s) {
-    StepParams P = step_params(h);
-    if (h->use_persist) h->ks.step_persist(P, &h->maps[h->cur], pgrid, ntz, ntiles, h->stream);
-    else if (h->use_tma) h->ks.step_tma(P, &h->maps[h->cur], grid, h->stream);
-    else h->ks.step(P, grid, h->stream);
-    CK_LAUNCH(h, "lb_step_kernel launch");
-    h->cur = 1 - h->cur;
-    h->step += 1;
-    if (h->NPREV) h->have_prev = 1;
+    void* tape = nullptr;
+    int r = adj_before_step(h, &tape);
+    if (r != LBPWFA_OK) return r;
+    r = launch_step(h, tape);
+    if (r != LBPWFA_OK) return r;
   }
   return LBPWFA_OK;
 }
@@ -603,7 +575,9 @@ int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double*
   if (Ed || Bd) {
     h->ks.import_fields(A, Ed, Bd, h->E[h->cur].p, h->B[h->cur].p, h->stream);
     CK_LAUNCH(h, "import_fields_kernel launch");
+    h->fields_from_driver = false;
   }
+  adj_invalidate(h);
   h->have_prev = 0;
   if (!src_is_device) CK(h, cudaStreamSynchronize(h->stream));
   return LBPWFA_OK;
@@ -706,6 +680,7 @@ struct CkptHeader {
   char magic[8];
   int32_t version;
   int32_t dim, n0, n1, n2, closure, dv, precision, boundary, K, Q, have_prev;
+  int32_t from_driver, pad_;  // E, B still the driver's initial fields
   int64_t step;
   double dx, courant, tau, mu, alpha, sigma_z, sigma_r, z0;
   uint64_t pop_bytes, fld_bytes, prev_bytes;
@@ -715,11 +690,12 @@ struct CkptHeader {
 int lbpwfa_save(lbpwfa_t h, const char* path) {
   if (!h || !path) return LBPWFA_ERR_INVALID;
   CkptHeader H{};
-  std::memcpy(H.magic, "LBPWFA01", 8);
+  std::memcpy(H.magic, "LBPWFA02", 8);
   H.version = 1;
   H.dim = h->prm.dim; H.n0 = h->n[0]; H.n1 = h->n[1]; H.n2 = h->n[2];
   H.closure = h->prm.closure; H.dv = h->prm.dv; H.precision = h->prm.precision; H.boundary = h->prm.boundary;
   H.K = h->K; H.Q = h->Q; H.have_prev = h->have_prev; H.step = h->step;
+  H.from_driver = h->fields_from_driver ? 1 : 0;
   H.dx = h->prm.dx; H.courant = h->prm.courant; H.tau = h->prm.tau; H.mu = h->prm.mu;
   H.alpha = h->prm.alpha; H.sigma_z = h->prm.sigma_z; H.sigma_r = h->prm.sigma_r; H.z0 = h->prm.z0;
   H.pop_bytes = h->f[h->cur].bytes; H.fld_bytes = h->E[h->cur].bytes; H.prev_bytes = h->prev.bytes;
@@ -748,7 +724,7 @@ int lbpwfa_load(lbpwfa_t h, const char* path) {
   FILE* fp = std::fopen(path, "rb");
   if (!fp) return LBPWFA_ERR_IO;
   CkptHeader H{};
-  if (std::fread(&H, sizeof(H), 1, fp) != 1 || std::memcmp(H.magic, "LBPWFA01", 8) != 0) {
+  if (std::fread(&H, sizeof(H), 1, fp) != 1 || std::memcmp(H.magic, "LBPWFA02", 8) != 0) {
     std::fclose(fp);
     return LBPWFA_ERR_IO;
   }
@@ -775,8 +751,10 @@ int lbpwfa_load(lbpwfa_t h, const char* path) {
   q += H.fld_bytes;
   if (H.prev_bytes) CK(h, cudaMemcpyAsync(h->prev.p, q, H.prev_bytes, cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  adj_invalidate(h);
   h->step = H.step;
   h->have_prev = H.have_prev;
+  h->fields_from_driver = H.from_driver != 0;
   return LBPWFA_OK;
 }
 

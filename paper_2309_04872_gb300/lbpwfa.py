@@ -62,6 +62,15 @@ class BatchInfo(ctypes.Structure):
                 ("tuned_ms", ctypes.c_double * 4)]
 
 
+class RecordParams(ctypes.Structure):
+    _fields_ = [("max_steps", ctypes.c_int64), ("checkpoint_every", ctypes.c_int64)]
+
+
+class AdjointIO(ctypes.Structure):
+    _fields_ = [("witness", ctypes.c_int * 3), ("seed", ctypes.c_double), ("J", ctypes.c_double),
+                ("grad_driver", ctypes.c_double * 3), ("grad_profile", ctypes.POINTER(ctypes.c_double))]
+
+
 _lib = None
 _DP = ctypes.POINTER(ctypes.c_double)
 EXPORTED = ["lbpwfa_create", "lbpwfa_step", "lbpwfa_moments", "lbpwfa_fields", "lbpwfa_advected",
@@ -69,7 +78,7 @@ EXPORTED = ["lbpwfa_create", "lbpwfa_step", "lbpwfa_moments", "lbpwfa_fields", "
             "lbpwfa_load", "lbpwfa_set_stream", "lbpwfa_synchronize", "lbpwfa_destroy",
             "lbpwfa_status_string", "lbpwfa_last_error", "lbpwfa_reduce_noalloc",
             "lbpwfa_batch_create", "lbpwfa_batch_step", "lbpwfa_batch_member", "lbpwfa_batch_info",
-            "lbpwfa_batch_destroy"]
+            "lbpwfa_batch_destroy", "lbpwfa_record", "lbpwfa_adjoint_step"]
 
 
 def library_path() -> str:
@@ -114,6 +123,8 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbpwfa_batch_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
     L.lbpwfa_batch_destroy.argtypes = [vp]
     L.lbpwfa_batch_destroy.restype = None
+    L.lbpwfa_record.argtypes = [vp, ctypes.POINTER(RecordParams)]
+    L.lbpwfa_adjoint_step.argtypes = [vp, ctypes.POINTER(AdjointIO)]
     _lib = L
     return L
 
@@ -279,6 +290,28 @@ class Run:
 
     def load(self, path: str):
         self._check(load_library().lbpwfa_load(self._h, path.encode()), "lbpwfa_load")
+
+    def record(self, max_steps: int, checkpoint_every: int = 0):
+        """Start an adjoint recording window of up to max_steps steps
+        (checkpoint_every = 0 keeps every step's tape)."""
+        rp = RecordParams(int(max_steps), int(checkpoint_every))
+        self._check(load_library().lbpwfa_record(self._h, ctypes.byref(rp)), "lbpwfa_record")
+
+    def adjoint(self, witness, seed: float = 1.0):
+        """Reverse sweep over the recorded window: returns (J, dL/d(alpha,
+        sigma_z, sigma_r), dL/d(profile samples) or None) for J = E_z at the
+        witness node's slot and L = seed J."""
+        io = AdjointIO()
+        w = list(witness) + [0, 0]
+        for a in range(3):
+            io.witness[a] = int(w[a])
+        io.seed = float(seed)
+        gp = None
+        if self._keep is not None:
+            gp = np.zeros(self._keep.size)
+            io.grad_profile = gp.ctypes.data_as(_DP)
+        self._check(load_library().lbpwfa_adjoint_step(self._h, ctypes.byref(io)), "lbpwfa_adjoint_step")
+        return float(io.J), np.array([io.grad_driver[q] for q in range(3)]), gp
 
 
 class _Member(Run):

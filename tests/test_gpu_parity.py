@@ -152,6 +152,26 @@ def test_fp64_driver_from_rest_parity(dim, closure):
         _compare(run, orc, 1e-12, label="driver")
 
 
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+@pytest.mark.parametrize("dz", [0.0317, 0.025])
+def test_fp64_profile_driver_parity(dim, closure, dz):
+    """Sampled-profile driver (linear interpolation, zero samples just
+    outside both ends), including the initial fields it induces.  The
+    profile is cut off where it is still 0.14 of its peak, so its ends are
+    exercised."""
+    zs = (np.arange(61) - 30) * dz
+    prof = 0.2 * np.exp(-zs ** 2 / (2 * 0.4 ** 2))
+    cfg = _cfg(dim, closure, "open", profile=prof, profile_dz=dz)
+    orc = O.Oracle(cfg)
+    with lb.Run(cfg, "fp64") as run:
+        _compare(run, orc, 1e-12, label="t0")
+        nsteps = 30 if dim == 3 else 100
+        orc.step(nsteps)
+        run.step(nsteps)
+        _compare(run, orc, 1e-12, label="profile")
+
+
 def test_fp64_config1_full_run_matches_oracle():
     """1D, 2048 cells over 40 k_p^-1, C = 0.5, LEC D = 1, mu = 1e-3,
     alpha = 0.01, sigma_z = 1, z0 = -5, 4000 steps."""

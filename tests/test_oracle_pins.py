@@ -307,6 +307,33 @@ def test_driver_normalised_charge():
     assert np.isclose(O.driver_density(cfg, 3.0, t=3.0), 0.01)
 
 
+def test_driver_profile_reading():
+    """Sampled profile: samples at zeta_j = (j - (len-1)/2) dz, linear between
+    them, zero samples just outside both ends (continuous).  The values below
+    follow from that definition by hand; a profile equal to the Gaussian at
+    fine spacing reproduces the Gaussian's charge."""
+    prof = np.array([1.0, 3.0, 2.0, 5.0])
+    cfg = dict(dim=1, n=(8,), dx=0.1, courant=0.5, tau=0.52, profile=prof, profile_dz=0.5, z0=0.0)
+    # sample positions -0.75, -0.25, 0.25, 0.75
+    for j, zj in enumerate([-0.75, -0.25, 0.25, 0.75]):
+        assert O.driver_density(cfg, zj) == prof[j]
+    assert O.driver_density(cfg, 0.0) == 2.5              # midway between 3 and 2
+    assert O.driver_density(cfg, -0.5) == 2.0             # midway between 1 and 3
+    assert O.driver_density(cfg, -1.0) == 0.5             # half a sample below the first: half of 1
+    assert O.driver_density(cfg, 1.0) == 2.5              # half a sample above the last: half of 5
+    assert O.driver_density(cfg, -1.25) == 0.0 and O.driver_density(cfg, 1.25) == 0.0
+    assert O.driver_density(cfg, 7.0) == 0.0
+    # moves with the driver
+    assert O.driver_density(dict(cfg, z0=2.0), 2.25 + 1.5, t=1.5) == 2.0
+    # a finely sampled Gaussian carries the Gaussian's charge
+    dz = 0.01
+    zs = (np.arange(1601) - 800) * dz
+    cfgg = dict(cfg, profile=0.01 * np.exp(-zs ** 2 / 2), profile_dz=dz)
+    z = np.linspace(-9, 9, 18001)
+    Q = np.trapezoid(np.array([O.driver_density(cfgg, zz) for zz in z]), z)
+    assert abs(Q - np.sqrt(2 * np.pi) * 0.01) < 1e-9
+
+
 # ---------------------------------------------------------------------------
 # 1D wake against the linear closed form (App. B, eq. fhow, in 1D):
 # (1 - c_s^2) n1'' + a^2 n1 = -a^2 n_b, far behind the driver
