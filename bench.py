@@ -48,6 +48,11 @@ CONFIG_1D = dict(dim=1, n=(2048,), dx=40 / 2048, courant=0.5, tau=0.52, closure=
 # the 3D configuration: 512 (z) x 256 x 256, warm-plasma closure
 CONFIG_3D = dict(dim=3, n=(512, 256, 256), dx=0.05, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=1e-2,
                  alpha=1.0, sigma_z=0.7, sigma_r=0.3, z0=2.8, boundary="open", init_fields=True)
+# the adjoint configuration: 2D 512 (z) x 256 (x) WARMC, 1000 steps, J = E_z on
+# axis at 4 k_p^-1 behind the driver centre at the end
+CONFIG_ADJ = dict(dim=2, n=(512, 256), dx=0.05, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=5e-3,
+                  alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=4.0, boundary="open", init_fields=True)
+ADJ_STEPS = 1000
 
 
 def _args():
@@ -57,9 +62,12 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
-    ap.add_argument("--workload", default="2d_lec", choices=["2d_lec", "3d_warmc", "3d_warmc_128"],
+    ap.add_argument("--workload", default="2d_lec",
+                    choices=["2d_lec", "3d_warmc", "3d_warmc_128", "adjoint_2d_warmc"],
                     help="2d_lec: 1024 x 512 LEC (default); 3d_warmc: 512 x 256 x 256 WARMC; "
-                         "3d_warmc_128: 128^3 WARMC (small case for profiling)")
+                         "3d_warmc_128: 128^3 WARMC (small case for profiling); adjoint_2d_warmc: "
+                         "forward + reverse sweep of the 512 x 256 WARMC adjoint case over --steps steps "
+                         "(whole tape kept), for profiling")
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="0: automatic (TMA box per CTA in 2D), 1: plain global-memory pull kernel, "
                          "2: TMA box per CTA, 3: persistent CTAs with two TMA boxes in flight")
@@ -68,6 +76,7 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 1D and 3D configuration measurements")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint cost and gradient check")
     return ap.parse_args()
 
 
@@ -216,6 +225,33 @@ def _oracle_sample(cfg, budget_s=15.0):
     return ncell * nsteps / dt / 1e6, nsteps, dt
 
 
+def run_adjoint_case(a):
+    """Forward steps with recording and the reverse sweep of the adjoint
+    configuration, --steps steps (after --warmup forward steps), whole tape
+    kept; prints the timings as one JSON line."""
+    import torch
+
+    from paper_2309_04872_gb300 import lbpwfa as lb
+    cfg = dict(CONFIG_ADJ)
+    N = a.steps
+    stream = torch.cuda.Stream()
+    with lb.Run(cfg, a.precision, stream=stream.cuda_stream, variant=a.variant) as run:
+        run.step(a.warmup)
+        wit = _adj_witness(cfg, a.warmup + N, run.info().dt)
+        run.record(N, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run.step(N)
+        run.synchronize()
+        t1 = time.perf_counter()
+        J, g, _ = run.adjoint(wit)
+        t2 = time.perf_counter()
+    print(json.dumps({"metric": "adjoint sweep timing", "workload": "adjoint_2d_warmc_512x256", "steps": N,
+                      "precision": a.precision, "variant": a.variant, "forward_recording_ms": round((t1 - t0) * 1e3, 3),
+                      "reverse_ms": round((t2 - t1) * 1e3, 3), "J": J, "grad": [float(v) for v in g]}),
+          flush=True)
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -322,6 +358,9 @@ def run_ours(a):
     if rank == 0 and not a.no_configs and a.workload == "2d_lec":
         out["configs_measured"] = _configs(stream, flush, hbm)
 
+    if rank == 0 and not a.no_adjoint and a.workload == "2d_lec":
+        out["adjoint"] = _adjoint(stream)
+
     if rank == 0 and not a.no_e2e:
         out["e2e"] = _e2e(cfg, a, world)
 
@@ -422,6 +461,108 @@ def _configs(stream, flush, hbm):
     return res
 
 
+def _adj_witness(cfg, nsteps, dt):
+    """On-axis E_z slot 4 k_p^-1 behind the driver centre at t_{N-1/2}
+    (the time of the stored E)."""
+    zc = cfg["z0"] + (nsteps - 0.5) * dt
+    return (int(round((zc - 4.0) / cfg["dx"])), cfg["n"][1] // 2 - 1)
+
+
+def _adjoint(stream):
+    """Cost of forward + reverse sweep against the forward alone (FP32
+    storage), with checkpoints every 50 steps and with the whole tape kept,
+    and the gradient against central differences of the FP64 path."""
+    import torch
+
+    from paper_2309_04872_gb300 import lbpwfa as lb
+    cfg = dict(CONFIG_ADJ)
+    N = ADJ_STEPS
+    sc = stream.cuda_stream
+    res = {"config": "2d_warmc_512x256_fp32_1000steps", "steps": N}
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    with lb.Run(cfg, "fp32", stream=sc) as run:
+        dt = run.info().dt
+    wit = _adj_witness(cfg, N, dt)
+    res["witness"] = list(wit)
+
+    def fwd():
+        with lb.Run(cfg, "fp32", stream=sc) as run:
+            run.step(N)
+            run.synchronize()
+
+    def fwd_adj(C):
+        with lb.Run(cfg, "fp32", stream=sc) as run:
+            run.record(N, C)
+            run.step(N)
+            return run.adjoint(wit)
+
+    fwd()
+    fwd_adj(50)  # warm-up (allocations, module load)
+    t_f = min(wall(fwd)[0] for _ in range(3))
+    t_c, (J32, g32, _) = min((wall(lambda: fwd_adj(50)) for _ in range(3)), key=lambda r: r[0])
+    t_t, (J32t, g32t, _) = min((wall(lambda: fwd_adj(0)) for _ in range(3)), key=lambda r: r[0])
+    res["forward_ms"] = round(t_f * 1e3, 2)
+    res["forward_plus_adjoint_ms_checkpoint50"] = round(t_c * 1e3, 2)
+    res["forward_plus_adjoint_ms_whole_tape"] = round(t_t * 1e3, 2)
+    res["cost_ratio_checkpoint50"] = round(t_c / t_f, 3)
+    res["cost_ratio_whole_tape"] = round(t_t / t_f, 3)
+    res["target_ratio"] = 3.0
+    res["note"] = ("wall time of (forward steps + recording + reverse sweep) / wall time of the same forward "
+                   "steps alone; run creation included in both")
+    res["J_fp32"] = J32
+    res["grad_fp32"] = [float(v) for v in g32]
+    res["checkpoint_equals_tape"] = bool(J32 == J32t and np.array_equal(g32, g32t))
+
+    def J64(c):
+        with lb.Run(c, "fp64", stream=sc) as run:
+            run.step(N)
+            ez = run.fields(lb.F_EZ)[0]
+        return float(ez[wit[0] + c["n"][0] * wit[1]])
+
+    with lb.Run(cfg, "fp64", stream=sc) as run:
+        run.record(N, 50)
+        run.step(N)
+        J64v, g64, _ = run.adjoint(wit)
+    fd = []
+    for k, name in enumerate(["alpha", "sigma_z", "sigma_r"]):
+        h = 1e-4 * cfg[name]
+        fd.append((J64(dict(cfg, **{name: cfg[name] + h})) - J64(dict(cfg, **{name: cfg[name] - h}))) / (2 * h))
+    fd = np.array(fd)
+    res["J_fp64"] = J64v
+    res["grad_fp64"] = [float(v) for v in g64]
+    res["fd_fp64_h1e-4"] = [float(v) for v in fd]
+    res["rel_err_fp32_adjoint_vs_fd"] = [float(v) for v in np.abs(g32 - fd) / np.abs(fd)]
+    res["rel_err_fp64_adjoint_vs_fd"] = [float(v) for v in np.abs(g64 - fd) / np.abs(fd)]
+    # the 256-sample profile (dz = 0.05, the Gaussian), FP32 adjoint vs FP64
+    # central differences on four samples around the peak
+    zs = (np.arange(256) - 127.5) * 0.05
+    prof = cfg["alpha"] * np.exp(-zs ** 2 / (2 * cfg["sigma_z"] ** 2))
+    cp = dict(cfg, profile=prof, profile_dz=0.05)
+    with lb.Run(cp, "fp32", stream=sc) as run:
+        run.record(N, 50)
+        run.step(N)
+        _, gsr, gp = run.adjoint(wit)
+    errs = []
+    scale = float(np.abs(gp).max())
+    for j in (112, 124, 128, 140):
+        h = 1e-4 * cfg["alpha"]
+        pp, pm = prof.copy(), prof.copy()
+        pp[j] += h
+        pm[j] -= h
+        fdj = (J64(dict(cp, profile=pp)) - J64(dict(cp, profile=pm))) / (2 * h)
+        errs.append({"sample": j, "adjoint_fp32": float(gp[j]), "fd_fp64": fdj,
+                     "rel_err_of_max": abs(gp[j] - fdj) / scale})
+    res["profile_samples"] = errs
+    return res
+
+
 def _e2e(cfg, a, world):
     """Same metric through the public C ABI with host buffers: upload of the
     initial state from pinned host memory, K steps, read-back of n and E_z."""
@@ -494,5 +635,7 @@ if __name__ == "__main__":
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "adjoint_2d_warmc":
+        run_adjoint_case(args)
     else:
         run_ours(args)

@@ -101,11 +101,13 @@ typedef struct {
                               (2D, 3D); 0: zero fields */
   void* stream;            /* cudaStream_t to queue work on; NULL = a stream
                               owned by the library */
-  int kernel_variant;      /* 0: automatic (2D open-boundary runs stage each
-                              tile's populations in shared memory with one
-                              TMA bulk-tensor load per CTA; the rest pull
-                              from global memory); 1: plain global-memory
-                              pull; 2: one TMA box per CTA (as 0 for 2D);
+  int kernel_variant;      /* 0: automatic (2D open-boundary LEC runs stage
+                              each tile's populations in shared memory with
+                              one TMA bulk-tensor load per CTA; the rest,
+                              WARMC included, pull from global memory, which
+                              measures faster for its 72 population planes);
+                              1: plain global-memory pull; 2: one TMA box per
+                              CTA (2D open boundaries);
                               3: LEC 2D with one persistent CTA per SM and two
                               TMA boxes in flight.  All compute the same step. */
 } lbpwfa_params;

@@ -70,49 +70,90 @@ __device__ __forceinline__ Pre preimage(int c, int n, int delta, int periodic) {
   return r;
 }
 
-// Adjoint of the post-collision population (k, i) of node (z, x): the sum of
-// the next state's population adjoints of every node that pulls it.  Node y
-// pulls f*_i(bulk(y) - xi_i); with open boundaries the boundary nodes copy
-// their nearest bulk node, so a bulk target also collects their adjoints.
+// Adjoints of the post-collision populations of set k at node (z, x): for
+// velocity i, the sum of the next state's population adjoints of every node
+// that pulls it.  Node y pulls f*_i(bulk(y) - xi_i); with open boundaries the
+// boundary nodes copy their nearest bulk node, so a bulk target also
+// collects their adjoints.  EDGE = false promises that (z, x) lies at least
+// three nodes inside the grid, so no boundary rule applies and the Q loads
+// are issued back to back.
 template <int DIM, typename real>
-__device__ __forceinline__ real lfs_get(const StepParams& P, const real* lfk, int i, int z, int x, bool edge) {
+__device__ __forceinline__ void edge_lfs(const StepParams& P, const real* lfk, int z, int x,
+                                         real (&l)[Lattice<DIM>::Q]);
+
+template <int DIM, bool EDGE, typename real>
+__device__ __forceinline__ void load_lfs(const StepParams& P, const real* lfk, int z, int x,
+                                         real (&l)[Lattice<DIM>::Q]) {
   using L = Lattice<DIM>;
+  constexpr int Q = L::Q;
   const int pl = (int)P.plane;
-  const real* b = lfk + (size_t)i * pl;
-  int yz = z + L::c(i, 0), yx = DIM >= 2 ? x + L::c(i, 1) : 0;
-  if (!edge) return b[aidx(P, yz, yx)];
-  if (P.periodic) {
-    yz = wrap_or_clamp(yz, P.n[0], 1);
-    if (DIM >= 2) yx = wrap_or_clamp(yx, P.n[1], 1);
-    return b[aidx(P, yz, yx)];
-  }
-  if (yz < 1 || yz > P.n[0] - 2) return real(0);
-  if (DIM >= 2 && (yx < 1 || yx > P.n[1] - 2)) return real(0);
-  int cz[3] = {yz, -1, -1}, cx[3] = {yx, -1, -1};
-  if (yz == 1) cz[1] = 0;
-  if (yz == P.n[0] - 2) cz[2] = P.n[0] - 1;
-  if (DIM >= 2) {
-    if (yx == 1) cx[1] = 0;
-    if (yx == P.n[1] - 2) cx[2] = P.n[1] - 1;
-  }
-  real s = 0;
+  if constexpr (!EDGE) {
+    const real* b = lfk + aidx(P, z, x);
 #pragma unroll
-  for (int qz = 0; qz < 3; ++qz) {
-    if (cz[qz] < 0) continue;
-#pragma unroll
-    for (int qx = 0; qx < (DIM >= 2 ? 3 : 1); ++qx) {
-      if (cx[qx] < 0) continue;
-      s += b[aidx(P, cz[qz], cx[qx])];
-    }
+    for (int i = 0; i < Q; ++i) l[i] = __ldg(b + i * pl + L::c(i, 0) + (DIM >= 2 ? L::c(i, 1) * P.nzp : 0));
+  } else {
+    edge_lfs<DIM, real>(P, lfk, z, x, l);
   }
-  return s;
 }
 
-// Node not within reach of a boundary rule for the population gather.
-template <int DIM>
-__device__ __forceinline__ bool gather_interior(const StepParams& P, int z, int x) {
-  bool in = z >= 3 && z <= P.n[0] - 4;
-  if (DIM >= 2) in = in && x >= 3 && x <= P.n[1] - 4;
+// The boundary-aware form of load_lfs.
+template <int DIM, typename real>
+__device__ __forceinline__ void edge_lfs(const StepParams& P, const real* lfk, int z, int x,
+                                         real (&l)[Lattice<DIM>::Q]) {
+  using L = Lattice<DIM>;
+  constexpr int Q = L::Q;
+  const int pl = (int)P.plane;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const real* b = lfk + (size_t)i * pl;
+    int yz = z + L::c(i, 0), yx = DIM >= 2 ? x + L::c(i, 1) : 0;
+    if (P.periodic) {
+      yz = wrap_or_clamp(yz, P.n[0], 1);
+      if (DIM >= 2) yx = wrap_or_clamp(yx, P.n[1], 1);
+      l[i] = b[aidx(P, yz, yx)];
+      continue;
+    }
+    real s = 0;
+    const bool in = yz >= 1 && yz <= P.n[0] - 2 && (DIM < 2 || (yx >= 1 && yx <= P.n[1] - 2));
+    if (in) {
+      int cz[3] = {yz, -1, -1}, cx[3] = {yx, -1, -1};
+      if (yz == 1) cz[1] = 0;
+      if (yz == P.n[0] - 2) cz[2] = P.n[0] - 1;
+      if (DIM >= 2) {
+        if (yx == 1) cx[1] = 0;
+        if (yx == P.n[1] - 2) cx[2] = P.n[1] - 1;
+      }
+#pragma unroll
+      for (int qz = 0; qz < 3; ++qz) {
+        if (cz[qz] < 0) continue;
+#pragma unroll
+        for (int qx = 0; qx < (DIM >= 2 ? 3 : 1); ++qx) {
+          if (cx[qx] < 0) continue;
+          s += b[aidx(P, cz[qz], cx[qx])];
+        }
+      }
+    }
+    l[i] = s;
+  }
+}
+
+// Source of the next state's population adjoints for the gather.
+template <int DIM, bool EDGE, typename real>
+struct GlobalLSrc {
+  const StepParams& P;
+  const real* lf;
+  __device__ __forceinline__ void load(int k, int z, int x, real (&l)[Lattice<DIM>::Q]) const {
+    load_lfs<DIM, EDGE, real>(P, lf + (size_t)k * Lattice<DIM>::Q * P.plane, z, x, l);
+  }
+};
+
+// Whether every node of the block's tile lies three or more nodes inside
+// the grid (no boundary rule in the population gather).
+template <int DIM, int TZ, int TX>
+__device__ __forceinline__ bool block_interior(const StepParams& P) {
+  const int z0 = blockIdx.x * TZ, x0 = blockIdx.y * TX;
+  bool in = z0 >= 3 && z0 + TZ - 1 <= P.n[0] - 4;
+  if (DIM >= 2) in = in && x0 >= 3 && x0 + TX - 1 <= P.n[1] - 4;
   return in;
 }
 
@@ -259,17 +300,14 @@ __device__ __forceinline__ void decode_adjoint(const StepParams& P, const StepCo
 // ---------------------------------------------------------------------------
 // Kernel 1: streaming, collision and local source adjoints.
 // ---------------------------------------------------------------------------
-template <int DIM, int CL, typename real, int TZ, int TX>
-__global__ void __launch_bounds__(TZ* TX) adj_local_kernel(const AdjParams A) {
+template <int DIM, int CL, typename real, class LSrc>
+__device__ __forceinline__ void adj_local_node(const AdjParams& A, const LSrc& src, int z, int x) {
   using M = Model<DIM, CL>;
   using AM = AdjModel<DIM, CL>;
   using L = Lattice<DIM>;
   constexpr int K = M::K, Q = L::Q;
   const StepParams& P = A.P;
   const StepConst<real>& S = consts<real>(P);
-  const int z = blockIdx.x * TZ + threadIdx.x % TZ;
-  const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
-  if (z >= P.n[0] || (DIM >= 2 && x >= P.n[1])) return;
   const int pl = (int)P.plane;
   const int id = aidx(P, z, x);
   const real* tp = reinterpret_cast<const real*>(A.tape);
@@ -283,43 +321,6 @@ __global__ void __launch_bounds__(TZ* TX) adj_local_kernel(const AdjParams A) {
 
   LMac<real> lm;
   lm.zero();
-
-  // ---- streaming + collision adjoint --------------------------------------
-  // fs = f (1 - 1/tau) + f^eq(A, C u)/tau + w dt F with
-  // f^eq = w A (1 + 3 cu + 9/2 cu^2 - 3/2 u^2):
-  //   lambda_A += sum_i w_i (1 + P_i) lambda_fs / tau
-  //   lambda_u += sum_i w_i A C (3 xi + 9 cu xi - 3 u) lambda_fs / tau
-  //   lambda_F  = dt sum_i w_i lambda_fs
-  const bool edge = !gather_interior<DIM>(P, z, x);
-  real ul[3] = {0, 0, 0}, usq = 0;
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) { ul[a] = S.courant * u[a]; usq += ul[a] * ul[a]; }
-  const real* lf = reinterpret_cast<const real*>(A.lf_in);
-  real lA[K], lF[K], lu_c[3] = {0, 0, 0};
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const real* lfk = lf + (size_t)k * Q * pl;
-    real m0 = 0, mA = 0, mu_[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const real l = lfs_get<DIM, real>(P, lfk, i, z, x, edge);
-      const real wl = real(L::w(i)) * l;
-      real cu = 0;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) cu += real(L::c(i, a)) * ul[a];
-      m0 += wl;
-      mA += wl * (real(1) + real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq);
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) mu_[a] += wl * (real(L::c(i, a)) * (real(3) + real(9) * cu) - real(3) * ul[a]);
-    }
-    const real Ak = S.Arest[k] + N.dA[k];
-    lA[k] = mA * S.inv_tau;
-    lF[k] = S.dt * m0;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) lu_c[a] += Ak * mu_[a];
-  }
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) lm.u[a] += lu_c[a] * S.courant * S.inv_tau;
 
   // ---- fields at the node (E^{n+1/2}, B^n from the tape) -------------------
   const real* tE = tp + K * pl;
@@ -337,6 +338,103 @@ __global__ void __launch_bounds__(TZ* TX) adj_local_kernel(const AdjParams A) {
     En[1] = real(0.5) * (tE[pl + id] + tE[pl + aidx(P, zm, x)]);
     Bn[2] = tp[(K + DIM) * pl + id];
   }
+
+  // ---- WARMC: values of the sources' time and space derivatives ------------
+  const int hp = P.have_prev;
+  real th0[3] = {0, 0, 0}, w[3] = {0, 0, 0}, dw[3] = {0, 0, 0};
+  real gw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  if constexpr (CL == CL_WARMC) {
+    const real lam = N.rec[M::R_LAM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { th0[a] = N.rec[M::R_TH0 + a]; w[a] = lam * u[a]; }
+    // previous-step w (backward time difference)
+    if (hp) {
+      real wp[3] = {0, 0, 0};
+      if (A.tape_prev) {
+        Node<DIM, CL, real> Np;
+        load_node<DIM, CL, real>(P, reinterpret_cast<const real*>(A.tape_prev), id, Np);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) wp[a] = Np.rec[M::R_LAM] * Np.rec[M::R_U + a];
+      } else {
+        const real* p0 = reinterpret_cast<const real*>(A.prev0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) wp[a] = p0[(1 + DIM + a) * pl + id];
+      }
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) dw[a] = (w[a] - wp[a]) * S.idt;
+    }
+    // gradients of w from the neighbours' decode
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const int ck = k == 0 ? z : x;
+      const int cp = wrap_or_clamp(ck + 1, P.n[k], P.periodic), cm = wrap_or_clamp(ck - 1, P.n[k], P.periodic);
+      const int idp = k == 0 ? aidx(P, cp, x) : aidx(P, z, cp);
+      const int idm = k == 0 ? aidx(P, cm, x) : aidx(P, z, cm);
+      // w^a = lambda u^a of the neighbours, as their records give it
+      const real np_ = real(1) + tp[idp], nm_ = real(1) + tp[idm];
+      const real nlp = S.Arest[1] + tp[pl + idp], nlm = S.Arest[1] + tp[pl + idm];
+      const real lamp = nlp / np_, lamm = nlm / nm_;
+      const real inlp = real(1) / nlp, inlm = real(1) / nlm;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a)
+        gw[a][k] = (lamp * (tp[(2 + a) * pl + idp] * inlp) - lamm * (tp[(2 + a) * pl + idm] * inlm)) * S.i2dx;
+    }
+    // adjoints of the previous-step values this step wrote
+    if (A.lp_in) {
+      const real* lpi = reinterpret_cast<const real*>(A.lp_in);
+      lm.th00 += lpi[id];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        lm.th0[a] += lpi[(1 + a) * pl + id];
+        lm.w[a] += lpi[(1 + DIM + a) * pl + id];
+      }
+    }
+  }
+
+  // ---- streaming + collision adjoint --------------------------------------
+  // fs = f (1 - 1/tau) + f^eq(A, C u)/tau + w dt F with
+  // f^eq = w A (1 + 3 cu + 9/2 cu^2 - 3/2 u^2):
+  //   lambda_A += sum_i w_i (1 + P_i) lambda_fs / tau
+  //   lambda_u += sum_i w_i A C (3 xi + 9 cu xi - 3 u) lambda_fs / tau
+  //   lambda_F  = dt sum_i w_i lambda_fs
+  real ul[3] = {0, 0, 0}, usq = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { ul[a] = S.courant * u[a]; usq += ul[a] * ul[a]; }
+  // opposite velocities (i, i + 1) share w_i and |cu|: with s = l_i + l_j and
+  // d = l_i - l_j the even part carries 1 + 9/2 cu^2 - 3/2 u^2, the odd 3 cu
+  static_assert(opposite_pairs<DIM>(), "lattice order must pair opposite velocities");
+  real lA[K], lF[K], lu_c[3] = {0, 0, 0};
+  const real even0 = real(1) - real(1.5) * usq;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    real lk[Q];
+    src.load(k, z, x, lk);
+    const real w0l = real(L::w(0)) * lk[0];
+    real m0 = w0l, mA = w0l * even0, mu_[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) mu_[a] = -real(3) * ul[a] * w0l;
+#pragma unroll
+    for (int q = 0; q < (Q - 1) / 2; ++q) {
+      const int i = 1 + 2 * q;
+      const real wi = real(L::w(i));
+      const real sp = wi * (lk[i] + lk[i + 1]), dm = wi * (lk[i] - lk[i + 1]);
+      real cu = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) cu += real(L::c(i, a)) * ul[a];
+      m0 += sp;
+      mA += sp * (even0 + real(4.5) * cu * cu) + real(3) * cu * dm;
+      const real t = real(3) * dm + real(9) * cu * sp;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) mu_[a] += real(L::c(i, a)) * t - real(3) * ul[a] * sp;
+    }
+    const real Ak = S.Arest[k] + N.dA[k];
+    lA[k] = mA * S.inv_tau;
+    lF[k] = S.dt * m0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) lu_c[a] += Ak * mu_[a];
+  }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) lm.u[a] += lu_c[a] * S.courant * S.inv_tau;
 
   // ---- source adjoint, local terms ----------------------------------------
   real lEn[3] = {0, 0, 0}, lBn[3] = {0, 0, 0};
@@ -368,53 +466,6 @@ __global__ void __launch_bounds__(TZ* TX) adj_local_kernel(const AdjParams A) {
       lorentz(a, lF[1 + a]);
     }
   } else {
-    const int hp = P.have_prev;
-    const real lam = N.rec[M::R_LAM];
-    real th0[3] = {0, 0, 0}, w[3] = {0, 0, 0};
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) { th0[a] = N.rec[M::R_TH0 + a]; w[a] = lam * u[a]; }
-    // previous-step w (backward time difference)
-    real dw[3] = {0, 0, 0};
-    if (hp) {
-      real wp[3] = {0, 0, 0};
-      if (A.tape_prev) {
-        Node<DIM, CL, real> Np;
-        load_node<DIM, CL, real>(P, reinterpret_cast<const real*>(A.tape_prev), id, Np);
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) wp[a] = Np.rec[M::R_LAM] * Np.rec[M::R_U + a];
-      } else {
-        const real* p0 = reinterpret_cast<const real*>(A.prev0);
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) wp[a] = p0[(1 + DIM + a) * pl + id];
-      }
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) dw[a] = (w[a] - wp[a]) * S.idt;
-    }
-    // gradients of w from the neighbours' decode
-    real gw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      const int ck = k == 0 ? z : x;
-      const int cp = wrap_or_clamp(ck + 1, P.n[k], P.periodic), cm = wrap_or_clamp(ck - 1, P.n[k], P.periodic);
-      const int idp = k == 0 ? aidx(P, cp, x) : aidx(P, z, cp);
-      const int idm = k == 0 ? aidx(P, cm, x) : aidx(P, z, cm);
-      Node<DIM, CL, real> Np, Nm;
-      load_node<DIM, CL, real>(P, tp, idp, Np);
-      load_node<DIM, CL, real>(P, tp, idm, Nm);
-#pragma unroll
-      for (int a = 0; a < DIM; ++a)
-        gw[a][k] = (Np.rec[M::R_LAM] * Np.rec[M::R_U + a] - Nm.rec[M::R_LAM] * Nm.rec[M::R_U + a]) * S.i2dx;
-    }
-    // adjoints of the previous-step values this step wrote
-    if (A.lp_in) {
-      const real* lpi = reinterpret_cast<const real*>(A.lp_in);
-      lm.th00 += lpi[id];
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        lm.th0[a] += lpi[(1 + a) * pl + id];
-        lm.w[a] += lpi[(1 + DIM + a) * pl + id];
-      }
-    }
     // F_{n lambda} = -d_t th00 - d_k th0k - n E.u
     {
       const real l = lF[1];
@@ -498,6 +549,20 @@ __global__ void __launch_bounds__(TZ* TX) adj_local_kernel(const AdjParams A) {
   }
 }
 
+template <int DIM, int CL, typename real, int TZ, int TX>
+__global__ void __launch_bounds__(TZ* TX) adj_local_kernel(const AdjParams A) {
+  const StepParams& P = A.P;
+  const int z = blockIdx.x * TZ + threadIdx.x % TZ;
+  const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
+  const real* lf = reinterpret_cast<const real*>(A.lf_in);
+  if (block_interior<DIM, TZ, TX>(P)) {
+    adj_local_node<DIM, CL, real>(A, GlobalLSrc<DIM, false, real>{P, lf}, z, x);
+  } else {
+    if (z >= P.n[0] || (DIM >= 2 && x >= P.n[1])) return;
+    adj_local_node<DIM, CL, real>(A, GlobalLSrc<DIM, true, real>{P, lf}, z, x);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Kernel 2: field adjoints, gradient-stencil gathers, decode adjoint and the
 // population adjoint of the previous state.
@@ -543,21 +608,32 @@ __device__ __forceinline__ real lEn_slot(const AdjParams& A, int a, int sz, int 
   }
 }
 
-template <int DIM, int CL, typename real, int TZ, int TX>
-__global__ void __launch_bounds__(TZ* TX) adj_field_kernel(const AdjParams A) {
+// Per-row partial sums of the driver-gradient weights of the block's tile.
+template <int TZ, int TX>
+__device__ __forceinline__ void row_partials(const AdjParams& A, double (&red)[2][TX][TZ], int tzi, int txi, int z,
+                                             double r0, double r2) {
+  red[0][txi][tzi] = r0;
+  red[1][txi][tzi] = r2;
+  __syncthreads();
+  if (txi == 0 && z < A.P.n[0]) {
+    double s0 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int t = 0; t < TX; ++t) { s0 += red[0][t][tzi]; s2 += red[1][t][tzi]; }
+    const int ntx = gridDim.y;
+    A.rows[(size_t)blockIdx.y * A.P.n[0] + z] = s0;
+    A.rows[((size_t)ntx + blockIdx.y) * A.P.n[0] + z] = s2;
+  }
+}
+
+template <int DIM, int CL, typename real, class LSrc>
+__device__ __forceinline__ void adj_field_node(const AdjParams& A, const LSrc& src, int z, int x, double& r0,
+                                               double& r2) {
   using M = Model<DIM, CL>;
-  using AM = AdjModel<DIM, CL>;
   using L = Lattice<DIM>;
   constexpr int K = M::K, Q = L::Q;
   const StepParams& P = A.P;
   const StepConst<real>& S = consts<real>(P);
-  __shared__ double red[2][TX][TZ];
-  const int tzi = threadIdx.x % TZ, txi = threadIdx.x / TZ;
-  const int z = blockIdx.x * TZ + tzi;
-  const int x = DIM >= 2 ? blockIdx.y * TX + txi : 0;
-  const bool inside = z < P.n[0] && (DIM < 2 || x < P.n[1]);
-  double r0 = 0.0, r2 = 0.0;
-  if (inside) {
+  {
     const int pl = (int)P.plane;
     const int id = aidx(P, z, x);
     const real* tp = reinterpret_cast<const real*>(A.tape);
@@ -596,7 +672,9 @@ __global__ void __launch_bounds__(TZ* TX) adj_field_kernel(const AdjParams A) {
         real jsum = real(0.5) * lc;   // slot s = this node
         lBy -= cdt * lc;
         const Pre pr = preimage(x, P.n[1], +1, P.periodic);
-        for (int q = 0; q < pr.cnt; ++q) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (q >= pr.cnt) break;
           const real ls = pr.v[q] == x ? lc : lEn_slot<DIM, real>(A, 0, z, pr.v[q]);
           jsum += real(0.5) * ls;
           lBy += cdt * ls;
@@ -611,7 +689,9 @@ __global__ void __launch_bounds__(TZ* TX) adj_field_kernel(const AdjParams A) {
         real jsum = real(0.5) * lc;
         lBy += cdt * lc;
         const Pre pr = preimage(z, P.n[0], +1, P.periodic);
-        for (int q = 0; q < pr.cnt; ++q) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (q >= pr.cnt) break;
           const real ls = pr.v[q] == z ? lc : lEn_slot<DIM, real>(A, 1, pr.v[q], x);
           jsum += real(0.5) * ls;
           lBy -= cdt * ls;
@@ -632,7 +712,9 @@ __global__ void __launch_bounds__(TZ* TX) adj_field_kernel(const AdjParams A) {
         // side 0: m + e_k = this node (coefficient -1/2dx); side 1: m - e_k
         const Pre pr = preimage(ck, P.n[k], side == 0 ? +1 : -1, P.periodic);
         const real sgn = side == 0 ? real(-1) : real(1);
-        for (int q = 0; q < pr.cnt; ++q) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (q >= pr.cnt) break;
           const int m = k == 0 ? aidx(P, pr.v[q], x) : aidx(P, z, pr.v[q]);
           const real c = sgn * S.i2dx;
           if constexpr (CL == CL_LEC) {
@@ -656,30 +738,34 @@ __global__ void __launch_bounds__(TZ* TX) adj_field_kernel(const AdjParams A) {
     decode_adjoint<DIM, CL, real>(P, S, N, lm, lA);
 
     // ---- population adjoint of the previous state ----------------------------
-    const bool edge = !gather_interior<DIM>(P, z, x);
-    const real* lf = reinterpret_cast<const real*>(A.lf_in);
     real* lfo = reinterpret_cast<real*>(A.lf_out);
     const real omt = real(1) - S.inv_tau;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const real* lfk = lf + (size_t)k * Q * pl;
-      real* lok = lfo + (size_t)k * Q * pl;
+      real lk[Q];
+      src.load(k, z, x, lk);
+      real* lok = lfo + (size_t)k * Q * pl + id;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) lok[i * pl + id] = omt * lfs_get<DIM, real>(P, lfk, i, z, x, edge) + lA[k];
+      for (int i = 0; i < Q; ++i) lok[i * pl] = omt * lk[i] + lA[k];
     }
   }
-  // ---- per-row partial sums of the driver-gradient weights ---------------
-  red[0][txi][tzi] = r0;
-  red[1][txi][tzi] = r2;
-  __syncthreads();
-  if (txi == 0 && z < P.n[0]) {
-    double s0 = 0.0, s2 = 0.0;
-#pragma unroll
-    for (int t = 0; t < TX; ++t) { s0 += red[0][t][tzi]; s2 += red[1][t][tzi]; }
-    const int ntx = gridDim.y;
-    A.rows[(size_t)blockIdx.y * P.n[0] + z] = s0;
-    A.rows[((size_t)ntx + blockIdx.y) * P.n[0] + z] = s2;
+}
+
+template <int DIM, int CL, typename real, int TZ, int TX>
+__global__ void __launch_bounds__(TZ* TX) adj_field_kernel(const AdjParams A) {
+  const StepParams& P = A.P;
+  __shared__ double red[2][TX][TZ];
+  const int tzi = threadIdx.x % TZ, txi = threadIdx.x / TZ;
+  const int z = blockIdx.x * TZ + tzi;
+  const int x = DIM >= 2 ? blockIdx.y * TX + txi : 0;
+  double r0 = 0.0, r2 = 0.0;
+  const real* lf = reinterpret_cast<const real*>(A.lf_in);
+  if (block_interior<DIM, TZ, TX>(P)) {
+    adj_field_node<DIM, CL, real>(A, GlobalLSrc<DIM, false, real>{P, lf}, z, x, r0, r2);
+  } else if (z < P.n[0] && (DIM < 2 || x < P.n[1])) {
+    adj_field_node<DIM, CL, real>(A, GlobalLSrc<DIM, true, real>{P, lf}, z, x, r0, r2);
   }
+  row_partials<TZ, TX>(A, red, tzi, txi, z, r0, r2);
 }
 
 // ---------------------------------------------------------------------------

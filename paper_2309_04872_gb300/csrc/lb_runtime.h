@@ -65,6 +65,7 @@ void release(Buf& b);
 lbp::StepParams step_params(const lbpwfa_s* h);
 double zeta0_of(double z0, long long step, double dt);
 int launch_step(lbpwfa_s* h, void* tape);
+int check_err_word(lbpwfa_s* h);
 
 // adjoint recording hooks (adjoint_rt.cu)
 int adj_before_step(lbpwfa_s* h, void** tape);  // checkpoint / tape slot of the next step

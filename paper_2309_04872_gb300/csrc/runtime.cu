@@ -440,7 +440,10 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
       h->use_persist = false;
     }
   }
-  h->use_tma = !h->use_persist && (p->kernel_variant == 0 || p->kernel_variant == 2) && tma_ok && h->ks.has_tma;
+  // automatic choice: the TMA box pays off for LEC (27 planes); the WARMC box
+  // (72 planes) leaves two CTAs per SM and the global-memory pull is faster
+  const bool tma_auto = p->kernel_variant == 0 && p->closure == LBPWFA_LEC;
+  h->use_tma = !h->use_persist && (tma_auto || p->kernel_variant == 2) && tma_ok && h->ks.has_tma;
   if (h->use_tma) {
     cudaError_t e = h->ks.prepare_tma();
     bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0], h->ks.tma_box) &&
