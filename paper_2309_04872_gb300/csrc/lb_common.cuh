@@ -165,13 +165,22 @@ template <> __device__ __forceinline__ const StepConst<double>& consts<double>(c
 
 // Storage codec: populations are kept as deviations from w_i A_rest,k.
 template <int PR> struct Codec;
+// store_q stores v and returns the value a later load reads back.
 template <> struct Codec<PR_F64> {
   __device__ static double load(const double* p, long long i, float) { return __ldg(p + i); }
   __device__ static void store(double* p, long long i, double v, float) { p[i] = v; }
+  __device__ static double store_q(double* p, long long i, double v, float, float) {
+    p[i] = v;
+    return v;
+  }
 };
 template <> struct Codec<PR_F32> {
   __device__ static float load(const float* p, long long i, float) { return __ldg(p + i); }
   __device__ static void store(float* p, long long i, float v, float) { p[i] = v; }
+  __device__ static float store_q(float* p, long long i, float v, float, float) {
+    p[i] = v;
+    return v;
+  }
 };
 template <> struct Codec<PR_F16S> {
   __device__ static float load(const __half* p, long long i, float inv_s) {
@@ -179,6 +188,11 @@ template <> struct Codec<PR_F16S> {
   }
   __device__ static void store(__half* p, long long i, float v, float s) {
     p[i] = __float2half_rn(v * s);
+  }
+  __device__ static float store_q(__half* p, long long i, float v, float s, float inv_s) {
+    const __half h = __float2half_rn(v * s);
+    p[i] = h;
+    return __half2float(h) * inv_s;
   }
 };
 
@@ -192,6 +206,12 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, int periodic) {
 __device__ __forceinline__ int cell_index32(const StepParams& P, int z, int x, int y) {
   return z + x * P.axis_stride[1] + y * P.axis_stride[2];
 }
+
+// Uncontracted sums: the same rounding in every kernel that inlines them.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
 __device__ __forceinline__ float rsqrt_t(float x) { return 1.0f / sqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }

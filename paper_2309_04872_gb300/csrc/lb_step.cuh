@@ -600,6 +600,11 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   // f* - w A_rest = df (1 - 1/tau) + (f^eq - w A_rest)/tau + w dt F, with
   // f^eq - w A_rest = w (dA + A P_i), P_i = 3 cu + 9/2 cu^2 - 3/2 u^2 split
   // into its even and odd parts over each pair of opposite velocities.
+  // The moving populations are stored first; the rest population takes the
+  // remainder of the set's post-collision moment dA + dt F (Eq. lbe with
+  // sum_i w_i = 1, sum_i w_i P_i = 0), summed over the values as stored.  In
+  // reduced precision the rounded weights sum to 1 + O(eps), and the direct
+  // form would scale every moment deviation by 1 + O(eps)/tau each step.
   static_assert(opposite_pairs<DIM>(), "lattice order must pair opposite velocities");
   real ul[3] = {0, 0, 0};
   real usq = 0;
@@ -624,13 +629,9 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
     }
     const real A = S.Arest[k] + dA;
     const real dtF = dt * source(k);
-    const float sc = P.scale[k];
+    const float sc = P.scale[k], isc = P.inv_scale[k];
     store* fk = fout + (size_t)k * Q * (size_t)P.plane;
-    {
-      const real w0 = real(L::w(0));
-      const real dfeq = w0 * (dA + A * base);
-      Codec<PR>::store(fk, id, df[0] * omt + dfeq * itau + w0 * dtF, sc);
-    }
+    real moved = 0;
 #pragma unroll
     for (int q = 0; q < (Q - 1) / 2; ++q) {
       const int i = 1 + 2 * q, j = i + 1;
@@ -641,9 +642,10 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       const real even = wi * (dA + A * (base + real(4.5) * cu * cu));
       const real odd = (real(3) * wi) * A * cu;
       const real wF = wi * dtF;
-      Codec<PR>::store(fk, i * pl + id, df[i] * omt + (even + odd) * itau + wF, sc);
-      Codec<PR>::store(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF, sc);
+      moved = add_rn(moved, Codec<PR>::store_q(fk, i * pl + id, df[i] * omt + (even + odd) * itau + wF, sc, isc));
+      moved = add_rn(moved, Codec<PR>::store_q(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF, sc, isc));
     }
+    Codec<PR>::store(fk, id, sub_rn(add_rn(dA, dtF), moved), sc);
   }
 }
 
