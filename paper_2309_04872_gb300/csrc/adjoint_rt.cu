@@ -302,7 +302,7 @@ extern "C" int lbpwfa_adjoint_step(lbpwfa_t h, lbpwfa_adjoint_io* io) {
   const long long wid = (long long)wz + (long long)wx * h->nzp;
 
   // J and the seed
-  r->ak.read_slot(h->E[h->cur].p, wid, (double*)r->jv.p, h->stream);
+  r->ak.read_slot(h->E[h->cur].p, lo_of(h, h->E[h->cur]), wid, (double*)r->jv.p, h->stream);
   CK_LAUNCH(h, "read_slot_kernel launch");
   for (int j = 0; j < 2; ++j) {
     CK(h, cudaMemsetAsync(r->lf[j].p, 0, r->lf[j].bytes, h->stream));

@@ -29,8 +29,8 @@ struct AdjImpl {
   static void seed(void* lE, long long idx, double v, cudaStream_t s) {
     adj_seed_kernel<real><<<1, 32, 0, s>>>((real*)lE, idx, v);
   }
-  static void read_slot(const void* E, long long idx, double* out, cudaStream_t s) {
-    read_slot_kernel<real><<<1, 32, 0, s>>>((const real*)E, idx, out);
+  static void read_slot(const void* E, const void* Elo, long long idx, double* out, cudaStream_t s) {
+    read_slot_kernel<real><<<1, 32, 0, s>>>((const real*)E, (const real*)Elo, idx, out);
   }
   static void fill(AdjKernelSet* k) {
     using AM = AdjModel<DIM, CL>;

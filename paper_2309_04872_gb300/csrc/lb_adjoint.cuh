@@ -175,12 +175,13 @@ __device__ __forceinline__ void load_node(const StepParams& P, const real* tp, i
   decode_record<DIM, CL, real>(P, consts<real>(P), N.dA, N.rec);
 }
 
-// WARMC theta^{ab} from the record (stored pairs, symmetric; 0 elsewhere).
+// WARMC theta^{ab} from the record (stored pairs as deviations from rest,
+// symmetric; 0 elsewhere).
 template <int DIM, typename real>
-__device__ __forceinline__ real th_of(const real* rec, int a, int b) {
+__device__ __forceinline__ real th_of(const StepConst<real>& S, const real* rec, int a, int b) {
   using M = Model<DIM, CL_WARMC>;
   const int j = M::thidx(a, b);
-  return j >= 0 ? rec[M::R_TH + j] : real(0);
+  return j >= 0 ? S.threst[j] + rec[M::R_TH + j] : real(0);
 }
 
 // Adjoint of the decoded values of one node.
@@ -267,7 +268,7 @@ __device__ __forceinline__ void decode_adjoint(const StepParams& P, const StepCo
 #pragma unroll
       for (int b = 0; b < DIM; ++b) {
         if (M::thidx(a, b) < 0) continue;
-        lm.u[b] += lm.th0[a] * th_of<DIM>(N.rec, a, b);
+        lm.u[b] += lm.th0[a] * th_of<DIM>(S, N.rec, a, b);
         lm.th[a][b] += lm.th0[a] * u[b];
       }
     // w^a = lambda u^a
@@ -499,9 +500,9 @@ __device__ __forceinline__ void adj_local_node(const AdjParams& A, const LSrc& s
 #pragma unroll
       for (int q = 0; q < DIM; ++q) {
         lm.th[b][q] -= gw[a][q] * l;
-        lgw[a][q] -= th_of<DIM>(N.rec, b, q) * l;
+        lgw[a][q] -= th_of<DIM>(S, N.rec, b, q) * l;
         lm.th[a][q] -= gw[b][q] * l;
-        lgw[b][q] -= th_of<DIM>(N.rec, a, q) * l;
+        lgw[b][q] -= th_of<DIM>(S, N.rec, a, q) * l;
       }
       lEn[a] -= th0[b] * l;
       lm.th0[b] -= En[a] * l;
@@ -514,11 +515,11 @@ __device__ __forceinline__ void adj_local_node(const AdjParams& A, const LSrc& s
           const int ea = levi(a, q, r), eb = levi(b, q, r);
           if (ea != 0) {
             lm.th[b][q] -= real(ea) * Bn[r] * l;
-            lBn[r] -= real(ea) * th_of<DIM>(N.rec, b, q) * l;
+            lBn[r] -= real(ea) * th_of<DIM>(S, N.rec, b, q) * l;
           }
           if (eb != 0) {
             lm.th[a][q] -= real(eb) * Bn[r] * l;
-            lBn[r] -= real(eb) * th_of<DIM>(N.rec, a, q) * l;
+            lBn[r] -= real(eb) * th_of<DIM>(S, N.rec, a, q) * l;
           }
         }
     }
@@ -901,8 +902,8 @@ __global__ void adj_seed_kernel(real* lE, long long idx, double v) {
 }
 
 template <typename real>
-__global__ void read_slot_kernel(const real* E, long long idx, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *out = (double)E[idx];
+__global__ void read_slot_kernel(const real* E, const real* Elo, long long idx, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = (double)E[idx] + (Elo ? (double)Elo[idx] : 0.0);
 }
 
 }  // namespace lbp

@@ -19,7 +19,7 @@ struct AdjKernelSet {
   void (*init_rows)(const StepParams&, const void* lE, const void* lB, const double* Kx, double* rows, dim3 grid,
                     cudaStream_t);
   void (*seed)(void* lE, long long idx, double v, cudaStream_t);
-  void (*read_slot)(const void* E, long long idx, double* out, cudaStream_t);
+  void (*read_slot)(const void* E, const void* Elo, long long idx, double* out, cudaStream_t);
 };
 
 // 1D/2D, LEC/WARMC, FP64/FP32 storage; false otherwise.

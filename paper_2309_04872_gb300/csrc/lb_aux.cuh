@@ -51,11 +51,24 @@ __device__ __forceinline__ double radial_factor(double r2, double sr) {
   return s > 0.0 ? -expm1(-s) / (2.0 * s) : 0.5;
 }
 
+// A field value into its slot: FP64 as is; FP32 as a high part and the
+// rounding remainder in the low array (value = high + low).
+template <typename real>
+__device__ __forceinline__ void put_field(real* hi, real* lo, long long i, double v) {
+  const real h = real(v);
+  hi[i] = h;
+  if (lo) lo[i] = real(v - (double)h);
+}
+template <typename real>
+__device__ __forceinline__ double get_field(const real* hi, const real* lo, long long i) {
+  return (double)hi[i] + (lo ? (double)lo[i] : 0.0);
+}
+
 // Initial fields: rigid bunch field in the v -> c limit (Sec. 6): E_z = 0,
 // div_perp E_perp = -n_b, B = z x E; E at t = -dt/2, B at t = 0.
 // Conducting-wall slots of E are zero.
 template <int DIM, typename real>
-__global__ void init_fields_kernel(AuxParams A, real* E, real* B) {
+__global__ void init_fields_kernel(AuxParams A, real* E, real* B, real* Elo, real* Blo) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= A.ncell) return;
   int e[3];
@@ -64,37 +77,39 @@ __global__ void init_fields_kernel(AuxParams A, real* E, real* B) {
   const double dx = A.dx, sr = A.sigma_r;
   const double z = e[0] * dx, x = (e[1] - A.xoff) * dx, y = (e[2] - A.yoff) * dx;
   const double tE = -0.5 * A.dt;
-  for (int a = 0; a < 3; ++a) { E[a * A.plane + p] = real(0); B[a * A.plane + p] = real(0); }
+  double Ev[3] = {0, 0, 0}, Bv[3] = {0, 0, 0};
   if (DIM == 2) {
     const double k = sr * sqrt(M_PI / 2.0) * erf(x / (sqrt(2.0) * sr));
-    double Ex = -driver_long_d(A, z + 0.5 * dx - A.z0 - tE) * k;   // E_x slot: z + dx/2
-    double By = -driver_long_d(A, z - A.z0) * k;                   // B_y at the node
-    E[1 * A.plane + p] = real(Ex);
-    B[2 * A.plane + p] = real(By);
+    Ev[1] = -driver_long_d(A, z + 0.5 * dx - A.z0 - tE) * k;   // E_x slot: z + dx/2
+    Bv[2] = -driver_long_d(A, z - A.z0) * k;                   // B_y at the node
   } else if (DIM == 3) {
     {  // E_x slot (x, y + dx/2, z + dx/2)
       double yy = y + 0.5 * dx;
-      E[1 * A.plane + p] = real(-driver_long_d(A, z + 0.5 * dx - A.z0 - tE) * x * radial_factor(x * x + yy * yy, sr));
+      Ev[1] = -driver_long_d(A, z + 0.5 * dx - A.z0 - tE) * x * radial_factor(x * x + yy * yy, sr);
     }
     {  // E_y slot (x + dx/2, y, z + dx/2)
       double xx = x + 0.5 * dx;
-      E[2 * A.plane + p] = real(-driver_long_d(A, z + 0.5 * dx - A.z0 - tE) * y * radial_factor(xx * xx + y * y, sr));
+      Ev[2] = -driver_long_d(A, z + 0.5 * dx - A.z0 - tE) * y * radial_factor(xx * xx + y * y, sr);
     }
     {  // B_x slot (x + dx/2, y, z): B_x = -E_y
       double xx = x + 0.5 * dx;
-      B[1 * A.plane + p] = real(driver_long_d(A, z - A.z0) * y * radial_factor(xx * xx + y * y, sr));
+      Bv[1] = driver_long_d(A, z - A.z0) * y * radial_factor(xx * xx + y * y, sr);
     }
     {  // B_y slot (x, y + dx/2, z): B_y = E_x
       double yy = y + 0.5 * dx;
-      B[2 * A.plane + p] = real(-driver_long_d(A, z - A.z0) * x * radial_factor(x * x + yy * yy, sr));
+      Bv[2] = -driver_long_d(A, z - A.z0) * x * radial_factor(x * x + yy * yy, sr);
     }
   }
   if (!A.periodic) {
     for (int a = 0; a < 3; ++a) {
       const int b = (a + 1) % 3, d = (a + 2) % 3;
       bool wall = (b >= 1 && b < DIM && e[b] == A.n[b] - 1) || (d >= 1 && d < DIM && e[d] == A.n[d] - 1);
-      if (wall) E[a * A.plane + p] = real(0);
+      if (wall) Ev[a] = 0.0;
     }
+  }
+  for (int a = 0; a < 3; ++a) {
+    put_field(E, Elo, a * A.plane + p, Ev[a]);
+    put_field(B, Blo, a * A.plane + p, Bv[a]);
   }
 }
 
@@ -244,8 +259,8 @@ __global__ void moments_kernel(AuxParams A, const typename Prec<PR>::store* fs, 
 // Field slots (real, padded) -> FP64 unpadded, for the selected components
 // (comp[j] = internal component index z=0, x=1, y=2; is_b[j] picks B).
 template <typename real>
-__global__ void export_fields_kernel(AuxParams A, const real* E, const real* B, int ncomp,
-                                     int4 comps, int4 isb, double* out) {
+__global__ void export_fields_kernel(AuxParams A, const real* E, const real* B, const real* Elo, const real* Blo,
+                                     int ncomp, int4 comps, int4 isb, double* out) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= A.ncell) return;
   int e[3];
@@ -255,12 +270,14 @@ __global__ void export_fields_kernel(AuxParams A, const real* E, const real* B, 
   const int bb[4] = {isb.x, isb.y, isb.z, isb.w};
   for (int j = 0; j < ncomp; ++j) {
     const real* src = bb[j] ? B : E;
-    out[(long long)j * A.ncell + c] = (double)src[cc[j] * A.plane + p];
+    const real* lo = bb[j] ? Blo : Elo;
+    out[(long long)j * A.ncell + c] = get_field(src, lo, cc[j] * A.plane + p);
   }
 }
 
 template <int DIM, typename real>
-__global__ void import_fields_kernel(AuxParams A, const double* Ein, const double* Bin, real* E, real* B) {
+__global__ void import_fields_kernel(AuxParams A, const double* Ein, const double* Bin, real* E, real* B, real* Elo,
+                                     real* Blo) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= A.ncell) return;
   int e[3];
@@ -271,9 +288,9 @@ __global__ void import_fields_kernel(AuxParams A, const double* Ein, const doubl
       const int b = (a + 1) % 3, d = (a + 2) % 3;
       bool wall = !A.periodic &&
                   ((b >= 1 && b < DIM && e[b] == A.n[b] - 1) || (d >= 1 && d < DIM && e[d] == A.n[d] - 1));
-      E[a * A.plane + p] = (e_present<DIM>(a) && !wall) ? real(Ein[a * A.ncell + c]) : real(0);
+      put_field(E, Elo, a * A.plane + p, (e_present<DIM>(a) && !wall) ? Ein[a * A.ncell + c] : 0.0);
     }
-    if (Bin) B[a * A.plane + p] = b_present<DIM>(a) ? real(Bin[a * A.ncell + c]) : real(0);
+    if (Bin) put_field(B, Blo, a * A.plane + p, b_present<DIM>(a) ? Bin[a * A.ncell + c] : 0.0);
   }
 }
 

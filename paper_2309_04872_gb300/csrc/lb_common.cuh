@@ -131,6 +131,8 @@ struct StepConst {
   real xoff, yoff;        // (nx-1)/2, (ny-1)/2
   real pdz_inv, phalf;    // 1/profile_dz, (len-1)/2
   real Arest[11];
+  real ilam0;             // WARMC 1 / lambda_0
+  real threst[6];         // WARMC rest theta pairs A_rest,j / lambda_0
 };
 
 struct StepParams {
@@ -140,6 +142,12 @@ struct StepParams {
   void* Eout;            // E^{n+1/2}
   const void* Bin;       // B^n
   void* Bout;            // B^{n+1}
+  // reduced precision: low parts of E and B (value = high + low, FP32 each;
+  // null in FP64)
+  const void* Ein_lo;
+  void* Eout_lo;
+  const void* Bin_lo;
+  void* Bout_lo;
   void* prev;            // WARMC previous-step th00, th0[DIM], w[DIM]: [NPREV][plane]
   int have_prev;
   int n[3];              // nodes along z, x, y (1 for absent axes)
@@ -207,6 +215,17 @@ __device__ __forceinline__ int cell_index32(const StepParams& P, int z, int x, i
   return z + x * P.axis_stride[1] + y * P.axis_stride[2];
 }
 
+// Compensated (two-float) accumulation hi + lo += d: Knuth's two-sum of hi
+// and d, its error folded into lo and renormalised, FP32 operations only.
+__device__ __forceinline__ void two_float_add(float& hi, float& lo, float d) {
+  const float s = __fadd_rn(hi, d);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+  const float l = __fadd_rn(lo, err);
+  hi = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(hi, s));
+}
+
 // Uncontracted sums: the same rounding in every kernel that inlines them.
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
@@ -225,13 +244,28 @@ template <> __device__ __forceinline__ float pow_2_over_D<float>(float x, int D)
   return D == 1 ? x * x : (D == 3 ? cbrtf(x * x) : x);
 }
 
+// Pi - 1 = (n/gamma)^(1+2/D) - 1 without cancellation near rest, from
+// dn = n - 1, |p|^2 and gamma: x - 1 = (dn - (gamma - 1)) / gamma with
+// gamma - 1 = |p|^2 / (gamma + 1); D = 1: x^3 - 1 = d (3 + 3 d + d^2);
+// D = 3: x^(5/3) - 1 = d x^(2/3) + (x^(2/3) - 1), x^(2/3) - 1 =
+// (x^2 - 1) / (x^(4/3) + x^(2/3) + 1).
+template <typename real>
+__device__ __forceinline__ real lec_pi_minus_1(real dn, real p2, real g, int D) {
+  const real d = (dn - p2 / (g + real(1))) / g;
+  if (D == 1) return d * (real(3) + d * (real(3) + d));
+  const real x = real(1) + d;
+  const real xe = pow_2_over_D<real>(x, D);
+  return d * xe + d * (real(2) + d) / (xe * xe + xe + real(1));
+}
+
 // LEC transport velocity, Sec. 4.1: p^(0) = A_p / n, then
 // gamma^(k) = sqrt(1 + |p^(k)|^2), p^(k+1) = p^(0) / (1 + (1 + D/2) mu (n/gamma^(k))^(2/D)),
 // stopped when the largest change is within a few ulps of the largest |p|.
 // cH = (1 + D/2) mu.
 template <int DIM, typename real>
 __device__ __forceinline__ void decode_lec(real n, const real* Ap, real cH, int D, real* u, real& Pi,
-                                           real* gamma_out = nullptr) {
+                                           real* gamma_out = nullptr, real dn = real(0),
+                                           real* pim1_out = nullptr) {
   constexpr bool dbl = sizeof(real) == 8;
   const real tol = dbl ? real(1e-15) : real(4e-7);
   const int maxit = dbl ? 64 : 32;
@@ -265,6 +299,7 @@ __device__ __forceinline__ void decode_lec(real n, const real* Ap, real cH, int 
   const real x = n * ig;
   Pi = x * pow_2_over_D<real>(x, D);
   if (gamma_out) *gamma_out = g;
+  if (pim1_out) *pim1_out = lec_pi_minus_1<real>(dn, s - real(1), g, D);
 }
 
 // FP32 form of the same iteration for the reduced-precision modes.  Inside
@@ -273,7 +308,8 @@ __device__ __forceinline__ void decode_lec(real n, const real* Ap, real cH, int 
 // for mu <= 5e-2).  The returned u and Pi are evaluated once more with
 // correctly rounded sqrt, reciprocal and cbrt.
 template <int DIM>
-__device__ __forceinline__ void decode_lec_f32(float n, const float* Ap, float cH, int D, float* u, float& Pi) {
+__device__ __forceinline__ void decode_lec_f32(float n, const float* Ap, float cH, int D, float* u, float& Pi,
+                                               float dn = 0.0f, float* pim1_out = nullptr) {
   const float in_ = __frcp_rn(n);
   float p0[DIM], p[DIM];
 #pragma unroll
@@ -299,11 +335,18 @@ __device__ __forceinline__ void decode_lec_f32(float n, const float* Ap, float c
   float s = 1.0f;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) s = fmaf(p[a], p[a], s);
-  const float ig = __frcp_rn(sqrtf(s));
+  const float g = sqrtf(s);
+  const float ig = __frcp_rn(g);
 #pragma unroll
   for (int a = 0; a < DIM; ++a) u[a] = p[a] * ig;
   const float x = n * ig;
   Pi = x * pow_2_over_D<float>(x, D);
+  if (pim1_out) {
+    float p2 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) p2 = fmaf(p[a], p[a], p2);
+    *pim1_out = lec_pi_minus_1<float>(dn, p2, g, D);
+  }
 }
 
 // Driver longitudinal factor L(zeta) (Eq. bunch-density, rms reading).  A

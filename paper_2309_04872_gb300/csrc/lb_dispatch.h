@@ -16,14 +16,16 @@ struct KernelSet {
   size_t step_smem;      // dynamic shared memory of the step kernel
   cudaError_t (*prepare)();
   void (*step)(const StepParams&, dim3 grid, cudaStream_t);
-  void (*init_fields)(const AuxParams&, void* E, void* B, cudaStream_t);
+  void (*init_fields)(const AuxParams&, void* E, void* B, void* Elo, void* Blo, cudaStream_t);
   void (*import_pops)(const AuxParams&, const double* src, void* dst, cudaStream_t);
   void (*export_pops)(const AuxParams&, const void* src, double* dst, cudaStream_t);
   void (*advected)(const AuxParams&, const void* src, double* dst, cudaStream_t);
   void (*moments)(const AuxParams&, const void* src, uint32_t mask, double* dst, cudaStream_t);
-  void (*import_fields)(const AuxParams&, const double* E, const double* B, void* Ed, void* Bd, cudaStream_t);
-  void (*export_fields)(const AuxParams&, const void* E, const void* B, int ncomp, int4 comps, int4 isb,
-                        double* dst, cudaStream_t);
+  // FP32 fields carry low parts (Elo, Blo); null in FP64
+  void (*import_fields)(const AuxParams&, const double* E, const double* B, void* Ed, void* Bd, void* Elo,
+                        void* Blo, cudaStream_t);
+  void (*export_fields)(const AuxParams&, const void* E, const void* B, const void* Elo, const void* Blo, int ncomp,
+                        int4 comps, int4 isb, double* dst, cudaStream_t);
   void (*reduce_partial)(const AuxParams&, const void* src, double* partial, int nblk, cudaStream_t);
   // TMA-staged 2D step (open boundaries); has_tma == false when not built
   bool has_tma;

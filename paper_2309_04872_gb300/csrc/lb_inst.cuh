@@ -35,8 +35,8 @@ struct Impl {
   static void step(const StepParams& P, dim3 grid, cudaStream_t s) {
     lb_step_kernel<DIM, CL, PR, T::TZ, T::TX, T::TY><<<grid, Cfg::NT, Cfg::smem_bytes, s>>>(P);
   }
-  static void init_fields(const AuxParams& A, void* E, void* B, cudaStream_t s) {
-    init_fields_kernel<DIM, real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, (real*)E, (real*)B);
+  static void init_fields(const AuxParams& A, void* E, void* B, void* Elo, void* Blo, cudaStream_t s) {
+    init_fields_kernel<DIM, real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, (real*)E, (real*)B, (real*)Elo, (real*)Blo);
   }
   static void import_pops(const AuxParams& A, const double* src, void* dst, cudaStream_t s) {
     import_pops_kernel<DIM, CL, PR><<<grid1(A.ncell, 128), 128, 0, s>>>(A, src, (store*)dst);
@@ -50,13 +50,15 @@ struct Impl {
   static void moments(const AuxParams& A, const void* src, uint32_t mask, double* dst, cudaStream_t s) {
     moments_kernel<DIM, CL, PR><<<grid1(A.ncell, 128), 128, 0, s>>>(A, (const store*)src, mask, dst);
   }
-  static void import_fields(const AuxParams& A, const double* E, const double* B, void* Ed, void* Bd,
-                            cudaStream_t s) {
-    import_fields_kernel<DIM, real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, E, B, (real*)Ed, (real*)Bd);
+  static void import_fields(const AuxParams& A, const double* E, const double* B, void* Ed, void* Bd, void* Elo,
+                            void* Blo, cudaStream_t s) {
+    import_fields_kernel<DIM, real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, E, B, (real*)Ed, (real*)Bd, (real*)Elo,
+                                                                         (real*)Blo);
   }
-  static void export_fields(const AuxParams& A, const void* E, const void* B, int ncomp, int4 comps,
-                            int4 isb, double* dst, cudaStream_t s) {
-    export_fields_kernel<real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, (const real*)E, (const real*)B, ncomp,
+  static void export_fields(const AuxParams& A, const void* E, const void* B, const void* Elo, const void* Blo,
+                            int ncomp, int4 comps, int4 isb, double* dst, cudaStream_t s) {
+    export_fields_kernel<real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, (const real*)E, (const real*)B,
+                                                                    (const real*)Elo, (const real*)Blo, ncomp,
                                                                     comps, isb, dst);
   }
   static void reduce_partial(const AuxParams& A, const void* src, double* partial, int nblk, cudaStream_t s) {

@@ -59,6 +59,13 @@ struct lbpwfa_s {
 
 namespace lbprt {
 
+// FP32 fields are kept as high + low parts: each E or B buffer holds the
+// three high components followed by the three low ones (FP64: high only).
+inline bool split_fields(const lbpwfa_s* h) { return h->real_sz == 4; }
+inline void* lo_of(const lbpwfa_s* h, const Buf& b) {
+  return split_fields(h) ? (char*)b.p + 3 * (size_t)h->plane * h->real_sz : nullptr;
+}
+
 int fail_cuda(lbpwfa_s* h, cudaError_t e, const char* what);
 int alloc(lbpwfa_s* h, Buf& b, size_t bytes);
 void release(Buf& b);

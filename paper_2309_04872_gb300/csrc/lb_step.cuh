@@ -33,6 +33,19 @@ __host__ __device__ constexpr int levi(int i, int j, int k) {
        : (((i == 0 && j == 1) || (i == 1 && j == 2) || (i == 2 && j == 0)) ? 1 : -1);
 }
 
+// Moment of one population set, A_k = sum_i f_ki (Eq. disc-moments-ade), with
+// each pair of opposite velocities added first: the pair sum cancels the odd
+// (momentum-flux) parts before they meet the set's total, which halves the
+// rounding of the deviation moment in reduced precision.  Uncontracted, so
+// every caller gets the same bits.
+template <int Q, typename real>
+__device__ __forceinline__ real set_moment(const real* df) {
+  real s = df[0];
+#pragma unroll
+  for (int i = 1; i + 1 < Q; i += 2) s = add_rn(s, add_rn(df[i], df[i + 1]));
+  return s;
+}
+
 template <int DIM, int CL, int PR, int TZ, int TX, int TY>
 struct StepCfg {
   using M = Model<DIM, CL>;
@@ -44,7 +57,11 @@ struct StepCfg {
   static constexpr int NR = RZ * RX * RY;
   // records, E slots, and the separable driver factors of the tile's slots
   static constexpr int NDRV = (TZ + 1) + (TX + 1) + (TY + 1);
-  static constexpr size_t smem_bytes = ((size_t)(M::NM + 3) * NR + NDRV) * sizeof(real);
+  // FP32 fields are carried as high + low parts (compensated updates)
+  static constexpr bool CF = sizeof(real) == 4;
+  static constexpr int NEC = DIM;                   // present E components (z[, x[, y]])
+  static constexpr int NE_SLOTS = CF ? 2 * NEC : NEC;
+  static constexpr size_t smem_bytes = ((size_t)(M::NM + NE_SLOTS) * NR + NDRV) * sizeof(real);
   __host__ __device__ static constexpr int stride(int a) { return a == 0 ? 1 : (a == 1 ? RZ : RZ * RX); }
 };
 
@@ -86,22 +103,25 @@ struct GlobalPull {
   }
 };
 
-// Decode the record of one node from its deviation moments dA[K].
+// Decode the record of one node from its deviation moments dA[K].  Values
+// that only enter central differences are kept as deviations from rest
+// (LEC: Pi - 1; WARMC: theta - theta_rest), so the differences of neighbours
+// do not cancel against the rest value in reduced precision.
 template <int DIM, int CL, typename real>
 __device__ __forceinline__ void decode_record(const StepParams& P, const StepConst<real>& S, const real* dA,
                                               real* rec) {
   using M = Model<DIM, CL>;
   if constexpr (CL == CL_LEC) {
     real n = real(1) + dA[0];
-    real Ap[DIM], u[DIM], Pi;
+    real Ap[DIM], u[DIM], Pi, Pim1;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) Ap[a] = dA[1 + a];
-    if constexpr (sizeof(real) == 4) decode_lec_f32<DIM>(n, Ap, S.cH, P.D, u, Pi);
-    else decode_lec<DIM, real>(n, Ap, S.cH, P.D, u, Pi);
+    if constexpr (sizeof(real) == 4) decode_lec_f32<DIM>(n, Ap, S.cH, P.D, u, Pi, dA[0], &Pim1);
+    else decode_lec<DIM, real>(n, Ap, S.cH, P.D, u, Pi, nullptr, dA[0], &Pim1);
     rec[M::R_N] = n;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) rec[M::R_U + a] = u[a];
-    rec[M::R_PI] = Pi;
+    rec[M::R_PI] = Pim1;
   } else {
     const real n = real(1) + dA[0];
     const real nl = S.Arest[1] + dA[1];
@@ -111,15 +131,21 @@ __device__ __forceinline__ void decode_record(const StepParams& P, const StepCon
     real u[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < DIM; ++a) u[a] = dA[2 + a] * inl;
-    real th[M::NTH];
+    // theta_j - theta_rest,j = A_rest,j (n/nl - 1/lambda_0) + dA_j n/nl with
+    // n/nl - 1/lambda_0 = (dA_0 - dA_1/lambda_0)/nl
+    const real dil = (dA[0] - dA[1] * S.ilam0) * inl;
+    real th[M::NTH], thd[M::NTH];
 #pragma unroll
-    for (int j = 0; j < M::NTH; ++j) th[j] = (S.Arest[2 + DIM + j] + dA[2 + DIM + j]) * ilam;
+    for (int j = 0; j < M::NTH; ++j) {
+      thd[j] = S.Arest[2 + DIM + j] * dil + dA[2 + DIM + j] * ilam;
+      th[j] = S.threst[j] + thd[j];
+    }
     rec[M::R_N] = n;
     rec[M::R_LAM] = lam;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) rec[M::R_U + a] = u[a];
 #pragma unroll
-    for (int j = 0; j < M::NTH; ++j) rec[M::R_TH + j] = th[j];
+    for (int j = 0; j < M::NTH; ++j) rec[M::R_TH + j] = thd[j];
     // theta^{0a} = u_b theta^{ab} (Eq. traces4, App. A mass-shell rows)
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -140,9 +166,11 @@ __device__ __forceinline__ void decode_record(const StepParams& P, const StepCon
 //   Bc[a]    = B_a^n at the node's slot
 //   Bp[d][b] = B_d^n one node up along axis b (curl at the E slot)
 //   Bm[a]    = B_a^n one node down along a (node average of B_a)
+//   *_lo: low parts of the same values (FP32 fields; zero in FP64)
 template <typename real>
 struct FieldPF {
   real Ec[3], Bc[3], Bp[3][3], Bm[3];
+  real Ec_lo[3], Bc_lo[3], Bp_lo[3][3], Bm_lo[3];
 };
 
 template <bool EDGE>
@@ -154,25 +182,57 @@ __device__ __forceinline__ int nb_offset(const StepParams& P, int e, int axis, i
 
 template <int DIM, typename real, bool EDGE>
 __device__ __forceinline__ void load_fields(const StepParams& P, int e0, int e1, int e2, int id, FieldPF<real>& F) {
+  constexpr bool CF = sizeof(real) == 4;
   const real* Ein = reinterpret_cast<const real*>(P.Ein);
   const real* Bin = reinterpret_cast<const real*>(P.Bin);
+  const real* Elo = reinterpret_cast<const real*>(P.Ein_lo);
+  const real* Blo = reinterpret_cast<const real*>(P.Bin_lo);
   const int pl = (int)P.plane;
   const int e[3] = {e0, e1, e2};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (e_present<DIM>(a)) F.Ec[a] = Ein[a * pl + id];
+    F.Ec_lo[a] = F.Bc_lo[a] = F.Bm_lo[a] = real(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) F.Bp_lo[a][b] = real(0);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (e_present<DIM>(a)) {
+      F.Ec[a] = Ein[a * pl + id];
+      if (CF) F.Ec_lo[a] = Elo[a * pl + id];
+    }
     if (b_present<DIM>(a)) {
       F.Bc[a] = Bin[a * pl + id];
-      if (axis_present<DIM>(a)) F.Bm[a] = Bin[a * pl + id + nb_offset<EDGE>(P, e[a], a, -1)];
+      if (CF) F.Bc_lo[a] = Blo[a * pl + id];
+      if (axis_present<DIM>(a)) {
+        const int o = a * pl + id + nb_offset<EDGE>(P, e[a], a, -1);
+        F.Bm[a] = Bin[o];
+        if (CF) F.Bm_lo[a] = Blo[o];
+      }
     }
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (!e_present<DIM>(a)) continue;
     const int b = (a + 1) % 3, d = (a + 2) % 3;
-    if (axis_present<DIM>(b) && b_present<DIM>(d)) F.Bp[d][b] = Bin[d * pl + id + nb_offset<EDGE>(P, e[b], b, +1)];
-    if (axis_present<DIM>(d) && b_present<DIM>(b)) F.Bp[b][d] = Bin[b * pl + id + nb_offset<EDGE>(P, e[d], d, +1)];
+    if (axis_present<DIM>(b) && b_present<DIM>(d)) {
+      const int o = d * pl + id + nb_offset<EDGE>(P, e[b], b, +1);
+      F.Bp[d][b] = Bin[o];
+      if (CF) F.Bp_lo[d][b] = Blo[o];
+    }
+    if (axis_present<DIM>(d) && b_present<DIM>(b)) {
+      const int o = b * pl + id + nb_offset<EDGE>(P, e[d], d, +1);
+      F.Bp[b][d] = Bin[o];
+      if (CF) F.Bp_lo[b][d] = Blo[o];
+    }
   }
+}
+
+// Difference of two compensated values (high parts first: close values
+// subtract exactly).
+template <typename real>
+__device__ __forceinline__ real diff2(real ah, real al, real bh, real bl) {
+  return (ah - bh) + (al - bl);
 }
 
 // Driver current n_b at the E_z slot of node e: L(z - z0 - t) at the node's
@@ -213,11 +273,17 @@ __device__ __forceinline__ void e_slot(const StepParams& P, const StepConst<type
       bool wall = false;
       if (b >= 1 && axis_present<DIM>(b) && e[b] == P.n[b] - 1) wall = true;
       if (d >= 1 && axis_present<DIM>(d) && e[d] == P.n[d] - 1) wall = true;
-      if (wall) { sE[a * NR + r] = real(0); continue; }
+      if (wall) {
+        sE[a * NR + r] = real(0);
+        if (C::CF) sE[(C::NEC + a) * NR + r] = real(0);
+        continue;
+      }
     }
     real curl = 0;
-    if (axis_present<DIM>(b) && b_present<DIM>(d)) curl += (F.Bp[d][b] - F.Bc[d]) * S.idx;
-    if (axis_present<DIM>(d) && b_present<DIM>(b)) curl -= (F.Bp[b][d] - F.Bc[b]) * S.idx;
+    if (axis_present<DIM>(b) && b_present<DIM>(d))
+      curl += diff2(F.Bp[d][b], F.Bp_lo[d][b], F.Bc[d], F.Bc_lo[d]) * S.idx;
+    if (axis_present<DIM>(d) && b_present<DIM>(b))
+      curl -= diff2(F.Bp[b][d], F.Bp_lo[b][d], F.Bc[b], F.Bc_lo[b]) * S.idx;
     real J = 0;
     if (a < DIM) {
       const bool ob = axis_present<DIM>(b), od = axis_present<DIM>(d);
@@ -246,7 +312,14 @@ __device__ __forceinline__ void e_slot(const StepParams& P, const StepConst<type
       }
       J += nbv;
     }
-    sE[a * NR + r] = F.Ec[a] + S.dt * (curl + J);
+    if constexpr (C::CF) {
+      real hi = F.Ec[a], lo = F.Ec_lo[a];
+      two_float_add(hi, lo, S.dt * (curl + J));
+      sE[a * NR + r] = hi;
+      sE[(C::NEC + a) * NR + r] = lo;
+    } else {
+      sE[a * NR + r] = F.Ec[a] + S.dt * (curl + J);
+    }
   }
 }
 
@@ -263,10 +336,7 @@ __device__ __forceinline__ void decode_node(const StepParams& P, const StepConst
   for (int k = 0; k < K; ++k) {
     real df[Q];
     pull.template get<EDGE>(z, x, y, k, df);
-    real s = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) s += df[i];
-    dA[k] = s;
+    dA[k] = set_moment<Q>(df);
   }
   real rec[M::NM];
   decode_record<DIM, CL, real>(P, S, dA, rec);
@@ -299,8 +369,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
 
   const StepConst<real>& S = consts<real>(P);
   real* smac = reinterpret_cast<real*>(smem);  // [NM][NR]
-  real* sE = smac + M::NM * NR;                 // [3][NR]
-  real* sdrv = sE + 3 * NR;                     // [TZ+1 | TX+1 | TY+1] driver factors
+  real* sE = smac + M::NM * NR;                 // [DIM][NR] (+ [DIM][NR] low parts in FP32)
+  real* sdrv = sE + C::NE_SLOTS * NR;           // [TZ+1 | TX+1 | TY+1] driver factors
 
   const int tid = threadIdx.x;
   const int tz = tid % TZ, tx = (tid / TZ) % TX, ty = tid / (TZ * TX);
@@ -340,13 +410,11 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
     for (int k = 0; k < K; ++k) {
       real df[Q];
       pull.template get<EDGE>(ez, ex, ey, k, df);
-      real s = 0;
+      if constexpr (KEEP) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        s += df[i];
-        if constexpr (KEEP) keep[k * Q + i] = df[i];
+        for (int i = 0; i < Q; ++i) keep[k * Q + i] = df[i];
       }
-      dA_own[k] = s;
+      dA_own[k] = set_moment<Q>(df);
     }
     real rec[M::NM];
     decode_record<DIM, CL, real>(P, S, dA_own, rec);
@@ -359,7 +427,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
         const int id_own = cell_index32(P, gz, gx, gy);
 #pragma unroll
         for (int k = 0; k < K; ++k) tp[k * pl + id_own] = dA_own[k];
-        if constexpr (DIM == 2) tp[(K + DIM) * pl + id_own] = F.Bc[2];
+        if constexpr (DIM == 2) tp[(K + DIM) * pl + id_own] = F.Bc[2] + F.Bc_lo[2];
       }
     }
   }
@@ -433,7 +501,11 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
           const bool trans_out = (DIM >= 2 && (e1 < 0 || e1 >= P.n[1])) || (DIM >= 3 && (e2 < 0 || e2 >= P.n[2]));
           if (trans_out) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) if (e_present<DIM>(a)) sE[a * NR + r] = real(0);
+            for (int a = 0; a < 3; ++a)
+              if (e_present<DIM>(a)) {
+                sE[a * NR + r] = real(0);
+                if (C::CF) sE[(C::NEC + a) * NR + r] = real(0);
+              }
             continue;
           }
           if (e0 < 0) { r_eff = r + 1; e0 = 0; }
@@ -446,7 +518,11 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       e_slot<DIM, CL, PR, TZ, TX, TY, EDGE>(P, S, smac, sE, sdrv, oz, ox, oy, r_eff, e0, e1, e2, G);
       if (r_eff != r) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) if (e_present<DIM>(a)) sE[a * NR + r] = sE[a * NR + r_eff];
+        for (int a = 0; a < 3; ++a)
+          if (e_present<DIM>(a)) {
+            sE[a * NR + r] = sE[a * NR + r_eff];
+            if (C::CF) sE[(C::NEC + a) * NR + r] = sE[(C::NEC + a) * NR + r_eff];
+          }
       }
     }
   }
@@ -462,11 +538,20 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   real* Bout = reinterpret_cast<real*>(P.Bout);
   real En[3] = {0, 0, 0}, Bn[3] = {0, 0, 0};
   real* tape = reinterpret_cast<real*>(P.tape);
+  real* Eout_lo = reinterpret_cast<real*>(P.Eout_lo);
+  real* Bout_lo = reinterpret_cast<real*>(P.Bout_lo);
+  // E slot value (high + low in FP32)
+  auto Ev = [&](int a, int rr) -> real { return C::CF ? sE[a * NR + rr] + sE[(C::NEC + a) * NR + rr] : sE[a * NR + rr]; };
+  auto Ed = [&](int a, int r1, int r2) -> real {
+    return C::CF ? diff2(sE[a * NR + r1], sE[(C::NEC + a) * NR + r1], sE[a * NR + r2], sE[(C::NEC + a) * NR + r2])
+                 : sE[a * NR + r1] - sE[a * NR + r2];
+  };
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (e_present<DIM>(a)) {
       Eout[a * pl + id] = sE[a * NR + r];
-      if (DIM <= 2 && tape != nullptr) tape[(K + a) * pl + id] = sE[a * NR + r];
+      if (C::CF) Eout_lo[a * pl + id] = sE[(C::NEC + a) * NR + r];
+      if (DIM <= 2 && tape != nullptr) tape[(K + a) * pl + id] = Ev(a, r);
       const int b = (a + 1) % 3, d = (a + 2) % 3;
       const bool ob = axis_present<DIM>(b), od = axis_present<DIM>(d);
       const int sb = ob ? C::stride(b) : 0, sd = od ? C::stride(d) : 0;
@@ -476,19 +561,24 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       for (int jb = 0; jb < 2; ++jb)
 #pragma unroll
         for (int jd = 0; jd < 2; ++jd)
-          if (jb < nb && jd < nd) s += sE[a * NR + r - jb * sb - jd * sd];
+          if (jb < nb && jd < nd) s += Ev(a, r - jb * sb - jd * sd);
       En[a] = s * (real(1) / real(nb * nd));
     }
     if (b_present<DIM>(a)) {
-      const real bo = F.Bc[a];
-      Bn[a] = axis_present<DIM>(a) ? real(0.5) * (bo + F.Bm[a]) : bo;
+      const real bo = F.Bc[a] + F.Bc_lo[a];
+      Bn[a] = axis_present<DIM>(a) ? real(0.5) * (bo + (F.Bm[a] + F.Bm_lo[a])) : bo;
       const int b = (a + 1) % 3, d = (a + 2) % 3;
       real curl = 0;
-      if (axis_present<DIM>(b) && e_present<DIM>(d))
-        curl += (sE[d * NR + r] - sE[d * NR + r - C::stride(b)]) * S.idx;
-      if (axis_present<DIM>(d) && e_present<DIM>(b))
-        curl -= (sE[b * NR + r] - sE[b * NR + r - C::stride(d)]) * S.idx;
-      Bout[a * pl + id] = bo - dt * curl;
+      if (axis_present<DIM>(b) && e_present<DIM>(d)) curl += Ed(d, r, r - C::stride(b)) * S.idx;
+      if (axis_present<DIM>(d) && e_present<DIM>(b)) curl -= Ed(b, r, r - C::stride(d)) * S.idx;
+      if constexpr (C::CF) {
+        real hi = F.Bc[a], lo = F.Bc_lo[a];
+        two_float_add(hi, lo, -(dt * curl));
+        Bout[a * pl + id] = hi;
+        Bout_lo[a * pl + id] = lo;
+      } else {
+        Bout[a * pl + id] = F.Bc[a] - dt * curl;
+      }
     }
   }
 
@@ -520,7 +610,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const int j = M::thidx(a, b);
-        th[a][b] = j >= 0 ? smac[(M::R_TH + j) * NR + r] : real(0);
+        th[a][b] = j >= 0 ? S.threst[j] + smac[(M::R_TH + j) * NR + r] : real(0);
       }
     real w[3] = {0, 0, 0};
     const real lam = smac[M::R_LAM * NR + r];
@@ -623,9 +713,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       dA = dA_own[k];
     } else {
       pull.template get<EDGE>(gz, gx, gy, k, df);
-      dA = 0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) dA += df[i];
+      dA = set_moment<Q>(df);
     }
     const real A = S.Arest[k] + dA;
     const real dtF = dt * source(k);

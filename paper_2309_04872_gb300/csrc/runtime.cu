@@ -154,6 +154,9 @@ void fill_consts(const lbpwfa_s* h, StepConst<real>& c) {
   c.pdz_inv = (real)(h->prm.profile_dz > 0 ? 1.0 / h->prm.profile_dz : 0.0);
   c.phalf = (real)(0.5 * ((double)h->profile_h.size() - 1.0));
   for (int k = 0; k < 11; ++k) c.Arest[k] = (real)h->Arest[k];
+  const int nth = h->prm.closure == LBPWFA_WARMC ? h->K - 2 - h->prm.dim : 0;
+  c.ilam0 = (real)(h->prm.closure == LBPWFA_WARMC ? 1.0 / h->Arest[1] : 0.0);
+  for (int j = 0; j < 6; ++j) c.threst[j] = (real)(j < nth ? h->Arest[2 + h->prm.dim + j] / h->Arest[1] : 0.0);
 }
 
 StepParams step_params(const lbpwfa_s* h) {
@@ -165,6 +168,10 @@ StepParams step_params(const lbpwfa_s* h) {
   P.Eout = h->E[out].p;
   P.Bin = h->B[in].p;
   P.Bout = h->B[out].p;
+  P.Ein_lo = lo_of(h, h->E[in]);
+  P.Eout_lo = lo_of(h, h->E[out]);
+  P.Bin_lo = lo_of(h, h->B[in]);
+  P.Bout_lo = lo_of(h, h->B[out]);
   P.prev = h->prev.p;
   P.have_prev = h->have_prev;
   for (int a = 0; a < 3; ++a) P.n[a] = h->n[a];
@@ -255,7 +262,7 @@ int init_rest_state(lbpwfa_s* h) {
   if (h->prm.init_fields && h->prm.dim >= 2) {
     AuxParams A = aux_params(h);
     A.t = 0.0;
-    h->ks.init_fields(A, h->E[0].p, h->B[0].p, h->stream);
+    h->ks.init_fields(A, h->E[0].p, h->B[0].p, lo_of(h, h->E[0]), lo_of(h, h->B[0]), h->stream);
     CK_LAUNCH(h, "init_fields");
   }
   h->fields_from_driver = h->prm.init_fields && h->prm.dim >= 2;
@@ -408,7 +415,7 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
   if (pe != cudaSuccess) { fail_cuda(h, pe, "cudaFuncSetAttribute"); lbpwfa_destroy(h); return LBPWFA_ERR_CUDA; }
 
   const size_t pop_bytes = (size_t)h->K * h->Q * h->plane * h->store_sz;
-  const size_t fld_bytes = 3 * (size_t)h->plane * h->real_sz;
+  const size_t fld_bytes = 3 * (size_t)h->plane * h->real_sz * (h->real_sz == 4 ? 2 : 1);
   int r = LBPWFA_OK;
   for (int j = 0; j < 2 && r == LBPWFA_OK; ++j) {
     r = alloc(h, h->f[j], pop_bytes);
@@ -545,7 +552,8 @@ int lbpwfa_fields(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_
     const int m = nb - j0 < 4 ? nb - j0 : 4;
     int c4[4] = {0, 0, 0, 0}, b4[4] = {0, 0, 0, 0};
     for (int j = 0; j < m; ++j) { c4[j] = comps[j0 + j]; b4[j] = isb[j0 + j]; }
-    h->ks.export_fields(A, h->E[h->cur].p, h->B[h->cur].p, m, make_int4(c4[0], c4[1], c4[2], c4[3]),
+    h->ks.export_fields(A, h->E[h->cur].p, h->B[h->cur].p, lo_of(h, h->E[h->cur]), lo_of(h, h->B[h->cur]), m,
+                        make_int4(c4[0], c4[1], c4[2], c4[3]),
                         make_int4(b4[0], b4[1], b4[2], b4[3]), out + (size_t)j0 * h->ncell, h->stream);
     CK_LAUNCH(h, "export_fields_kernel launch");
   }
@@ -576,7 +584,8 @@ int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double*
     CK_LAUNCH(h, "import_pops_kernel launch");
   }
   if (Ed || Bd) {
-    h->ks.import_fields(A, Ed, Bd, h->E[h->cur].p, h->B[h->cur].p, h->stream);
+    h->ks.import_fields(A, Ed, Bd, h->E[h->cur].p, h->B[h->cur].p, lo_of(h, h->E[h->cur]), lo_of(h, h->B[h->cur]),
+                        h->stream);
     CK_LAUNCH(h, "import_fields_kernel launch");
     h->fields_from_driver = false;
   }
@@ -614,7 +623,8 @@ int lbpwfa_get_state(lbpwfa_t h, double* f, double* E, double* B, int dst_is_dev
       if (r != LBPWFA_OK) return r;
       out = (double*)h->scratch.p;
     }
-    h->ks.export_fields(A, h->E[h->cur].p, h->B[h->cur].p, 3, make_int4(0, 1, 2, 0),
+    h->ks.export_fields(A, h->E[h->cur].p, h->B[h->cur].p, lo_of(h, h->E[h->cur]), lo_of(h, h->B[h->cur]), 3,
+                        make_int4(0, 1, 2, 0),
                         make_int4(which, which, which, 0), out, h->stream);
     CK_LAUNCH(h, "export_fields_kernel launch");
     if (!dst_is_device) {
@@ -651,7 +661,9 @@ int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info) {
   const int dim = h->prm.dim;
   const int ne = dim == 1 ? 1 : (dim == 2 ? 2 : 3);
   const int nbf = dim == 1 ? 0 : (dim == 2 ? 1 : 3);
-  info->bytes_per_update = 2.0 * h->K * h->Q * h->store_sz + 2.0 * (ne + nbf + h->NPREV) * h->real_sz;
+  // FP32 fields: high and low parts
+  const double field_words = (ne + nbf) * (h->real_sz == 4 ? 2.0 : 1.0);
+  info->bytes_per_update = 2.0 * h->K * h->Q * h->store_sz + 2.0 * (field_words + h->NPREV) * h->real_sz;
   info->kernel_variant = h->use_persist ? 3 : (h->use_tma ? 2 : 1);
   return LBPWFA_OK;
 }
