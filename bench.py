@@ -63,8 +63,9 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
     ap.add_argument("--workload", default="2d_lec",
-                    choices=["2d_lec", "3d_warmc", "3d_warmc_128", "adjoint_2d_warmc"],
-                    help="2d_lec: 1024 x 512 LEC (default); 3d_warmc: 512 x 256 x 256 WARMC; "
+                    choices=["2d_lec", "2d_warmc", "3d_warmc", "3d_warmc_128", "adjoint_2d_warmc"],
+                    help="2d_lec: 1024 x 512 LEC (default); 2d_warmc: the same grid with the warm-plasma "
+                         "closure; 3d_warmc: 512 x 256 x 256 WARMC; "
                          "3d_warmc_128: 128^3 WARMC (small case for profiling); adjoint_2d_warmc: "
                          "forward + reverse sweep of the 512 x 256 WARMC adjoint case over --steps steps "
                          "(whole tape kept), for profiling")
@@ -266,7 +267,7 @@ def run_ours(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lb.load_library()
-    cfg = {"2d_lec": WORKLOAD_2D, "3d_warmc": CONFIG_3D,
+    cfg = {"2d_lec": WORKLOAD_2D, "2d_warmc": dict(WORKLOAD_2D, closure="warmc"), "3d_warmc": CONFIG_3D,
            "3d_warmc_128": dict(CONFIG_3D, n=(128, 128, 128), z0=2.0)}[a.workload]
     cfg = dict(cfg)
     stream = torch.cuda.Stream(device=dev)

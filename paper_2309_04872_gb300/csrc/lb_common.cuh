@@ -257,6 +257,16 @@ __device__ __forceinline__ real lec_pi_minus_1(real dn, real p2, real g, int D) 
   const real xe = pow_2_over_D<real>(x, D);
   return d * xe + d * (real(2) + d) / (xe * xe + xe + real(1));
 }
+// FP32 form: x^(2/3) enters only multiplied by d or in a denominator near 3,
+// so the hardware log2/exp2 (a few ulp) keeps Pi - 1 to a few ulp; the
+// reciprocals are correctly rounded.
+__device__ __forceinline__ float lec_pi_minus_1_f32(float dn, float p2, float ig, float g, int D) {
+  const float d = (dn - p2 * __frcp_rn(g + 1.0f)) * ig;
+  if (D == 1) return d * (3.0f + d * (3.0f + d));
+  const float x = 1.0f + d;
+  const float xe = exp2f((2.0f / 3.0f) * __log2f(x));
+  return d * xe + d * (2.0f + d) * __frcp_rn(fmaf(xe, xe, xe) + 1.0f);
+}
 
 // LEC transport velocity, Sec. 4.1: p^(0) = A_p / n, then
 // gamma^(k) = sqrt(1 + |p^(k)|^2), p^(k+1) = p^(0) / (1 + (1 + D/2) mu (n/gamma^(k))^(2/D)),
@@ -339,13 +349,16 @@ __device__ __forceinline__ void decode_lec_f32(float n, const float* Ap, float c
   const float ig = __frcp_rn(g);
 #pragma unroll
   for (int a = 0; a < DIM; ++a) u[a] = p[a] * ig;
-  const float x = n * ig;
-  Pi = x * pow_2_over_D<float>(x, D);
   if (pim1_out) {
+    // only Pi - 1 is wanted (central differences)
     float p2 = 0.0f;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) p2 = fmaf(p[a], p[a], p2);
-    *pim1_out = lec_pi_minus_1<float>(dn, p2, g, D);
+    *pim1_out = lec_pi_minus_1_f32(dn, p2, ig, g, D);
+    Pi = 1.0f + *pim1_out;
+  } else {
+    const float x = n * ig;
+    Pi = x * pow_2_over_D<float>(x, D);
   }
 }
 
