@@ -9,14 +9,13 @@ namespace lbp {
 
 // Tiles of the plain step kernel.  1D: 64 nodes per CTA spreads the 2048-node
 // run over 32 SMs.  3D: 32 x 4 x 4 keeps the decode halo at 2.4x the tile
-// (512 threads, register budget 128) where the closure fits that budget
-// (LEC in FP32/FP16S); the WARMC sources need more registers, so WARMC and
-// FP64 keep 32 x 4 x 2 (256 threads).
+// (512 threads, register budget 128; the rolled set loops fit it for both
+// closures).
 template <int DIM, int CL, int PR> struct Tile;
 template <int CL, int PR> struct Tile<1, CL, PR> { static constexpr int TZ = 64, TX = 1, TY = 1; };
 template <int CL, int PR> struct Tile<2, CL, PR> { static constexpr int TZ = 32, TX = 8, TY = 1; };
 template <int CL, int PR> struct Tile<3, CL, PR> {
-  static constexpr int TZ = 32, TX = 4, TY = (PR == PR_F64 || CL == CL_WARMC) ? 2 : 4;
+  static constexpr int TZ = 32, TX = 4, TY = 4;
 };
 
 inline unsigned grid1(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }

@@ -46,6 +46,14 @@ __device__ __forceinline__ real set_moment(const real* df) {
   return s;
 }
 
+// 3D models keep the loops over population sets rolled: one 19-velocity body
+// per loop instead of K (up to 11), so the step fits the instruction cache.
+// 2D models unroll them (2D WARMC, 8 x 9 populations, runs faster unrolled at
+// 110 registers than rolled at 63).
+template <int DIM, int K> struct RollSets {
+  static constexpr bool value = DIM == 3;
+};
+
 template <int DIM, int CL, int PR, int TZ, int TX, int TY>
 struct StepCfg {
   using M = Model<DIM, CL>;
@@ -332,11 +340,20 @@ __device__ __forceinline__ void decode_node(const StepParams& P, const StepConst
   using real = typename Prec<PR>::real;
   constexpr int K = M::K, Q = Lattice<DIM>::Q;
   real dA[K];
+  if constexpr (RollSets<DIM, K>::value) {
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+      real df[Q];
+      pull.template get<EDGE>(z, x, y, k, df);
+      dA[k] = set_moment<Q>(df);
+    }
+  } else {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    real df[Q];
-    pull.template get<EDGE>(z, x, y, k, df);
-    dA[k] = set_moment<Q>(df);
+    for (int k = 0; k < K; ++k) {
+      real df[Q];
+      pull.template get<EDGE>(z, x, y, k, df);
+      dA[k] = set_moment<Q>(df);
+    }
   }
   real rec[M::NM];
   decode_record<DIM, CL, real>(P, S, dA, rec);
@@ -406,15 +423,25 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
     const int ez = EDGE ? wrap_or_clamp(gz, P.n[0], P.periodic) : gz;
     const int ex = DIM >= 2 ? (EDGE ? wrap_or_clamp(gx, P.n[1], P.periodic) : gx) : 0;
     const int ey = DIM >= 3 ? (EDGE ? wrap_or_clamp(gy, P.n[2], P.periodic) : gy) : 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      real df[Q];
-      pull.template get<EDGE>(ez, ex, ey, k, df);
-      if constexpr (KEEP) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) keep[k * Q + i] = df[i];
+    if constexpr (RollSets<DIM, K>::value) {
+      static_assert(!KEEP, "rolled set loops keep no populations in registers");
+#pragma unroll 1
+      for (int k = 0; k < K; ++k) {
+        real df[Q];
+        pull.template get<EDGE>(ez, ex, ey, k, df);
+        dA_own[k] = set_moment<Q>(df);
       }
-      dA_own[k] = set_moment<Q>(df);
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        real df[Q];
+        pull.template get<EDGE>(ez, ex, ey, k, df);
+        if constexpr (KEEP) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) keep[k * Q + i] = df[i];
+        }
+        dA_own[k] = set_moment<Q>(df);
+      }
     }
     real rec[M::NM];
     decode_record<DIM, CL, real>(P, S, dA_own, rec);
@@ -703,8 +730,9 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   const real itau = S.inv_tau, omt = real(1) - S.inv_tau;
   const real base = real(-1.5) * usq;
   store* fout = reinterpret_cast<store*>(P.fout);
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
+  // one population set: pull (or the kept values), relax, store; the source
+  // dt F_k is evaluated after the pull (dtF_of), as in a plain loop body
+  auto collide_set = [&](int k, real Arest_k, float sc, float isc, auto dtF_of) {
     real df[Q];
     real dA;
     if constexpr (KEEP) {
@@ -715,9 +743,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       pull.template get<EDGE>(gz, gx, gy, k, df);
       dA = set_moment<Q>(df);
     }
-    const real A = S.Arest[k] + dA;
-    const real dtF = dt * source(k);
-    const float sc = P.scale[k], isc = P.inv_scale[k];
+    const real A = Arest_k + dA;
+    const real dtF = dtF_of();
     store* fk = fout + (size_t)k * Q * (size_t)P.plane;
     real moved = 0;
 #pragma unroll
@@ -734,6 +761,24 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       moved = add_rn(moved, Codec<PR>::store_q(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF, sc, isc));
     }
     Codec<PR>::store(fk, id, sub_rn(add_rn(dA, dtF), moved), sc);
+  };
+  if constexpr (RollSets<DIM, K>::value) {
+    // per-set values gathered first (the rolled loop indexes small local
+    // arrays, never the launch parameters)
+    real Fk[K], Ak[K];
+    float sck[K], isck[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      Fk[k] = dt * source(k);
+      Ak[k] = S.Arest[k];
+      sck[k] = P.scale[k];
+      isck[k] = P.inv_scale[k];
+    }
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) collide_set(k, Ak[k], sck[k], isck[k], [&] { return Fk[k]; });
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) collide_set(k, S.Arest[k], P.scale[k], P.inv_scale[k], [&] { return dt * source(k); });
   }
 }
 
@@ -768,7 +813,7 @@ __device__ __forceinline__ void prefetch_own(const StepParams& P, FieldPF<real>&
 // dimension, open or periodic boundaries).
 template <int DIM, int CL, int PR, int TZ, int TX, int TY>
 __global__ void __launch_bounds__(TZ* TX* TY)
-lb_step_kernel(const StepParams P) {
+lb_step_kernel(const __grid_constant__ StepParams P) {
   using real = typename Prec<PR>::real;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GlobalPull<DIM, CL, PR> pull{P};
