@@ -70,8 +70,9 @@ def _args():
                          "forward + reverse sweep of the 512 x 256 WARMC adjoint case over --steps steps "
                          "(whole tape kept), for profiling")
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="0: automatic (TMA box per CTA in 2D), 1: plain global-memory pull kernel, "
-                         "2: TMA box per CTA, 3: persistent CTAs with two TMA boxes in flight")
+                    help="0: automatic (2D LEC: persistent TMA CTAs in FP32 and FP16S, a TMA box per CTA "
+                         "in FP64), 1: plain global-memory pull kernel, 2: TMA box per CTA, "
+                         "3: persistent CTAs that refill their TMA box after the decode phase")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-precision mode table")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -338,10 +339,10 @@ def run_ours(a):
         modes = {}
         for prec in ("fp64", "fp32", "fp16s"):
             for mu in (1e-3, 1e-2):
-                for variant in (0, 1, 3):
+                for variant in (0, 1, 2, 3):
                     steps = 300 if prec == "fp64" else 1000
                     r = measure(prec, steps, 5, mu=mu, variant=variant)
-                    key = f"lec_{prec}_mu{mu:g}" + {0: "", 1: "_plain", 3: "_persistent"}[variant]
+                    key = f"lec_{prec}_mu{mu:g}" + {0: "", 1: "_plain", 2: "_box", 3: "_persistent"}[variant]
                     modes[key] = {"mlups": round(r["mlups"], 2), "ms_per_step": round(r["ms"], 5),
                                   "achieved_gbs": round(r["gbs"], 1), "frac_of_measured_hbm": round(r["frac"], 4),
                                   "bytes_per_update": r["bytes_per_update"], "steps": steps, "kernel": r["kernel"]}

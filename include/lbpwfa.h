@@ -102,14 +102,18 @@ typedef struct {
   void* stream;            /* cudaStream_t to queue work on; NULL = a stream
                               owned by the library */
   int kernel_variant;      /* 0: automatic (2D open-boundary LEC runs stage
-                              each tile's populations in shared memory with
-                              one TMA bulk-tensor load per CTA; the rest,
+                              each tile's populations in shared memory by
+                              TMA bulk-tensor loads: FP32 and FP16S with
+                              persistent refilling CTAs (variant 3), FP64
+                              with one box per CTA (variant 2); the rest,
                               WARMC included, pull from global memory, which
                               measures faster for its 72 population planes);
                               1: plain global-memory pull; 2: one TMA box per
                               CTA (2D open boundaries);
-                              3: LEC 2D with one persistent CTA per SM and two
-                              TMA boxes in flight.  All compute the same step. */
+                              3: LEC 2D with persistent CTAs, each refilling
+                              its TMA box with its next tile as soon as the
+                              decode phase has read it.  All compute the
+                              same step. */
 } lbpwfa_params;
 
 typedef struct {

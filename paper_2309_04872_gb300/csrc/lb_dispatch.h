@@ -36,9 +36,10 @@ struct KernelSet {
   size_t tma_smem;
   cudaError_t (*prepare_tma)();
   void (*step_tma)(const StepParams&, const void* tensor_map, dim3 grid, cudaStream_t);
-  // persistent double-buffered TMA 2D step (LEC); has_persist == false when not built
-  bool has_persist;
-  int per_tz, per_tx;
+  // persistent TMA 2D step (LEC), per_ctas CTAs per SM; has_persist == false when not built;
+  // persist_auto: the automatic kernel choice takes it
+  bool has_persist, persist_auto;
+  int per_tz, per_tx, per_ctas;
   int per_box[3];
   size_t per_smem;
   cudaError_t (*prepare_persist)();

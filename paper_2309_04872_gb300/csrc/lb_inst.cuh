@@ -91,8 +91,10 @@ struct Impl {
   }
   static void fill(KernelSet* ks) {
     ks->has_persist = kPersist;
+    ks->persist_auto = kPersist && PC::automatic;
     ks->per_tz = PC::TZ;
     ks->per_tx = PC::TX;
+    ks->per_ctas = PC::MINB;
     ks->per_box[0] = PC::BZ;
     ks->per_box[1] = PC::BX;
     ks->per_box[2] = PC::BK;

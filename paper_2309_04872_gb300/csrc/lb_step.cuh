@@ -369,12 +369,27 @@ __device__ __forceinline__ void decode_node(const StepParams& P, const StepConst
 // In 1D and 2D the caller loads the own node's fields (FieldPF) before the
 // populations arrive; in 3D, where registers are scarce, they are loaded here
 // just before they are used.
+// Node h of the 2D decode halo ring (region coordinates rz, rx).
+template <int RZ, int RX>
+__device__ __forceinline__ void ring_node_2d(int h, int& rz, int& rx) {
+  if (h < RZ) { rz = h; rx = 0; }
+  else if (h < 2 * RZ) { rz = h - RZ; rx = RX - 1; }
+  else { const int j = h - 2 * RZ; rz = (j & 1) ? RZ - 1 : 0; rx = 1 + (j >> 1); }
+}
+
+// `after_decode` runs on every thread right after the barrier that ends the
+// decode phase: when the own populations stay in registers (K*Q <= 32) the
+// pull source is not read again, so a caller may start refilling it there.
 template <int DIM> struct EarlyFields { static constexpr bool value = DIM <= 2; };
 
-template <int DIM, int CL, int PR, int TZ, int TX, int TY, bool EDGE, class Pull>
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+template <int DIM, int CL, int PR, int TZ, int TX, int TY, bool EDGE, class Pull, class Hook = NoHook>
 __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* smem, const Pull& pull,
                                           FieldPF<typename Prec<PR>::real>& F, int tile_z, int tile_x,
-                                          int tile_y) {
+                                          int tile_y, const Hook& after_decode = Hook()) {
   using C = StepCfg<DIM, CL, PR, TZ, TX, TY>;
   using M = Model<DIM, CL>;
   using L = Lattice<DIM>;
@@ -458,41 +473,39 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       }
     }
   }
-  // halo ring
-  if constexpr (DIM <= 2) {
-    constexpr int NRING = NR - NT;
-    for (int h = tid; h < NRING; h += NT) {
-      int rz, rx = 0;
-      if constexpr (DIM == 1) {
-        rz = h == 0 ? 0 : RZ - 1;
-      } else {
-        if (h < RZ) { rz = h; rx = 0; }
-        else if (h < 2 * RZ) { rz = h - RZ; rx = RX - 1; }
-        else { const int j = h - 2 * RZ; rz = (j & 1) ? RZ - 1 : 0; rx = 1 + (j >> 1); }
+  {
+    // halo ring
+    if constexpr (DIM <= 2) {
+      constexpr int NRING = NR - NT;
+      for (int h = tid; h < NRING; h += NT) {
+        int rz, rx = 0;
+        if constexpr (DIM == 1) rz = h == 0 ? 0 : RZ - 1;
+        else ring_node_2d<RZ, RX>(h, rz, rx);
+        const int r = rz + RZ * rx;
+        int z = oz + rz, x = ox + rx;
+        if (EDGE) {
+          z = wrap_or_clamp(z, P.n[0], P.periodic);
+          if (DIM >= 2) x = wrap_or_clamp(x, P.n[1], P.periodic);
+        }
+        decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, 0, smac, NR, r);
       }
-      const int r = rz + RZ * rx;
-      int z = oz + rz, x = ox + rx;
-      if (EDGE) {
-        z = wrap_or_clamp(z, P.n[0], P.periodic);
-        if (DIM >= 2) x = wrap_or_clamp(x, P.n[1], P.periodic);
+    } else {
+      // 3D: stride over the region and skip the interior
+      for (int r = tid; r < NR; r += NT) {
+        const int rz = r % RZ, rx = (r / RZ) % RX, ry = r / (RZ * RX);
+        if (rz >= 1 && rz <= TZ && rx >= 1 && rx <= TX && ry >= 1 && ry <= TY) continue;
+        int z = oz + rz, x = ox + rx, y = oy + ry;
+        if (EDGE) {
+          z = wrap_or_clamp(z, P.n[0], P.periodic);
+          x = wrap_or_clamp(x, P.n[1], P.periodic);
+          y = wrap_or_clamp(y, P.n[2], P.periodic);
+        }
+        decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, y, smac, NR, r);
       }
-      decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, 0, smac, NR, r);
-    }
-  } else {
-    // 3D: stride over the region and skip the interior
-    for (int r = tid; r < NR; r += NT) {
-      const int rz = r % RZ, rx = (r / RZ) % RX, ry = r / (RZ * RX);
-      if (rz >= 1 && rz <= TZ && rx >= 1 && rx <= TX && ry >= 1 && ry <= TY) continue;
-      int z = oz + rz, x = ox + rx, y = oy + ry;
-      if (EDGE) {
-        z = wrap_or_clamp(z, P.n[0], P.periodic);
-        x = wrap_or_clamp(x, P.n[1], P.periodic);
-        y = wrap_or_clamp(y, P.n[2], P.periodic);
-      }
-      decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, y, smac, NR, r);
     }
   }
   __syncthreads();
+  after_decode();
 
   // ---------------- B: E^{n+1/2} on the slots of tile + low halo ----------
   if constexpr (!EarlyFields<DIM>::value) {

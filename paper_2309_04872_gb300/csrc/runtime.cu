@@ -300,7 +300,8 @@ int launch_step(lbpwfa_s* h, void* tape) {
   if (h->use_persist) {
     const int ntz = (h->n[0] + h->ks.per_tz - 1) / h->ks.per_tz;
     const int ntiles = ntz * ((h->n[1] + h->ks.per_tx - 1) / h->ks.per_tx);
-    const int pgrid = ntiles < h->num_sms ? ntiles : h->num_sms;
+    const int slots = h->num_sms * h->ks.per_ctas;
+    const int pgrid = ntiles < slots ? ntiles : slots;
     h->ks.step_persist(P, &h->maps[h->cur], pgrid, ntz, ntiles, h->stream);
   } else if (h->use_tma) {
     h->ks.step_tma(P, &h->maps[h->cur], grid, h->stream);
@@ -437,7 +438,11 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
   }
   const bool tma_ok = dim == 2 && p->boundary == LBPWFA_OPEN;
-  h->use_persist = p->kernel_variant == 3 && tma_ok && h->ks.has_persist && h->num_sms > 0;
+  // automatic choice for LEC: the persistent refilling CTAs where the tile
+  // table marks them faster, else one TMA box per CTA; WARMC's 72-plane box
+  // leaves two CTAs per SM and the global-memory pull is faster there
+  const bool persist_auto = p->kernel_variant == 0 && p->closure == LBPWFA_LEC && h->ks.persist_auto;
+  h->use_persist = (p->kernel_variant == 3 || persist_auto) && tma_ok && h->ks.has_persist && h->num_sms > 0;
   if (h->use_persist) {
     cudaError_t e = h->ks.prepare_persist();
     bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0], h->ks.per_box) &&
@@ -447,8 +452,6 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
       h->use_persist = false;
     }
   }
-  // automatic choice: the TMA box pays off for LEC (27 planes); the WARMC box
-  // (72 planes) leaves two CTAs per SM and the global-memory pull is faster
   const bool tma_auto = p->kernel_variant == 0 && p->closure == LBPWFA_LEC;
   h->use_tma = !h->use_persist && (tma_auto || p->kernel_variant == 2) && tma_ok && h->ks.has_tma;
   if (h->use_tma) {
