@@ -94,7 +94,9 @@ typedef struct {
   int profile_len;         /* >= 2 when profile != NULL */
   double profile_dz;       /* > 0 when profile != NULL */
   int precision;           /* population storage: FP64, FP32 (deviation from
-                              w_i A_rest), FP16S (binary16 deviation, scaled) */
+                              w_i A_rest), FP16S (binary16 deviation, scaled;
+                              the rest population of each set keeps a
+                              second binary16 with its rounding residual) */
   int boundary;            /* LBPWFA_OPEN (Eq. open-bc; conducting transverse
                               walls) or LBPWFA_PERIODIC (all axes) */
   int init_fields;         /* 1: start from the v -> c field of the driver

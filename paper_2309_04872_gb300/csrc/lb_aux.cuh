@@ -140,7 +140,11 @@ __global__ void import_pops_kernel(AuxParams A, const double* fin, typename Prec
       long long src = c;
       if (A.periodic || bulk) src = (long long)s[0] + (long long)A.n[0] * ((long long)s[1] + (long long)A.n[1] * s[2]);
       const double v = fin[((long long)k * L::Q + i) * A.ncell + src] - L::w(i) * A.Arest[k];
-      Codec<PR>::store(out + ((long long)k * L::Q + i) * A.plane, p, (typename Prec<PR>::real)v, A.scale[k]);
+      if (i == 0)
+        Codec<PR>::store0(out + (long long)k * L::Q * A.plane, p, out + ((long long)M::K * L::Q + k) * A.plane, p,
+                          (typename Prec<PR>::real)v, A.scale[k]);
+      else
+        Codec<PR>::store(out + ((long long)k * L::Q + i) * A.plane, p, (typename Prec<PR>::real)v, A.scale[k]);
     }
   }
 }
@@ -166,7 +170,11 @@ __global__ void export_pops_kernel(AuxParams A, const typename Prec<PR>::store* 
         s[a] -= L::c(i, a);
         if (A.periodic) s[a] = s[a] < 0 ? s[a] + A.n[a] : (s[a] >= A.n[a] ? s[a] - A.n[a] : s[a]);
       }
-      const double dv = (double)Codec<PR>::load(fs + ((long long)k * L::Q + i) * A.plane, padded(A, s), A.inv_scale[k]);
+      const long long ps = padded(A, s);
+      const double dv =
+          i == 0 ? (double)Codec<PR>::load0(fs + (long long)k * L::Q * A.plane, ps,
+                                            fs + ((long long)M::K * L::Q + k) * A.plane, ps, A.inv_scale[k])
+                 : (double)Codec<PR>::load(fs + ((long long)k * L::Q + i) * A.plane, ps, A.inv_scale[k]);
       out[((long long)k * L::Q + i) * A.ncell + c] = L::w(i) * A.Arest[k] + dv;
     }
   }
@@ -191,7 +199,10 @@ __device__ __forceinline__ void advected_d(const AuxParams& A, const typename Pr
         q[a] -= L::c(i, a);
         if (A.periodic) q[a] = q[a] < 0 ? q[a] + A.n[a] : (q[a] >= A.n[a] ? q[a] - A.n[a] : q[a]);
       }
-      s += (double)Codec<PR>::load(fs + ((long long)k * L::Q + i) * A.plane, padded(A, q), A.inv_scale[k]);
+      const long long pq = padded(A, q);
+      s += i == 0 ? (double)Codec<PR>::load0(fs + (long long)k * L::Q * A.plane, pq,
+                                             fs + ((long long)M::K * L::Q + k) * A.plane, pq, A.inv_scale[k])
+                  : (double)Codec<PR>::load(fs + ((long long)k * L::Q + i) * A.plane, pq, A.inv_scale[k]);
     }
     Av[k] = A.Arest[k] + s;
   }

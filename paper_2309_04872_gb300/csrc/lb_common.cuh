@@ -174,23 +174,42 @@ template <> __device__ __forceinline__ const StepConst<double>& consts<double>(c
 // Storage codec: populations are kept as deviations from w_i A_rest,k.
 template <int PR> struct Codec;
 // store_q stores v and returns the value a later load reads back.
+// load0 / store0 access the rest population (velocity 0) of a set: the
+// reduced-precision format keeps a low part for it in plane K*Q + k of the
+// buffer (lo, element j); the other formats ignore lo.
 template <> struct Codec<PR_F64> {
+  static constexpr int kLoPlanes = 0;  // extra planes per population set
   __device__ static double load(const double* p, long long i, float) { return __ldg(p + i); }
   __device__ static void store(double* p, long long i, double v, float) { p[i] = v; }
   __device__ static double store_q(double* p, long long i, double v, float, float) {
     p[i] = v;
     return v;
   }
+  __device__ static double load0(const double* p, long long i, const double*, long long, float) {
+    return __ldg(p + i);
+  }
+  __device__ static void store0(double* p, long long i, double*, long long, double v, float) { p[i] = v; }
 };
 template <> struct Codec<PR_F32> {
+  static constexpr int kLoPlanes = 0;
   __device__ static float load(const float* p, long long i, float) { return __ldg(p + i); }
   __device__ static void store(float* p, long long i, float v, float) { p[i] = v; }
   __device__ static float store_q(float* p, long long i, float v, float, float) {
     p[i] = v;
     return v;
   }
+  __device__ static float load0(const float* p, long long i, const float*, long long, float) {
+    return __ldg(p + i);
+  }
+  __device__ static void store0(float* p, long long i, float*, long long, float v, float) { p[i] = v; }
 };
+// Binary16 of the scaled deviation.  The rest population takes the remainder
+// of its set's moment in the collision, so its rounding is the one error of
+// the node's moment that does not cancel; it carries a second binary16 with
+// its rounding residual scaled by 2^11 (together about 22 significant bits).
 template <> struct Codec<PR_F16S> {
+  static constexpr int kLoPlanes = 1;
+  static constexpr float kLoScale = 2048.0f, kLoInv = 1.0f / 2048.0f;
   __device__ static float load(const __half* p, long long i, float inv_s) {
     return __half2float(__ldg(p + i)) * inv_s;
   }
@@ -201,6 +220,20 @@ template <> struct Codec<PR_F16S> {
     const __half h = __float2half_rn(v * s);
     p[i] = h;
     return __half2float(h) * inv_s;
+  }
+  __device__ static float join(__half hi, __half lo, float inv_s) {
+    return fmaf(__half2float(lo), kLoInv, __half2float(hi)) * inv_s;
+  }
+  __device__ static float load0(const __half* p, long long i, const __half* lo, long long j, float inv_s) {
+    return join(__ldg(p + i), __ldg(lo + j), inv_s);
+  }
+  __device__ static void store0(__half* p, long long i, __half* lo, long long j, float v, float s) {
+    const float x = v * s;
+    const __half h = __float2half_rn(x);
+    p[i] = h;
+    // x - h is exact in FP32: h is x rounded to 11 significant bits, and the
+    // difference holds the rest of x's bits
+    lo[j] = __float2half_rn(__fsub_rn(x, __half2float(h)) * kLoScale);
   }
 };
 

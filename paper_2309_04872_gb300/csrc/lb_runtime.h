@@ -32,6 +32,7 @@ struct lbpwfa_s {
   double* profile_d = nullptr;
   lbp::KernelSet ks{};
   int K = 0, Q = 0, NPREV = 0;
+  int NPL = 0;  // planes of a population buffer (K*Q, plus K low parts in FP16S)
   int n[3] = {1, 1, 1};
   int nzp = 0;
   long long plane = 0, ncell = 0;

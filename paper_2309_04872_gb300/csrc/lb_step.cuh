@@ -96,7 +96,14 @@ __device__ __forceinline__ void pulled_dev(const StepParams& P, int z, int x, in
       if (DIM >= 2) sx = sx < 0 ? sx + P.n[1] : (sx >= P.n[1] ? sx - P.n[1] : sx);
       if (DIM >= 3) sy = sy < 0 ? sy + P.n[2] : (sy >= P.n[2] ? sy - P.n[2] : sy);
     }
-    df[i] = Codec<PR>::load(f, i * pl + cell_index32(P, sz, sx, sy), is);
+    if (i == 0) {
+      // rest population (with its low part in the reduced-precision format)
+      const store* lo = (const store*)P.fin + ((size_t)Model<DIM, CL>::K * L::Q + k) * (size_t)P.plane;
+      const int c0 = cell_index32(P, sz, sx, sy);
+      df[0] = Codec<PR>::load0(f, c0, lo, c0, is);
+    } else {
+      df[i] = Codec<PR>::load(f, i * pl + cell_index32(P, sz, sx, sy), is);
+    }
   }
 }
 
@@ -773,7 +780,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       moved = add_rn(moved, Codec<PR>::store_q(fk, i * pl + id, df[i] * omt + (even + odd) * itau + wF, sc, isc));
       moved = add_rn(moved, Codec<PR>::store_q(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF, sc, isc));
     }
-    Codec<PR>::store(fk, id, sub_rn(add_rn(dA, dtF), moved), sc);
+    Codec<PR>::store0(fk, id, fout + ((size_t)K * Q + k) * (size_t)P.plane, id, sub_rn(add_rn(dA, dtF), moved), sc);
   };
   if constexpr (RollSets<DIM, K>::value) {
     // per-set values gathered first (the rolled loop indexes small local

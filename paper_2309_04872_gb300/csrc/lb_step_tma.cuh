@@ -61,7 +61,8 @@ struct TmaCfg2D {
   static constexpr int TZ = TmaTile2D<CL, PR>::TZ, TX = TmaTile2D<CL, PR>::TX, MINB = TmaTile2D<CL, PR>::MINB;
   static constexpr bool enabled = TZ > 0;
   static constexpr int HZ = 16 / (int)sizeof(store);
-  static constexpr int BZ = TZ + 2 * HZ, BX = TX + 4, BK = M::K * M::Q;
+  // K*Q population planes, then the rest populations' low parts (FP16S)
+  static constexpr int KQ = M::K * M::Q, BZ = TZ + 2 * HZ, BX = TX + 4, BK = KQ + M::K * Codec<PR>::kLoPlanes;
   static constexpr size_t box_bytes = (size_t)BZ * BX * BK * sizeof(store);
   static constexpr size_t box_pad = (box_bytes + 127) / 128 * 128;
   using Body = StepCfg<2, CL, PR, (TZ > 0 ? TZ : 1), (TX > 0 ? TX : 1), 1>;
@@ -90,6 +91,11 @@ struct SmemPull2D {
       const store v = bk[(i * T::BX + (bx - L::c(i, 1))) * T::BZ + (bz - L::c(i, 0))];
       if constexpr (PR == PR_F16S) df[i] = __half2float(v) * is;
       else df[i] = v;
+    }
+    if constexpr (Codec<PR>::kLoPlanes > 0) {
+      // the rest population with its low part (staged after the K*Q planes)
+      const store* lo = box + ((size_t)T::KQ + k) * T::BX * T::BZ;
+      df[0] = Codec<PR>::join(bk[bx * T::BZ + bz], lo[bx * T::BZ + bz], is);
     }
   }
 };
@@ -161,7 +167,8 @@ struct PersistCfg2D {
   static constexpr bool automatic = enabled && PersistTile2D<CL, PR>::AUTO != 0;
   static_assert(!enabled || M::K * Lattice<2>::Q <= 32, "the box is refilled after the decode phase");
   static constexpr int HZ = 16 / (int)sizeof(store);
-  static constexpr int BZ = TZ + 2 * HZ, BX = TX + 4, BK = M::K * M::Q;
+  // K*Q population planes, then the rest populations' low parts (FP16S)
+  static constexpr int KQ = M::K * M::Q, BZ = TZ + 2 * HZ, BX = TX + 4, BK = KQ + M::K * Codec<PR>::kLoPlanes;
   static constexpr size_t box_bytes = (size_t)BZ * BX * BK * sizeof(store);
   static constexpr size_t box_pad = (box_bytes + 127) / 128 * 128;
   using Body = StepCfg<2, CL, PR, (TZ > 0 ? TZ : 1), (TX > 0 ? TX : 1), 1>;
@@ -188,6 +195,11 @@ struct SmemPullBox2D {
       const store v = bk[(i * T::BX + (bx - L::c(i, 1))) * T::BZ + (bz - L::c(i, 0))];
       if constexpr (PR == PR_F16S) df[i] = __half2float(v) * is;
       else df[i] = v;
+    }
+    if constexpr (Codec<PR>::kLoPlanes > 0) {
+      // the rest population with its low part (staged after the K*Q planes)
+      const store* lo = box + ((size_t)T::KQ + k) * T::BX * T::BZ;
+      df[0] = Codec<PR>::join(bk[bx * T::BZ + bz], lo[bx * T::BZ + bz], is);
     }
   }
 };

@@ -221,7 +221,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Tensor map of one population buffer viewed as [K*Q planes][nx rows][nzp]:
+// Tensor map of one population buffer viewed as [NPL planes][nx rows][nzp]:
 // the step's box is (z, x, planes) = ks.tma_box.
 bool make_pop_map(lbpwfa_s* h, void* base, CUtensorMap* map, const int* boxdim) {
   auto enc = encode_fn();
@@ -229,7 +229,7 @@ bool make_pop_map(lbpwfa_s* h, void* base, CUtensorMap* map, const int* boxdim) 
   const cuuint64_t es = (cuuint64_t)h->ks.tma_elem_bytes;
   const CUtensorMapDataType dt = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                : (es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
-  cuuint64_t dims[3] = {(cuuint64_t)h->nzp, (cuuint64_t)h->n[1], (cuuint64_t)h->K * h->Q};
+  cuuint64_t dims[3] = {(cuuint64_t)h->nzp, (cuuint64_t)h->n[1], (cuuint64_t)h->NPL};
   cuuint64_t strides[2] = {(cuuint64_t)h->nzp * es, (cuuint64_t)h->plane * es};
   cuuint32_t box[3] = {(cuuint32_t)boxdim[0], (cuuint32_t)boxdim[1], (cuuint32_t)boxdim[2]};
   cuuint32_t estr[3] = {1, 1, 1};
@@ -415,7 +415,9 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
   cudaError_t pe = h->ks.prepare();
   if (pe != cudaSuccess) { fail_cuda(h, pe, "cudaFuncSetAttribute"); lbpwfa_destroy(h); return LBPWFA_ERR_CUDA; }
 
-  const size_t pop_bytes = (size_t)h->K * h->Q * h->plane * h->store_sz;
+  // FP16S: one more plane per set for the rest population's low part
+  h->NPL = h->K * h->Q + (p->precision == LBPWFA_FP16S ? h->K : 0);
+  const size_t pop_bytes = (size_t)h->NPL * h->plane * h->store_sz;
   const size_t fld_bytes = 3 * (size_t)h->plane * h->real_sz * (h->real_sz == 4 ? 2 : 1);
   int r = LBPWFA_OK;
   for (int j = 0; j < 2 && r == LBPWFA_OK; ++j) {
@@ -666,7 +668,7 @@ int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info) {
   const int nbf = dim == 1 ? 0 : (dim == 2 ? 1 : 3);
   // FP32 fields: high and low parts
   const double field_words = (ne + nbf) * (h->real_sz == 4 ? 2.0 : 1.0);
-  info->bytes_per_update = 2.0 * h->K * h->Q * h->store_sz + 2.0 * (field_words + h->NPREV) * h->real_sz;
+  info->bytes_per_update = 2.0 * h->NPL * h->store_sz + 2.0 * (field_words + h->NPREV) * h->real_sz;
   info->kernel_variant = h->use_persist ? 3 : (h->use_tma ? 2 : 1);
   return LBPWFA_OK;
 }

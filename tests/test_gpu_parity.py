@@ -244,9 +244,14 @@ def test_rest_state_is_exact_in_shifted_storage(prec, dim, closure):
         assert np.all(A[k] == np.float64(np.float32(rest[k])) ) or np.all(A[k] == rest[k])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_mass_conservation_periodic(prec):
-    cfg = _cfg(2, "warmc", "periodic")
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+def test_mass_conservation_periodic(prec, closure):
+    """Total mass after 50 steps.  The rest population takes the remainder
+    of each set's moment, so only its own rounding changes the mass: FP32
+    round-off in FP32, and in FP16S the rounding of the rest population's
+    high + low pair (about 22 bits) plus the FP32 remainder arithmetic."""
+    cfg = _cfg(2, closure, "periodic")
     orc = O.Oracle(cfg)
     f, E, B = _random_state(orc, 5, cfg["mu"])
     with lb.Run(cfg, prec) as run:
@@ -255,8 +260,35 @@ def test_mass_conservation_periodic(prec):
         run.step(50)
         m1, _, bad = run.reduce()
         assert bad == 0
-        tol = 1e-12 if prec == "fp64" else 1e-6
+        # measured 5e-10 (FP32) and 6e-11 (FP16S); without the low part of
+        # the rest population the FP16S drift is of order 1e-6
+        tol = {"fp64": 1e-12, "fp32": 1e-8, "fp16s": 1e-8}[prec]
+        print(f"mass drift {prec} {closure}: {abs(m1 - m0) / abs(m0):.3e}")
         assert abs(m1 - m0) <= tol * abs(m0)
+
+
+# 2D driver workload of 1024 x 512 cells (dx = 0.05, C = 0.1, mu = 1e-2,
+# n_b/n_0 = 0.1, sigma_z = 1, sigma_r = 0.5), 2000 steps
+_WAKE_2D = dict(dim=2, n=(1024, 512), dx=0.05, courant=0.1, tau=0.53, closure="lec", dv=3, mu=1e-2,
+                alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=4.0, boundary="open", init_fields=True)
+
+
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+def test_reduced_precision_wake_after_2000_steps(closure):
+    """Relative L2 error of n - 1 and E_z against the FP64 path: FP32 storage
+    within 1e-6, FP16-shifted storage within 1e-3."""
+    cfg = dict(_WAKE_2D, closure=closure)
+    out = {}
+    for prec in ("fp64", "fp32", "fp16s"):
+        with lb.Run(cfg, prec) as run:
+            run.step(2000)
+            out[prec] = (run.moments(lb.M_N)[0] - 1.0, run.fields(lb.F_EZ)[0])
+    n_ref, e_ref = out["fp64"]
+    for prec, tol in (("fp32", 1e-6), ("fp16s", 1e-3)):
+        n1, ez = out[prec]
+        en = np.linalg.norm(n1 - n_ref) / np.linalg.norm(n_ref)
+        ee = np.linalg.norm(ez - e_ref) / np.linalg.norm(e_ref)
+        assert en <= tol and ee <= tol, (prec, en, ee)
 
 
 def test_reduce_matches_oracle():
@@ -316,11 +348,19 @@ def test_zero_steps_and_edge_sizes():
 # ---------------------------------------------------------------------------
 # The 2D kernels (persistent TMA, TMA box per CTA, plain) compute the same step
 # ---------------------------------------------------------------------------
+# Runs on the same kernel are bit-identical.  Different kernels inline the same
+# step source but are optimised separately, and the compiler may fuse
+# multiply-adds differently in each, so they agree to the storage precision's
+# round-off (relative to the largest deviation from rest); on most
+# combinations they are bit-identical as well.
+_ROUNDOFF = {"fp64": 1e-12, "fp32": 1e-5, "fp16s": 1e-5}
+
+
 @pytest.mark.parametrize("closure", ["lec", "warmc"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
 # 700 x 300: more tiles than persistent CTAs, so those CTAs refill their box
 @pytest.mark.parametrize("n", [(131, 37), (300, 70), (700, 300)])
-def test_2d_kernel_variants_agree_bitwise(closure, prec, n):
+def test_2d_kernel_variants_agree(closure, prec, n):
     cfg = _cfg(2, closure, "open", n=n)
     orc = O.Oracle(cfg)
     f, E, B = _random_state(orc, 77, cfg["mu"])
@@ -330,15 +370,21 @@ def test_2d_kernel_variants_agree_bitwise(closure, prec, n):
     auto = (2 if prec == "fp64" else 3) if closure == "lec" else 1
     expect = {0: auto, 1: 1, 2: 2 if staged else 1, 3: 3 if closure == "lec" else 1}
     out = []
-    for variant in (0, 1, 2, 3):
+    for variant in (0, 1, 2, 3, 0):
         with lb.Run(cfg, prec, variant=variant) as run:
             assert run.info().kernel_variant == expect[variant]
             run.set_state(f, E, B)
             run.step(17)
             out.append((run.advected(), run.fields()))
-    for v in (1, 2, 3):
-        assert np.array_equal(out[0][0], out[v][0])
-        assert np.array_equal(out[0][1], out[v][1])
+    rest = orc.rest_advected()[:, None]
+    dev = np.max(np.abs(out[0][0] - rest))
+    fmax = np.max(np.abs(out[0][1]))
+    for v, variant in enumerate((0, 1, 2, 3, 0)):
+        if expect[variant] == expect[0]:
+            assert np.array_equal(out[0][0], out[v][0]) and np.array_equal(out[0][1], out[v][1]), variant
+        else:
+            assert np.max(np.abs(out[v][0] - out[0][0])) <= _ROUNDOFF[prec] * dev, variant
+            assert np.max(np.abs(out[v][1] - out[0][1])) <= _ROUNDOFF[prec] * fmax, variant
 
 
 @pytest.mark.parametrize("prec,tol,floor", [("fp64", 1e-12, 1e-13), ("fp32", 1e-4, 1e-7)])
