@@ -10,15 +10,21 @@ template <int DIM> struct AdjTile;
 template <> struct AdjTile<1> { static constexpr int TZ = 128, TX = 1; };
 template <> struct AdjTile<2> { static constexpr int TZ = 32, TX = 8; };
 
+// Resident CTAs per SM the register budget is held to (latency-bound
+// gathers want warps; FP32 WARMC 2D, 1000-step sweep: 1/1 CTAs 117 ms,
+// 2/2 103 ms, 3/3 107 ms, 3/4 101 ms); FP64 unconstrained.
+template <typename real> struct AdjMinBlocks { static constexpr int LOCAL = 1, FIELD = 1; };
+template <> struct AdjMinBlocks<float> { static constexpr int LOCAL = 3, FIELD = 4; };
+
 template <int DIM, int CL, int PR>
 struct AdjImpl {
   using real = typename Prec<PR>::real;
   using T = AdjTile<DIM>;
   static void local(const AdjParams& A, dim3 g, cudaStream_t s) {
-    adj_local_kernel<DIM, CL, real, T::TZ, T::TX><<<g, T::TZ * T::TX, 0, s>>>(A);
+    adj_local_kernel<DIM, CL, real, T::TZ, T::TX, AdjMinBlocks<real>::LOCAL><<<g, T::TZ * T::TX, 0, s>>>(A);
   }
   static void field(const AdjParams& A, dim3 g, cudaStream_t s) {
-    adj_field_kernel<DIM, CL, real, T::TZ, T::TX><<<g, T::TZ * T::TX, 0, s>>>(A);
+    adj_field_kernel<DIM, CL, real, T::TZ, T::TX, AdjMinBlocks<real>::FIELD><<<g, T::TZ * T::TX, 0, s>>>(A);
   }
   static void init_rows(const StepParams& P, const void* lE, const void* lB, const double* Kx, double* rows,
                         dim3 g, cudaStream_t s) {

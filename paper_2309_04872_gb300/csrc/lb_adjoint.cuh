@@ -550,8 +550,8 @@ __device__ __forceinline__ void adj_local_node(const AdjParams& A, const LSrc& s
   }
 }
 
-template <int DIM, int CL, typename real, int TZ, int TX>
-__global__ void __launch_bounds__(TZ* TX) adj_local_kernel(const AdjParams A) {
+template <int DIM, int CL, typename real, int TZ, int TX, int MINB>
+__global__ void __launch_bounds__(TZ* TX, MINB) adj_local_kernel(const AdjParams A) {
   const StepParams& P = A.P;
   const int z = blockIdx.x * TZ + threadIdx.x % TZ;
   const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
@@ -752,8 +752,8 @@ __device__ __forceinline__ void adj_field_node(const AdjParams& A, const LSrc& s
   }
 }
 
-template <int DIM, int CL, typename real, int TZ, int TX>
-__global__ void __launch_bounds__(TZ* TX) adj_field_kernel(const AdjParams A) {
+template <int DIM, int CL, typename real, int TZ, int TX, int MINB>
+__global__ void __launch_bounds__(TZ* TX, MINB) adj_field_kernel(const AdjParams A) {
   const StepParams& P = A.P;
   __shared__ double red[2][TX][TZ];
   const int tzi = threadIdx.x % TZ, txi = threadIdx.x / TZ;
