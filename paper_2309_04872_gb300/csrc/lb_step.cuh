@@ -69,7 +69,15 @@ struct StepCfg {
   static constexpr bool CF = sizeof(real) == 4;
   static constexpr int NEC = DIM;                   // present E components (z[, x[, y]])
   static constexpr int NE_SLOTS = CF ? 2 * NEC : NEC;
-  static constexpr size_t smem_bytes = ((size_t)(M::NM + NE_SLOTS) * NR + NDRV) * sizeof(real);
+  // rolled set loops keep their per-set values (moments, sources) in a
+  // per-thread shared-memory column [K][NT] instead of local memory
+  static constexpr bool ROLL = RollSets<DIM, M::K>::value;
+  static constexpr int NSCR = ROLL ? M::K * NT : 0;
+  // 2D: fields of the low-side halo E slots, staged by asynchronous copies
+  // (E_z, E_x, B_y and B_y one node up along x and z; FP32 also low parts)
+  static constexpr int NHALO_E = DIM == 2 ? (TZ + 1) * (TX + 1) - TZ * TX : 0;
+  static constexpr int NSTAGE = NHALO_E * (CF ? 10 : 5);
+  static constexpr size_t smem_bytes = ((size_t)(M::NM + NE_SLOTS) * NR + NDRV + NSCR + NSTAGE) * sizeof(real);
   __host__ __device__ static constexpr int stride(int a) { return a == 0 ? 1 : (a == 1 ? RZ : RZ * RX); }
 };
 
@@ -243,6 +251,57 @@ __device__ __forceinline__ void load_fields(const StepParams& P, int e0, int e1,
   }
 }
 
+// Asynchronous 4- or 8-byte copy global -> shared (cp.async); each thread
+// waits for its own copies with cp_async_wait_all.
+template <typename real>
+__device__ __forceinline__ void cp_async_el(real* dst, const real* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const size_t g = __cvta_generic_to_global(src);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(g), "n"(sizeof(real)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// 2D bulk node `id`: queue copies of the values load_fields reads (E_z, E_x,
+// B_y, B_y at x + 1 and at z + 1, then the low parts in FP32) to dst[v * ns].
+template <typename real>
+__device__ __forceinline__ void stage_fields_2d(const StepParams& P, int id, real* dst, int ns) {
+  constexpr bool CF = sizeof(real) == 4;
+  const int pl = (int)P.plane;
+  const int o[5] = {id, pl + id, 2 * pl + id, 2 * pl + id + P.axis_stride[1], 2 * pl + id + 1};
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    cp_async_el(dst + v * ns, (v < 2 ? reinterpret_cast<const real*>(P.Ein) : reinterpret_cast<const real*>(P.Bin)) + o[v]);
+    if (CF)
+      cp_async_el(dst + (5 + v) * ns,
+                  (v < 2 ? reinterpret_cast<const real*>(P.Ein_lo) : reinterpret_cast<const real*>(P.Bin_lo)) + o[v]);
+  }
+}
+
+// The staged values as load_fields<2> would have loaded them.
+template <typename real>
+__device__ __forceinline__ void fields_2d_from_stage(const real* src, int ns, FieldPF<real>& F) {
+  constexpr bool CF = sizeof(real) == 4;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    F.Ec[a] = F.Bc[a] = F.Bm[a] = F.Ec_lo[a] = F.Bc_lo[a] = F.Bm_lo[a] = real(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) F.Bp[a][b] = F.Bp_lo[a][b] = real(0);
+  }
+  F.Ec[0] = src[0];
+  F.Ec[1] = src[ns];
+  F.Bc[2] = src[2 * ns];
+  F.Bp[2][1] = src[3 * ns];
+  F.Bp[2][0] = src[4 * ns];
+  if (CF) {
+    F.Ec_lo[0] = src[5 * ns];
+    F.Ec_lo[1] = src[6 * ns];
+    F.Bc_lo[2] = src[7 * ns];
+    F.Bp_lo[2][1] = src[8 * ns];
+    F.Bp_lo[2][0] = src[9 * ns];
+  }
+}
+
 // Difference of two compensated values (high parts first: close values
 // subtract exactly).
 template <typename real>
@@ -342,18 +401,21 @@ __device__ __forceinline__ void e_slot(const StepParams& P, const StepConst<type
 template <int DIM, int CL, int PR, bool EDGE, class Pull>
 __device__ __forceinline__ void decode_node(const StepParams& P, const StepConst<typename Prec<PR>::real>& S,
                                             const Pull& pull, int z, int x, int y, typename Prec<PR>::real* smac,
-                                            int NR, int r) {
+                                            int NR, int r, typename Prec<PR>::real* scr, int NT) {
   using M = Model<DIM, CL>;
   using real = typename Prec<PR>::real;
   constexpr int K = M::K, Q = Lattice<DIM>::Q;
   real dA[K];
   if constexpr (RollSets<DIM, K>::value) {
+    // scr: this thread's shared-memory column (stride NT)
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
       real df[Q];
       pull.template get<EDGE>(z, x, y, k, df);
-      dA[k] = set_moment<Q>(df);
+      scr[k * NT] = set_moment<Q>(df);
     }
+#pragma unroll
+    for (int k = 0; k < K; ++k) dA[k] = scr[k * NT];
   } else {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -410,6 +472,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   real* smac = reinterpret_cast<real*>(smem);  // [NM][NR]
   real* sE = smac + M::NM * NR;                 // [DIM][NR] (+ [DIM][NR] low parts in FP32)
   real* sdrv = sE + C::NE_SLOTS * NR;           // [TZ+1 | TX+1 | TY+1] driver factors
+  real* scr = sdrv + C::NDRV + threadIdx.x;     // rolled loops: this thread's column [K] (stride NT)
 
   const int tid = threadIdx.x;
   const int tz = tid % TZ, tx = (tid / TZ) % TX, ty = tid / (TZ * TX);
@@ -438,6 +501,19 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   const bool own_inside = !EDGE || (gz < P.n[0] && (DIM < 2 || gx < P.n[1]) && (DIM < 3 || gy < P.n[2]));
   const int r_own = (tz + 1) + RZ * ((DIM >= 2 ? tx + 1 : 0) + RX * (DIM >= 3 ? ty + 1 : 0));
 
+  // 2D bulk tiles: the fields of the low-side halo E slots are copied to
+  // shared memory asynchronously now and used in phase B, so their global
+  // latency overlaps the decode
+  real* sH = sdrv + C::NDRV + C::NSCR;
+  if constexpr (DIM == 2 && !EDGE) {
+    static_assert(C::NHALO_E <= NT, "one halo slot per thread");
+    if (tid < C::NHALO_E) {
+      const int rz = tid <= TZ ? tid : 0, rx = tid <= TZ ? 0 : tid - TZ;
+      stage_fields_2d<real>(P, cell_index32(P, oz + rz, ox + rx, 0), sH + tid, C::NHALO_E);
+    }
+    cp_async_commit();
+  }
+
   // ---------------- A: pull + decode of the tile and its halo -------------
   real keep[KEEP ? K * Q : 1];
   real dA_own[K];
@@ -451,8 +527,10 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       for (int k = 0; k < K; ++k) {
         real df[Q];
         pull.template get<EDGE>(ez, ex, ey, k, df);
-        dA_own[k] = set_moment<Q>(df);
+        scr[k * NT] = set_moment<Q>(df);
       }
+#pragma unroll
+      for (int k = 0; k < K; ++k) dA_own[k] = scr[k * NT];
     } else {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -494,7 +572,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
           z = wrap_or_clamp(z, P.n[0], P.periodic);
           if (DIM >= 2) x = wrap_or_clamp(x, P.n[1], P.periodic);
         }
-        decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, 0, smac, NR, r);
+        decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, 0, smac, NR, r, scr, NT);
       }
     } else {
       // 3D: stride over the region and skip the interior
@@ -507,7 +585,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
           x = wrap_or_clamp(x, P.n[1], P.periodic);
           y = wrap_or_clamp(y, P.n[2], P.periodic);
         }
-        decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, y, smac, NR, r);
+        decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, y, smac, NR, r, scr, NT);
       }
     }
   }
@@ -561,7 +639,12 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       }
       const int id = cell_index32(P, e0, e1, e2);
       FieldPF<real> G;
-      load_fields<DIM, real, EDGE>(P, e0, e1, e2, id, G);
+      if constexpr (DIM == 2 && !EDGE) {
+        cp_async_wait_all();
+        fields_2d_from_stage<real>(sH + h, C::NHALO_E, G);
+      } else {
+        load_fields<DIM, real, EDGE>(P, e0, e1, e2, id, G);
+      }
       e_slot<DIM, CL, PR, TZ, TX, TY, EDGE>(P, S, smac, sE, sdrv, oz, ox, oy, r_eff, e0, e1, e2, G);
       if (r_eff != r) {
 #pragma unroll
@@ -783,19 +866,13 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
     Codec<PR>::store0(fk, id, fout + ((size_t)K * Q + k) * (size_t)P.plane, id, sub_rn(add_rn(dA, dtF), moved), sc);
   };
   if constexpr (RollSets<DIM, K>::value) {
-    // per-set values gathered first (the rolled loop indexes small local
-    // arrays, never the launch parameters)
-    real Fk[K], Ak[K];
-    float sck[K], isck[K];
+    // the sources first, into this thread's shared-memory column; the
+    // rolled loop reads them, and the per-set constants from the launch
+    // parameters (grid constants)
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      Fk[k] = dt * source(k);
-      Ak[k] = S.Arest[k];
-      sck[k] = P.scale[k];
-      isck[k] = P.inv_scale[k];
-    }
+    for (int k = 0; k < K; ++k) scr[k * NT] = dt * source(k);
 #pragma unroll 1
-    for (int k = 0; k < K; ++k) collide_set(k, Ak[k], sck[k], isck[k], [&] { return Fk[k]; });
+    for (int k = 0; k < K; ++k) collide_set(k, S.Arest[k], P.scale[k], P.inv_scale[k], [&] { return scr[k * NT]; });
   } else {
 #pragma unroll
     for (int k = 0; k < K; ++k) collide_set(k, S.Arest[k], P.scale[k], P.inv_scale[k], [&] { return dt * source(k); });
