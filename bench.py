@@ -441,7 +441,9 @@ def _configs(stream, flush, hbm):
             "mlups": round(info.ncell / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
             "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
             "nodes": int(info.ncell), "runs": 64, "lec_runs": nlec, "warmc_runs": 64 - nlec,
-            "tile": list(info.tile), "tuned_ms": [round(v, 4) for v in info.tuned_ms if v > 0],
+            "tile": {"lec": list(info.tile[0]), "warmc": list(info.tile[1])},
+            "tuned_ms": {"lec": [round(v, 4) for v in info.tuned_ms[0] if v > 0],
+                         "warmc": [round(v, 4) for v in info.tuned_ms[1] if v > 0]},
             "graph_steps": info.graph_steps, "steps": 96, "kernel": "lb_step_batch_kernel",
             "l2": "state larger than L2 (no flush)"}
     for prec in ("fp32", "fp64"):

@@ -271,9 +271,9 @@ int lbpwfa_adjoint_step(lbpwfa_t h, lbpwfa_adjoint_io* io);
  * Batched sweeps (uneven 2D grids, mixed closures, one launch per step).
  * The paper runs each parameter point as a separate simulation (Sec. 6:
  * temperature and driver scans, Figs. 3 and 6); a batch advances many such
- * runs together: every step is one persistent kernel over a work list of
- * (run, tile) items, and runs of lbpwfa_batch_step are replayed from a
- * captured CUDA graph.  A device-side step counter supplies each step's time
+ * runs together: every step is one persistent kernel per closure over that
+ * closure's work list of (run, tile) items, and runs of lbpwfa_batch_step
+ * are replayed from a captured CUDA graph.  A device-side step counter supplies each step's time
  * and buffer parity, so the graph is valid from any step.
  * ------------------------------------------------------------------------ */
 typedef struct lbpwfa_batch_s* lbpwfa_batch_t;
@@ -281,21 +281,23 @@ typedef struct lbpwfa_batch_s* lbpwfa_batch_t;
 typedef struct {
   int nruns;
   int64_t ncell;           /* nodes over all runs */
-  int64_t nitems;          /* (run, tile) work items per step */
-  int tile[2];             /* tile (z, x) chosen by the autotuner */
-  int grid;                /* CTAs of the persistent launch */
+  int64_t nitems;          /* (run, tile) work items per step, both closures */
+  int tile[2][2];          /* per closure [LBPWFA_LEC, LBPWFA_WARMC]: tile (z, x)
+                              chosen by the autotuner; 0 without such runs */
+  int grid[2];             /* per closure: CTAs of its persistent launch */
   int graph_steps;         /* steps per captured graph */
   int64_t step;
   size_t device_bytes;
   double bytes_per_step;   /* algorithmic HBM bytes of one batch step */
-  double tuned_ms[4];      /* autotuner timing per candidate tile (-1 unused) */
+  double tuned_ms[2][4];   /* per closure: autotuner step time per candidate
+                              tile (-1 unused) */
 } lbpwfa_batch_info_t;
 
 /* Create nruns >= 1 runs from p[0..nruns-1], each validated as by
  * lbpwfa_create.  Every run must be 2D with the same precision; closures,
  * grids and driver parameters may differ.  flags bit 0: skip the autotuner
- * (use the first candidate tile).  The autotuner times each candidate tile
- * over a few steps and restores the rest state; when the environment
+ * (use the first candidate tile).  The autotuner times each candidate tile,
+ * closure by closure, over a few steps and restores the rest state; when the environment
  * variable LBPWFA_TUNE_CACHE names a JSON file, choices are read from and
  * written to it.  p[i].stream of run 0 is the batch's stream.
  * Errors: INVALID, OOM, CUDA. */

@@ -1,10 +1,11 @@
-// Batched 2D step: one persistent launch advances many runs (uneven grids,
-// both closures) by one time step.  The work list holds (run, tile) items;
-// CTA b takes items b, b + gridDim.x, ...  Each item copies its run's launch
-// parameters into shared memory, sets the step's time and buffer parity from
-// a device-side step counter (so a captured CUDA graph can be replayed from
-// any step) and runs the same three-phase step as a single run, with the
-// LEC or WARMC body chosen per item (block-uniform branch).
+// Batched 2D step: one persistent launch per closure advances many runs
+// (uneven grids) by one time step.  The closure's work list holds (run, tile)
+// items; CTA b takes items b, b + gridDim.x, ...  Each item copies its run's
+// launch parameters into shared memory, sets the step's time and buffer
+// parity from a device-side step counter (so a captured CUDA graph can be
+// replayed from any step) and runs the same three-phase step as a single
+// run.  One kernel per closure keeps each at its own register budget and
+// occupancy (LEC needs far fewer registers than WARMC).
 #pragma once
 
 #include "lb_batch_types.cuh"
@@ -32,39 +33,50 @@ __device__ __forceinline__ void batch_item(const StepParams& P, unsigned char* s
   }
 }
 
-template <int PR, int TZ, int TX>
+template <int PR, int TZ, int TX, int CL>
 struct BatchCfg {
-  static constexpr size_t smem_lec = StepCfg<2, CL_LEC, PR, TZ, TX, 1>::smem_bytes;
-  static constexpr size_t smem_warmc = StepCfg<2, CL_WARMC, PR, TZ, TX, 1>::smem_bytes;
-  static constexpr size_t smem_bytes = smem_lec > smem_warmc ? smem_lec : smem_warmc;
+  static constexpr size_t smem_bytes = StepCfg<2, CL, PR, TZ, TX, 1>::smem_bytes;
+  // resident CTAs the register budget is held to in FP32: three for LEC (as
+  // the single-run LEC kernel runs), two for WARMC
+  static constexpr int MINB = PR == PR_F32 ? (CL == CL_LEC ? 3 : 2) : 1;
 };
 
-template <int PR, int TZ, int TX>
-__global__ void __launch_bounds__(TZ* TX) lb_step_batch_kernel(const BatchArgs A) {
+template <int PR, int TZ, int TX, int CL>
+__global__ void __launch_bounds__(TZ* TX, (BatchCfg<PR, TZ, TX, CL>::MINB)) lb_step_batch_kernel(const BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) StepParams Ps;
+  __shared__ int s_ntz;
   const long long step = *A.step;
   const int parity = (int)(step & 1);
-  for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
-    const int2 w = A.items[it];
-    const BatchRun* R = A.runs + w.x;
-    {
+  // the CTA's items are mostly consecutive tiles of one run: the run's launch
+  // parameters are copied only when the run changes, and the next item's
+  // index is loaded one item ahead
+  int run = -1;
+  int it = blockIdx.x;
+  int2 w = it < A.nitems ? A.items[it] : make_int2(0, 0);
+  for (; it < A.nitems; it += gridDim.x) {
+    const int itn = it + gridDim.x;
+    const int2 wn = itn < A.nitems ? A.items[itn] : w;
+    if (w.x != run) {
+      const BatchRun* R = A.runs + w.x;
       const int* src = reinterpret_cast<const int*>(&R->P[parity]);
       int* dst = reinterpret_cast<int*>(&Ps);
       for (int q = threadIdx.x; q < (int)(sizeof(StepParams) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double z = batch_zeta0(R->z0, step, R->dt);
+        Ps.cd.zeta0 = z;
+        Ps.cf.zeta0 = (float)z;
+        Ps.have_prev = step > R->prev_from ? 1 : 0;
+        s_ntz = R->ntz;
+      }
+      __syncthreads();
+      run = w.x;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const double z = batch_zeta0(R->z0, step, R->dt);
-      Ps.cd.zeta0 = z;
-      Ps.cf.zeta0 = (float)z;
-      Ps.have_prev = step > R->prev_from ? 1 : 0;
-    }
-    __syncthreads();
-    const int tz = w.y % R->ntz, tx = w.y / R->ntz;
-    if (R->closure == CL_LEC) batch_item<CL_LEC, PR, TZ, TX>(Ps, smem_raw, tz, tx);
-    else batch_item<CL_WARMC, PR, TZ, TX>(Ps, smem_raw, tz, tx);
+    const int tz = w.y % s_ntz, tx = w.y / s_ntz;
+    batch_item<CL, PR, TZ, TX>(Ps, smem_raw, tz, tx);
     __syncthreads();  // Ps and the records are reused by the next item
+    w = wn;
   }
 }
 

@@ -47,7 +47,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
 template <int CL, int PR> struct TmaTile2D;
 // Tile and resident CTAs per SM (the shared-memory box sets the occupancy;
 // the register budget is held to match it).
-template <> struct TmaTile2D<CL_LEC, PR_F32> { static constexpr int TZ = 64, TX = 8, MINB = 2; };
+template <> struct TmaTile2D<CL_LEC, PR_F32> { static constexpr int TZ = 32, TX = 8, MINB = 3; };
 template <> struct TmaTile2D<CL_LEC, PR_F16S> { static constexpr int TZ = 64, TX = 8, MINB = 2; };
 template <> struct TmaTile2D<CL_LEC, PR_F64> { static constexpr int TZ = 32, TX = 8, MINB = 2; };
 template <> struct TmaTile2D<CL_WARMC, PR_F32> { static constexpr int TZ = 32, TX = 4, MINB = 2; };

@@ -856,24 +856,31 @@ extern "C" int lbpwfa_reduce_noalloc(lbpwfa_t h, double* out, int out_is_device)
 // ---------------------------------------------------------------------------
 // Batched sweeps.
 // ---------------------------------------------------------------------------
+// Per closure (index LBPWFA_LEC, LBPWFA_WARMC): its candidate tile, grid and
+// (run, tile) work list; a step launches one persistent kernel per closure
+// that has runs.
 struct lbpwfa_batch_s {
   std::vector<lbpwfa_s*> runs;
   BatchKernelSet bk{};
-  int cand = 0;
-  int grid = 0;
+  int cand[2] = {0, 0};
+  int grid[2] = {0, 0};
   int precision = 0;
   std::vector<BatchRun> runs_h;
   BatchRun* runs_d = nullptr;
-  int2* items_d = nullptr;
+  int2* items_d[2] = {nullptr, nullptr};
   long long* step_d = nullptr;
-  long long nitems = 0;
+  long long nitems[2] = {0, 0};
   long long step = 0;
   cudaStream_t stream = nullptr;
   bool owns_stream = false;
+  // with runs of both closures the WARMC launch forks onto side_stream, so
+  // the two persistent kernels fill each other's tails
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_steps = 32;
-  double tuned_ms[4] = {-1, -1, -1, -1};
+  double tuned_ms[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
   size_t device_bytes = 0;
   std::string err;
 };
@@ -896,20 +903,24 @@ void batch_free_lists(lbpwfa_batch_s* b) {
   b->graph_exec = nullptr;
   b->graph = nullptr;
   if (b->runs_d) cudaFree(b->runs_d);
-  if (b->items_d) cudaFree(b->items_d);
   b->runs_d = nullptr;
-  b->items_d = nullptr;
+  for (int cl = 0; cl < 2; ++cl) {
+    if (b->items_d[cl]) cudaFree(b->items_d[cl]);
+    b->items_d[cl] = nullptr;
+  }
 }
 
-// Launch records and the (run, tile) work list for candidate tile c.
-int batch_build(lbpwfa_batch_s* b, int c) {
+// Launch records and the per-closure (run, tile) work lists for candidate
+// tiles c[LBPWFA_LEC] and c[LBPWFA_WARMC].
+int batch_build(lbpwfa_batch_s* b, const int* c) {
   batch_free_lists(b);
-  const int tz = b->bk.tz[c], tx = b->bk.tx[c];
   b->runs_h.assign(b->runs.size(), BatchRun{});
-  std::vector<int2> items;
+  std::vector<int2> items[2];
   for (size_t i = 0; i < b->runs.size(); ++i) {
     lbpwfa_s* h = b->runs[i];
     BatchRun& R = b->runs_h[i];
+    const int cl = h->prm.closure;
+    const int tz = b->bk.tz[c[cl]], tx = b->bk.tx[c[cl]];
     const int cur = h->cur;
     for (int par = 0; par < 2; ++par) {
       h->cur = par;
@@ -919,38 +930,54 @@ int batch_build(lbpwfa_batch_s* b, int c) {
     R.z0 = h->prm.z0;
     R.dt = h->dt;
     R.prev_from = h->have_prev ? -1 : b->step;
-    R.closure = h->prm.closure;
+    R.closure = cl;
     R.ntz = (h->n[0] + tz - 1) / tz;
     R.ntx = (h->n[1] + tx - 1) / tx;
-    for (int t = 0; t < R.ntz * R.ntx; ++t) items.push_back(make_int2((int)i, t));
+    for (int t = 0; t < R.ntz * R.ntx; ++t) items[cl].push_back(make_int2((int)i, t));
   }
-  b->nitems = (long long)items.size();
   BCK(b, cudaMalloc(&b->runs_d, sizeof(BatchRun) * b->runs_h.size()));
-  BCK(b, cudaMalloc(&b->items_d, sizeof(int2) * items.size()));
   BCK(b, cudaMemcpyAsync(b->runs_d, b->runs_h.data(), sizeof(BatchRun) * b->runs_h.size(),
                          cudaMemcpyHostToDevice, b->stream));
-  BCK(b, cudaMemcpyAsync(b->items_d, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
-                         b->stream));
-  BCK(b, cudaStreamSynchronize(b->stream));
-  BCK(b, b->bk.prepare[c]());
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int occ = b->bk.occupancy[c]();
-  long long g = (long long)sms * (occ > 0 ? occ : 1);
-  b->grid = (int)(g < b->nitems ? g : b->nitems);
-  b->cand = c;
+  for (int cl = 0; cl < 2; ++cl) {
+    b->nitems[cl] = (long long)items[cl].size();
+    b->cand[cl] = c[cl];
+    b->grid[cl] = 0;
+    if (items[cl].empty()) continue;
+    BCK(b, cudaMalloc(&b->items_d[cl], sizeof(int2) * items[cl].size()));
+    BCK(b, cudaMemcpyAsync(b->items_d[cl], items[cl].data(), sizeof(int2) * items[cl].size(), cudaMemcpyHostToDevice,
+                           b->stream));
+    BCK(b, b->bk.prepare[cl][c[cl]]());
+    const int occ = b->bk.occupancy[cl][c[cl]]();
+    const long long g = (long long)sms * (occ > 0 ? occ : 1);
+    b->grid[cl] = (int)(g < b->nitems[cl] ? g : b->nitems[cl]);
+  }
+  BCK(b, cudaStreamSynchronize(b->stream));
   return LBPWFA_OK;
 }
 
 int batch_launch_one(lbpwfa_batch_s* b) {
-  BatchArgs A{};
-  A.runs = b->runs_d;
-  A.items = b->items_d;
-  A.nitems = (int)b->nitems;
-  A.step = b->step_d;
-  b->bk.launch[b->cand](A, b->grid, b->stream);
-  BCK(b, cudaGetLastError());
+  const bool fork = b->nitems[0] > 0 && b->nitems[1] > 0 && b->side_stream;
+  if (fork) {
+    BCK(b, cudaEventRecord(b->fork_ev, b->stream));
+    BCK(b, cudaStreamWaitEvent(b->side_stream, b->fork_ev, 0));
+  }
+  for (int cl = 0; cl < 2; ++cl) {
+    if (b->nitems[cl] == 0) continue;
+    BatchArgs A{};
+    A.runs = b->runs_d;
+    A.items = b->items_d[cl];
+    A.nitems = (int)b->nitems[cl];
+    A.step = b->step_d;
+    b->bk.launch[cl][b->cand[cl]](A, b->grid[cl], fork && cl == 1 ? b->side_stream : b->stream);
+    BCK(b, cudaGetLastError());
+  }
+  if (fork) {
+    BCK(b, cudaEventRecord(b->join_ev, b->side_stream));
+    BCK(b, cudaStreamWaitEvent(b->stream, b->join_ev, 0));
+  }
   batch_advance(b->step_d, b->stream);
   BCK(b, cudaGetLastError());
   return LBPWFA_OK;
@@ -1022,36 +1049,47 @@ void cache_store(const std::string& key, int c) {
   }
 }
 
-// Time each candidate tile over a few steps of the real batch, keep the
-// fastest, and return to the rest state.
+// Time each candidate tile over a few steps of the real batch, one closure
+// at a time (the other closure's kernel is the same in every timing), keep
+// the fastest, and return to the rest state.  The cache stores the pair as
+// 4 * c[LEC] + c[WARMC].
 int batch_autotune(lbpwfa_batch_s* b) {
   const std::string key = batch_key(b);
   const int cached = cache_lookup(key);
-  if (cached >= 0 && cached < b->bk.ncand) return batch_build(b, cached);
+  if (cached >= 0 && cached / 4 < b->bk.ncand && cached % 4 < b->bk.ncand) {
+    const int c[2] = {cached / 4, cached % 4};
+    return batch_build(b, c);
+  }
+  bool present[2] = {false, false};
+  for (const lbpwfa_s* h : b->runs) present[h->prm.closure] = true;
   cudaEvent_t e0, e1;
   BCK(b, cudaEventCreate(&e0));
   BCK(b, cudaEventCreate(&e1));
-  int best = 0;
-  double best_ms = 1e30;
-  for (int c = 0; c < b->bk.ncand; ++c) {
-    int r = batch_build(b, c);
-    if (r != LBPWFA_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
-    for (int w = 0; w < 2 && r == LBPWFA_OK; ++w) r = batch_launch_one(b);
-    cudaEventRecord(e0, b->stream);
-    for (int w = 0; w < 4 && r == LBPWFA_OK; ++w) r = batch_launch_one(b);
-    cudaEventRecord(e1, b->stream);
-    if (r != LBPWFA_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
-    BCK(b, cudaEventSynchronize(e1));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    b->tuned_ms[c] = ms / 4.0;
-    if (b->tuned_ms[c] < best_ms) { best_ms = b->tuned_ms[c]; best = c; }
-    r = batch_reset(b);
-    if (r != LBPWFA_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+  int best[2] = {0, 0};
+  for (int cl = 0; cl < 2; ++cl) {
+    if (!present[cl]) continue;
+    double best_ms = 1e30;
+    for (int cc = 0; cc < b->bk.ncand; ++cc) {
+      int c[2] = {best[0], best[1]};
+      c[cl] = cc;
+      int r = batch_build(b, c);
+      for (int w = 0; w < 2 && r == LBPWFA_OK; ++w) r = batch_launch_one(b);
+      if (r == LBPWFA_OK) cudaEventRecord(e0, b->stream);
+      for (int w = 0; w < 4 && r == LBPWFA_OK; ++w) r = batch_launch_one(b);
+      if (r == LBPWFA_OK) cudaEventRecord(e1, b->stream);
+      if (r != LBPWFA_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+      BCK(b, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      b->tuned_ms[cl][cc] = ms / 4.0;
+      if (b->tuned_ms[cl][cc] < best_ms) { best_ms = b->tuned_ms[cl][cc]; best[cl] = cc; }
+      r = batch_reset(b);
+      if (r != LBPWFA_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cache_store(key, best);
+  cache_store(key, 4 * best[0] + best[1]);
   return batch_build(b, best);
 }
 
@@ -1062,7 +1100,11 @@ extern "C" {
 void lbpwfa_batch_destroy(lbpwfa_batch_t b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->side_stream) cudaStreamSynchronize(b->side_stream);
   batch_free_lists(b);
+  if (b->side_stream) cudaStreamDestroy(b->side_stream);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
   if (b->step_d) cudaFree(b->step_d);
   for (lbpwfa_s* h : b->runs) destroy_run(h);
   if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -1101,11 +1143,18 @@ int lbpwfa_batch_create(const lbpwfa_params* p, int nruns, int flags, lbpwfa_bat
     b->device_bytes += h->device_bytes;
   }
   if (cudaMalloc(&b->step_d, sizeof(long long)) != cudaSuccess) { lbpwfa_batch_destroy(b); return LBPWFA_ERR_OOM; }
+  if (cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    lbpwfa_batch_destroy(b);
+    return LBPWFA_ERR_CUDA;
+  }
   if (cudaMemsetAsync(b->step_d, 0, sizeof(long long), b->stream) != cudaSuccess) {
     lbpwfa_batch_destroy(b);
     return LBPWFA_ERR_CUDA;
   }
-  int st = (flags & 1) ? batch_build(b, 0) : batch_autotune(b);
+  const int first[2] = {0, 0};
+  int st = (flags & 1) ? batch_build(b, first) : batch_autotune(b);
   if (st != LBPWFA_OK) { lbpwfa_batch_destroy(b); return st; }
   *out = b;
   return LBPWFA_OK;
@@ -1172,14 +1221,16 @@ int lbpwfa_batch_info(lbpwfa_batch_t b, lbpwfa_batch_info_t* info) {
     info->ncell += ri.ncell;
     info->bytes_per_step += ri.bytes_per_update * (double)ri.ncell;
   }
-  info->nitems = b->nitems;
-  info->tile[0] = b->bk.tz[b->cand];
-  info->tile[1] = b->bk.tx[b->cand];
-  info->grid = b->grid;
+  info->nitems = b->nitems[0] + b->nitems[1];
+  for (int cl = 0; cl < 2; ++cl) {
+    info->tile[cl][0] = b->nitems[cl] ? b->bk.tz[b->cand[cl]] : 0;
+    info->tile[cl][1] = b->nitems[cl] ? b->bk.tx[b->cand[cl]] : 0;
+    info->grid[cl] = b->grid[cl];
+    for (int c = 0; c < 4; ++c) info->tuned_ms[cl][c] = b->tuned_ms[cl][c];
+  }
   info->graph_steps = b->graph_steps;
   info->step = b->step;
   info->device_bytes = b->device_bytes;
-  for (int c = 0; c < 4; ++c) info->tuned_ms[c] = b->tuned_ms[c];
   return LBPWFA_OK;
 }
 

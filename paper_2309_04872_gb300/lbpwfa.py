@@ -57,9 +57,9 @@ class Info(ctypes.Structure):
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("nruns", ctypes.c_int), ("ncell", ctypes.c_int64), ("nitems", ctypes.c_int64),
-                ("tile", ctypes.c_int * 2), ("grid", ctypes.c_int), ("graph_steps", ctypes.c_int),
+                ("tile", (ctypes.c_int * 2) * 2), ("grid", ctypes.c_int * 2), ("graph_steps", ctypes.c_int),
                 ("step", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("bytes_per_step", ctypes.c_double),
-                ("tuned_ms", ctypes.c_double * 4)]
+                ("tuned_ms", (ctypes.c_double * 4) * 2)]
 
 
 class RecordParams(ctypes.Structure):

@@ -117,17 +117,21 @@ def test_batch_autotune_cache(tmp_path, monkeypatch):
     path = tmp_path / "tune.json"
     monkeypatch.setenv("LBPWFA_TUNE_CACHE", str(path))
     runs = _runs()
+    closures = {r["closure"] for r in runs}
+    assert closures == {"lec", "warmc"}
     with lb.Batch(runs, "fp32", tune=True) as b:
         first = b.info()
-        assert all(first.tuned_ms[c] > 0 for c in range(3))
+        # both closures tuned over the three candidate tiles
+        assert all(first.tuned_ms[cl][c] > 0 for cl in range(2) for c in range(3))
+        assert all(first.grid[cl] > 0 for cl in range(2))
     entries = json.loads(path.read_text())
     assert len(entries) == 1
     (choice,) = entries.values()
     with lb.Batch(runs, "fp32", tune=True) as b:
         again = b.info()
-        assert all(again.tuned_ms[c] < 0 for c in range(4))  # read from the cache
-        assert list(again.tile) == list(first.tile)
-    assert choice in (0, 1, 2)
+        assert all(again.tuned_ms[cl][c] < 0 for cl in range(2) for c in range(4))  # read from the cache
+        assert [list(t) for t in again.tile] == [list(t) for t in first.tile]
+    assert choice // 4 in (0, 1, 2) and choice % 4 in (0, 1, 2)
 
 
 def test_batch_rejects_mixed_inputs():
