@@ -29,10 +29,10 @@ struct Impl {
 
   static cudaError_t prepare() {
     return cudaFuncSetAttribute(lb_step_kernel<DIM, CL, PR, T::TZ, T::TX, T::TY>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes);
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes_gkeep);
   }
   static void step(const StepParams& P, dim3 grid, cudaStream_t s) {
-    lb_step_kernel<DIM, CL, PR, T::TZ, T::TX, T::TY><<<grid, Cfg::NT, Cfg::smem_bytes, s>>>(P);
+    lb_step_kernel<DIM, CL, PR, T::TZ, T::TX, T::TY><<<grid, Cfg::NT, Cfg::smem_bytes_gkeep, s>>>(P);
   }
   static void init_fields(const AuxParams& A, void* E, void* B, void* Elo, void* Blo, cudaStream_t s) {
     init_fields_kernel<DIM, real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, (real*)E, (real*)B, (real*)Elo, (real*)Blo);
@@ -113,7 +113,7 @@ struct Impl {
     ks->prepare_tma = &prepare_tma;
     ks->step_tma = &step_tma;
     ks->tz = T::TZ; ks->tx = T::TX; ks->ty = T::TY;
-    ks->step_smem = Cfg::smem_bytes;
+    ks->step_smem = Cfg::smem_bytes_gkeep;
     ks->prepare = &prepare;
     ks->step = &step;
     ks->init_fields = &init_fields;

@@ -15,6 +15,8 @@
 // bulk node).  Populations are kept as deviations from w_i A_rest,k.
 #pragma once
 
+#include <type_traits>
+
 #include "lb_common.cuh"
 
 namespace lbp {
@@ -78,6 +80,15 @@ struct StepCfg {
   static constexpr int NHALO_E = DIM == 2 ? (TZ + 1) * (TX + 1) - TZ * TX : 0;
   static constexpr int NSTAGE = NHALO_E * (CF ? 10 : 5);
   static constexpr size_t smem_bytes = ((size_t)(M::NM + NE_SLOTS) * NR + NDRV + NSCR + NSTAGE) * sizeof(real);
+  // 2D sets too wide for registers (WARMC, K*Q = 72) in FP32 storage: the
+  // single-run kernel, which pulls from global memory, keeps the own node's
+  // populations in a shared-memory column [K*Q][NT] for the collision
+  // instead of pulling them again (2D WARMC 4.2 -> 5.6 GLUPS; in FP16S, and
+  // in the batch kernel, measured slower); its launch reserves
+  // smem_bytes_gkeep
+  static constexpr bool SKEEP_OK = DIM == 2 && M::K * M::Q > 32 && PR == PR_F32;
+  static constexpr int NKEEP = SKEEP_OK ? M::K * M::Q * NT : 0;
+  static constexpr size_t smem_bytes_gkeep = smem_bytes + (size_t)NKEEP * sizeof(real);
   __host__ __device__ static constexpr int stride(int a) { return a == 0 ? 1 : (a == 1 ? RZ : RZ * RX); }
 };
 
@@ -117,8 +128,11 @@ __device__ __forceinline__ void pulled_dev(const StepParams& P, int z, int x, in
 
 // Population source reading the stored post-collision array in global memory
 // (any boundary rule).
-template <int DIM, int CL, int PR>
+template <int DIM, int CL, int PR, bool SHARED_KEEP = false>
 struct GlobalPull {
+  // the step keeps the own node's populations in shared memory for the
+  // collision (sets too wide for registers) instead of pulling them again
+  static constexpr bool kSharedKeep = SHARED_KEEP;
   const StepParams& P;
   template <bool EDGE>
   __device__ __forceinline__ void get(int z, int x, int y, int k, typename Prec<PR>::real* df) const {
@@ -467,6 +481,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   constexpr int NT = C::NT, RZ = C::RZ, RX = C::RX, RY = C::RY, NR = C::NR;
   constexpr int K = M::K, Q = L::Q;
   constexpr bool KEEP = K * Q <= 32;  // own node's pulled populations stay in registers
+  // ... or, for global pulls of wider sets, in shared memory
+  constexpr bool SKEEP = C::SKEEP_OK && std::is_same<Pull, GlobalPull<DIM, CL, PR, true>>::value;
 
   const StepConst<real>& S = consts<real>(P);
   real* smac = reinterpret_cast<real*>(smem);  // [NM][NR]
@@ -505,6 +521,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   // shared memory asynchronously now and used in phase B, so their global
   // latency overlaps the decode
   real* sH = sdrv + C::NDRV + C::NSCR;
+  real* skeep = sH + C::NSTAGE + tid;  // SKEEP: this thread's column [K*Q] (stride NT)
   if constexpr (DIM == 2 && !EDGE) {
     static_assert(C::NHALO_E <= NT, "one halo slot per thread");
     if (tid < C::NHALO_E) {
@@ -539,6 +556,9 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
         if constexpr (KEEP) {
 #pragma unroll
           for (int i = 0; i < Q; ++i) keep[k * Q + i] = df[i];
+        } else if constexpr (SKEEP) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) skeep[(k * Q + i) * NT] = df[i];
         }
         dA_own[k] = set_moment<Q>(df);
       }
@@ -842,6 +862,10 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
 #pragma unroll
       for (int i = 0; i < Q; ++i) df[i] = keep[k * Q + i];
       dA = dA_own[k];
+    } else if constexpr (SKEEP) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) df[i] = skeep[(k * Q + i) * NT];
+      dA = dA_own[k];
     } else {
       pull.template get<EDGE>(gz, gx, gy, k, df);
       dA = set_moment<Q>(df);
@@ -913,7 +937,7 @@ __global__ void __launch_bounds__(TZ* TX* TY)
 lb_step_kernel(const __grid_constant__ StepParams P) {
   using real = typename Prec<PR>::real;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  GlobalPull<DIM, CL, PR> pull{P};
+  GlobalPull<DIM, CL, PR, StepCfg<DIM, CL, PR, TZ, TX, TY>::SKEEP_OK> pull{P};
   FieldPF<real> F;
   const int bz = blockIdx.x, bx = blockIdx.y, by = blockIdx.z;
   if (tile_is_bulk<DIM, TZ, TX, TY>(P, bz, bx, by)) {
