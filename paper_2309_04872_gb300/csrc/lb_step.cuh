@@ -903,6 +903,25 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   }
 }
 
+// 3D launch order of the tiles: z-tiles fastest, then the (x, y) tiles in
+// strips W rows high in y (x, then y within a strip), so the CTAs resident at
+// one time cover a compact patch and read their x and y neighbours' halos
+// while those are still in L2 (row by row, the y-neighbours of a row of
+// tiles came several waves later).
+template <int W>
+__device__ __forceinline__ void tile_order_3d(int& bz, int& bx, int& by) {
+  const int ntz = gridDim.x, ntx = gridDim.y, nty = gridDim.z;
+  const int lin = blockIdx.x + ntz * (blockIdx.y + ntx * blockIdx.z);
+  bz = lin % ntz;
+  const int rest = lin / ntz;
+  const int strip = rest / (ntx * W);
+  const int y0 = strip * W;
+  const int h = min(W, nty - y0);
+  const int q = rest - strip * ntx * W;
+  bx = q / h;
+  by = y0 + q % h;
+}
+
 // Whether the tile and its one-node halo lie in the bulk on every axis.
 template <int DIM, int TZ, int TX, int TY>
 __device__ __forceinline__ bool tile_is_bulk(const StepParams& P, int tile_z, int tile_x, int tile_y) {
@@ -939,7 +958,8 @@ lb_step_kernel(const __grid_constant__ StepParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GlobalPull<DIM, CL, PR, StepCfg<DIM, CL, PR, TZ, TX, TY>::SKEEP_OK> pull{P};
   FieldPF<real> F;
-  const int bz = blockIdx.x, bx = blockIdx.y, by = blockIdx.z;
+  int bz = blockIdx.x, bx = blockIdx.y, by = blockIdx.z;
+  if constexpr (DIM == 3) tile_order_3d<3>(bz, bx, by);
   if (tile_is_bulk<DIM, TZ, TX, TY>(P, bz, bx, by)) {
     if constexpr (EarlyFields<DIM>::value) prefetch_own<DIM, real, false, TZ, TX, TY>(P, F, bz, bx, by);
     step_body<DIM, CL, PR, TZ, TX, TY, false>(P, smem_raw, pull, F, bz, bx, by);
