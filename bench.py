@@ -63,12 +63,15 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
     ap.add_argument("--workload", default="2d_lec",
-                    choices=["2d_lec", "2d_warmc", "3d_warmc", "3d_warmc_128", "adjoint_2d_warmc"],
+                    choices=["2d_lec", "2d_warmc", "3d_warmc", "3d_warmc_128", "adjoint_2d_warmc", "batch_2d"],
                     help="2d_lec: 1024 x 512 LEC (default); 2d_warmc: the same grid with the warm-plasma "
                          "closure; 3d_warmc: 512 x 256 x 256 WARMC; "
                          "3d_warmc_128: 128^3 WARMC (small case for profiling); adjoint_2d_warmc: "
                          "forward + reverse sweep of the 512 x 256 WARMC adjoint case over --steps steps "
-                         "(whole tape kept), for profiling")
+                         "(whole tape kept), for profiling; batch_2d: the first --batch-runs runs of the batched "
+                         "sweep over --steps steps, for profiling")
+    ap.add_argument("--batch-runs", type=int, default=64, help="batch_2d: runs of the sweep (1..64)")
+    ap.add_argument("--no-tune", action="store_true", help="batch_2d: skip the tile autotuner")
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="0: automatic (2D LEC: persistent TMA CTAs in FP32 and FP16S, a TMA box per CTA "
                          "in FP64), 1: plain global-memory pull kernel, 2: TMA box per CTA, "
@@ -225,6 +228,43 @@ def _oracle_sample(cfg, budget_s=15.0):
     for v in cfg["n"]:
         ncell *= v
     return ncell * nsteps / dt / 1e6, nsteps, dt
+
+
+def _batch_cfgs(nruns):
+    """The first nruns of the batched sweep's 64 seeded draws, as run
+    configurations."""
+    from tests import inputs
+    draws = inputs.batch_draws(64, seed=2309)[:nruns]
+    cfgs = [dict(dim=2, n=(d["nz"], d["nx"]), dx=0.05, courant=0.1, tau=0.53, closure=d["closure"], dv=3,
+                 mu=d["mu"], alpha=d["alpha"], sigma_z=d["sigma_z"], sigma_r=0.5, z0=4.0 * d["sigma_z"],
+                 boundary="open", init_fields=True) for d in draws]
+    return draws, cfgs
+
+
+def run_batch_case(a):
+    """--warmup then --steps batched steps of the sweep's first --batch-runs
+    runs (FP32); prints the timing as one JSON line."""
+    import torch
+
+    from paper_2309_04872_gb300 import lbpwfa as lb
+    lb.load_library()
+    draws, cfgs = _batch_cfgs(max(1, min(64, a.batch_runs)))
+    stream = torch.cuda.Stream()
+    with lb.Batch(cfgs, "fp32", stream=stream.cuda_stream, tune=not a.no_tune) as b:
+        info = b.info()
+        b.step(a.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(a.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(1, a.steps)
+    print(json.dumps({"metric": "batched step timing", "workload": f"batch_2d_{len(cfgs)}runs_fp32",
+                      "runs": len(cfgs), "lec_runs": sum(1 for d in draws if d["closure"] == "lec"),
+                      "nodes": int(info.ncell), "steps": a.steps, "ms_per_step": round(ms, 4),
+                      "mlups": round(info.ncell / (ms * 1e-3) / 1e6, 2),
+                      "tile": {"lec": list(info.tile[0]), "warmc": list(info.tile[1])}}), flush=True)
 
 
 def run_adjoint_case(a):
@@ -419,12 +459,8 @@ def _configs(stream, flush, hbm):
         res["1d_lec_fp64_2048"] = {"steps": 4000, "ms_total": round(ms, 3), "steps_per_s": round(4000 / ms * 1e3, 1),
                                    "mlups": round(2048 * 4000 / ms / 1e3, 2),
                                    "note": "state is L2-resident and launch-bound; no flush"}
-    # the batched sweep: 64 uneven 2D runs, both closures, one launch per step
-    from tests import inputs
-    draws = inputs.batch_draws(64, seed=2309)
-    cfgs = [dict(dim=2, n=(d["nz"], d["nx"]), dx=0.05, courant=0.1, tau=0.53, closure=d["closure"], dv=3,
-                 mu=d["mu"], alpha=d["alpha"], sigma_z=d["sigma_z"], sigma_r=0.5, z0=4.0 * d["sigma_z"],
-                 boundary="open", init_fields=True) for d in draws]
+    # the batched sweep: 64 uneven 2D runs, both closures, one launch per closure and step
+    draws, cfgs = _batch_cfgs(64)
     with lb.Batch(cfgs, "fp32", stream=stream.cuda_stream, tune=True) as b:
         info = b.info()
         b.step(32)
@@ -641,5 +677,7 @@ if __name__ == "__main__":
         run_reference(args)
     elif args.workload == "adjoint_2d_warmc":
         run_adjoint_case(args)
+    elif args.workload == "batch_2d":
+        run_batch_case(args)
     else:
         run_ours(args)
