@@ -172,6 +172,17 @@ template <> __device__ __forceinline__ const StepConst<float>& consts<float>(con
 template <> __device__ __forceinline__ const StepConst<double>& consts<double>(const StepParams& P) { return P.cd; }
 
 // Storage codec: populations are kept as deviations from w_i A_rest,k.
+// Global-memory access with the state space explicit: a store through a
+// plain pointer could alias shared memory, so a kernel whose launch
+// parameters live in shared memory (the batched step) would have to reload
+// them after every store.
+// gld is for data no thread writes during the kernel (the read-only path
+// lets the compiler move it past stores); gldc for data the kernel also
+// writes (the previous-step values, read and then overwritten in place).
+template <typename T> __device__ __forceinline__ void gst(T* p, T v) { __stwb(p, v); }
+template <typename T> __device__ __forceinline__ T gld(const T* p) { return __ldg(p); }
+template <typename T> __device__ __forceinline__ T gldc(const T* p) { return __ldcg(p); }
+
 template <int PR> struct Codec;
 // store_q stores v and returns the value a later load reads back.
 // load0 / store0 access the rest population (velocity 0) of a set: the
@@ -180,28 +191,28 @@ template <int PR> struct Codec;
 template <> struct Codec<PR_F64> {
   static constexpr int kLoPlanes = 0;  // extra planes per population set
   __device__ static double load(const double* p, long long i, float) { return __ldg(p + i); }
-  __device__ static void store(double* p, long long i, double v, float) { p[i] = v; }
+  __device__ static void store(double* p, long long i, double v, float) { gst(p + i, v); }
   __device__ static double store_q(double* p, long long i, double v, float, float) {
-    p[i] = v;
+    gst(p + i, v);
     return v;
   }
   __device__ static double load0(const double* p, long long i, const double*, long long, float) {
     return __ldg(p + i);
   }
-  __device__ static void store0(double* p, long long i, double*, long long, double v, float) { p[i] = v; }
+  __device__ static void store0(double* p, long long i, double*, long long, double v, float) { gst(p + i, v); }
 };
 template <> struct Codec<PR_F32> {
   static constexpr int kLoPlanes = 0;
   __device__ static float load(const float* p, long long i, float) { return __ldg(p + i); }
-  __device__ static void store(float* p, long long i, float v, float) { p[i] = v; }
+  __device__ static void store(float* p, long long i, float v, float) { gst(p + i, v); }
   __device__ static float store_q(float* p, long long i, float v, float, float) {
-    p[i] = v;
+    gst(p + i, v);
     return v;
   }
   __device__ static float load0(const float* p, long long i, const float*, long long, float) {
     return __ldg(p + i);
   }
-  __device__ static void store0(float* p, long long i, float*, long long, float v, float) { p[i] = v; }
+  __device__ static void store0(float* p, long long i, float*, long long, float v, float) { gst(p + i, v); }
 };
 // Binary16 of the scaled deviation.  The rest population takes the remainder
 // of its set's moment in the collision, so its rounding is the one error of
@@ -214,11 +225,11 @@ template <> struct Codec<PR_F16S> {
     return __half2float(__ldg(p + i)) * inv_s;
   }
   __device__ static void store(__half* p, long long i, float v, float s) {
-    p[i] = __float2half_rn(v * s);
+    gst(p + i, __float2half_rn(v * s));
   }
   __device__ static float store_q(__half* p, long long i, float v, float s, float inv_s) {
     const __half h = __float2half_rn(v * s);
-    p[i] = h;
+    gst(p + i, h);
     return __half2float(h) * inv_s;
   }
   __device__ static float join(__half hi, __half lo, float inv_s) {
@@ -230,10 +241,10 @@ template <> struct Codec<PR_F16S> {
   __device__ static void store0(__half* p, long long i, __half* lo, long long j, float v, float s) {
     const float x = v * s;
     const __half h = __float2half_rn(x);
-    p[i] = h;
+    gst(p + i, h);
     // x - h is exact in FP32: h is x rounded to 11 significant bits, and the
     // difference holds the rest of x's bits
-    lo[j] = __float2half_rn(__fsub_rn(x, __half2float(h)) * kLoScale);
+    gst(lo + j, __float2half_rn(__fsub_rn(x, __half2float(h)) * kLoScale));
   }
 };
 
@@ -405,8 +416,8 @@ __device__ __forceinline__ real driver_long(const StepParams& P, const StepConst
     if (!(q > real(-1) && q < real(P.plen))) return real(0);
     const int j = (int)floor(q);
     const real fr = q - real(j);
-    const real a = j >= 0 ? real(P.profile[j]) : real(0);
-    const real b = j + 1 < P.plen ? real(P.profile[j + 1]) : real(0);
+    const real a = j >= 0 ? real(gld(P.profile + j)) : real(0);
+    const real b = j + 1 < P.plen ? real(gld(P.profile + j + 1)) : real(0);
     return (real(1) - fr) * a + fr * b;
   }
   return S.alpha * exp(-zeta * zeta * S.inv2sz2);

@@ -235,16 +235,16 @@ __device__ __forceinline__ void load_fields(const StepParams& P, int e0, int e1,
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (e_present<DIM>(a)) {
-      F.Ec[a] = Ein[a * pl + id];
-      if (CF) F.Ec_lo[a] = Elo[a * pl + id];
+      F.Ec[a] = gld(Ein + a * pl + id);
+      if (CF) F.Ec_lo[a] = gld(Elo + a * pl + id);
     }
     if (b_present<DIM>(a)) {
-      F.Bc[a] = Bin[a * pl + id];
-      if (CF) F.Bc_lo[a] = Blo[a * pl + id];
+      F.Bc[a] = gld(Bin + a * pl + id);
+      if (CF) F.Bc_lo[a] = gld(Blo + a * pl + id);
       if (axis_present<DIM>(a)) {
         const int o = a * pl + id + nb_offset<EDGE>(P, e[a], a, -1);
-        F.Bm[a] = Bin[o];
-        if (CF) F.Bm_lo[a] = Blo[o];
+        F.Bm[a] = gld(Bin + o);
+        if (CF) F.Bm_lo[a] = gld(Blo + o);
       }
     }
   }
@@ -254,13 +254,13 @@ __device__ __forceinline__ void load_fields(const StepParams& P, int e0, int e1,
     const int b = (a + 1) % 3, d = (a + 2) % 3;
     if (axis_present<DIM>(b) && b_present<DIM>(d)) {
       const int o = d * pl + id + nb_offset<EDGE>(P, e[b], b, +1);
-      F.Bp[d][b] = Bin[o];
-      if (CF) F.Bp_lo[d][b] = Blo[o];
+      F.Bp[d][b] = gld(Bin + o);
+      if (CF) F.Bp_lo[d][b] = gld(Blo + o);
     }
     if (axis_present<DIM>(d) && b_present<DIM>(b)) {
       const int o = b * pl + id + nb_offset<EDGE>(P, e[d], d, +1);
-      F.Bp[b][d] = Bin[o];
-      if (CF) F.Bp_lo[b][d] = Blo[o];
+      F.Bp[b][d] = gld(Bin + o);
+      if (CF) F.Bp_lo[b][d] = gld(Blo + o);
     }
   }
 }
@@ -573,8 +573,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
         real* tp = reinterpret_cast<real*>(P.tape);
         const int id_own = cell_index32(P, gz, gx, gy);
 #pragma unroll
-        for (int k = 0; k < K; ++k) tp[k * pl + id_own] = dA_own[k];
-        if constexpr (DIM == 2) tp[(K + DIM) * pl + id_own] = F.Bc[2] + F.Bc_lo[2];
+        for (int k = 0; k < K; ++k) gst(tp + k * pl + id_own, dA_own[k]);
+        if constexpr (DIM == 2) gst(tp + (K + DIM) * pl + id_own, F.Bc[2] + F.Bc_lo[2]);
       }
     }
   }
@@ -699,9 +699,9 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (e_present<DIM>(a)) {
-      Eout[a * pl + id] = sE[a * NR + r];
-      if (C::CF) Eout_lo[a * pl + id] = sE[(C::NEC + a) * NR + r];
-      if (DIM <= 2 && tape != nullptr) tape[(K + a) * pl + id] = Ev(a, r);
+      gst(Eout + a * pl + id, sE[a * NR + r]);
+      if (C::CF) gst(Eout_lo + a * pl + id, sE[(C::NEC + a) * NR + r]);
+      if (DIM <= 2 && tape != nullptr) gst(tape + (K + a) * pl + id, Ev(a, r));
       const int b = (a + 1) % 3, d = (a + 2) % 3;
       const bool ob = axis_present<DIM>(b), od = axis_present<DIM>(d);
       const int sb = ob ? C::stride(b) : 0, sd = od ? C::stride(d) : 0;
@@ -724,10 +724,10 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       if constexpr (C::CF) {
         real hi = F.Bc[a], lo = F.Bc_lo[a];
         two_float_add(hi, lo, -(dt * curl));
-        Bout[a * pl + id] = hi;
-        Bout_lo[a * pl + id] = lo;
+        gst(Bout + a * pl + id, hi);
+        gst(Bout_lo + a * pl + id, lo);
       } else {
-        Bout[a * pl + id] = F.Bc[a] - dt * curl;
+        gst(Bout + a * pl + id, F.Bc[a] - dt * curl);
       }
     }
   }
@@ -772,18 +772,18 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
     // backward time differences (zero on the first step after a reset)
     if (P.have_prev) {
       const real idt = S.idt;
-      dth00 = (th00 - prev[id]) * idt;
+      dth00 = (th00 - gldc(prev + id)) * idt;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
-        dth0[a] = (th0[a] - prev[(1 + a) * pl + id]) * idt;
-        dw[a] = (w[a] - prev[(1 + DIM + a) * pl + id]) * idt;
+        dth0[a] = (th0[a] - gldc(prev + (1 + a) * pl + id)) * idt;
+        dw[a] = (w[a] - gldc(prev + (1 + DIM + a) * pl + id)) * idt;
       }
     }
-    prev[id] = th00;
+    gst(prev + id, th00);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      prev[(1 + a) * pl + id] = th0[a];
-      prev[(1 + DIM + a) * pl + id] = w[a];
+      gst(prev + (1 + a) * pl + id, th0[a]);
+      gst(prev + (1 + DIM + a) * pl + id, w[a]);
     }
     // spatial gradients from the neighbours' records; gw[a][k] = d_k w^a
 #pragma unroll
