@@ -110,7 +110,7 @@ __device__ __forceinline__ void edge_lfs(const StepParams& P, const real* lfk, i
     if (P.periodic) {
       yz = wrap_or_clamp(yz, P.n[0], 1);
       if (DIM >= 2) yx = wrap_or_clamp(yx, P.n[1], 1);
-      l[i] = b[aidx(P, yz, yx)];
+      l[i] = gld(b + aidx(P, yz, yx));
       continue;
     }
     real s = 0;
@@ -129,7 +129,7 @@ __device__ __forceinline__ void edge_lfs(const StepParams& P, const real* lfk, i
 #pragma unroll
         for (int qx = 0; qx < (DIM >= 2 ? 3 : 1); ++qx) {
           if (cx[qx] < 0) continue;
-          s += b[aidx(P, cz[qz], cx[qx])];
+          s += gld(b + aidx(P, cz[qz], cx[qx]));
         }
       }
     }
@@ -171,7 +171,7 @@ __device__ __forceinline__ void load_node(const StepParams& P, const real* tp, i
   constexpr int K = Model<DIM, CL>::K;
   const int pl = (int)P.plane;
 #pragma unroll
-  for (int k = 0; k < K; ++k) N.dA[k] = tp[k * pl + id];
+  for (int k = 0; k < K; ++k) N.dA[k] = gld(tp + k * pl + id);
   decode_record<DIM, CL, real>(P, consts<real>(P), N.dA, N.rec);
 }
 
@@ -327,17 +327,17 @@ __device__ __forceinline__ void adj_local_node(const AdjParams& A, const LSrc& s
   const real* tE = tp + K * pl;
   real En[3] = {0, 0, 0}, Bn[3] = {0, 0, 0};
   if constexpr (DIM == 1) {
-    En[0] = tE[id];
+    En[0] = gld(tE + id);
   } else {
     // E_z: slots (z, x) and (z, x - 1) (conducting-wall ghost below x = 0)
-    real ez = tE[id];
-    if (x >= 1) ez += tE[aidx(P, z, x - 1)];
+    real ez = gld(tE + id);
+    if (x >= 1) ez += gld(tE + aidx(P, z, x - 1));
     else if (P.periodic) ez += tE[aidx(P, z, P.n[1] - 1)];
     En[0] = real(0.5) * ez;
     // E_x: slots (z, x) and (z - 1, x) (z clamps)
     const int zm = z >= 1 ? z - 1 : (P.periodic ? P.n[0] - 1 : 0);
-    En[1] = real(0.5) * (tE[pl + id] + tE[pl + aidx(P, zm, x)]);
-    Bn[2] = tp[(K + DIM) * pl + id];
+    En[1] = real(0.5) * (gld(tE + pl + id) + gld(tE + pl + aidx(P, zm, x)));
+    Bn[2] = gld(tp + (K + DIM) * pl + id);
   }
 
   // ---- WARMC: values of the sources' time and space derivatives ------------
@@ -359,7 +359,7 @@ __device__ __forceinline__ void adj_local_node(const AdjParams& A, const LSrc& s
       } else {
         const real* p0 = reinterpret_cast<const real*>(A.prev0);
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) wp[a] = p0[(1 + DIM + a) * pl + id];
+        for (int a = 0; a < DIM; ++a) wp[a] = gld(p0 + (1 + DIM + a) * pl + id);
       }
 #pragma unroll
       for (int a = 0; a < DIM; ++a) dw[a] = (w[a] - wp[a]) * S.idt;
@@ -372,22 +372,22 @@ __device__ __forceinline__ void adj_local_node(const AdjParams& A, const LSrc& s
       const int idp = k == 0 ? aidx(P, cp, x) : aidx(P, z, cp);
       const int idm = k == 0 ? aidx(P, cm, x) : aidx(P, z, cm);
       // w^a = lambda u^a of the neighbours, as their records give it
-      const real np_ = real(1) + tp[idp], nm_ = real(1) + tp[idm];
-      const real nlp = S.Arest[1] + tp[pl + idp], nlm = S.Arest[1] + tp[pl + idm];
+      const real np_ = real(1) + gld(tp + idp), nm_ = real(1) + gld(tp + idm);
+      const real nlp = S.Arest[1] + gld(tp + pl + idp), nlm = S.Arest[1] + gld(tp + pl + idm);
       const real lamp = nlp / np_, lamm = nlm / nm_;
       const real inlp = real(1) / nlp, inlm = real(1) / nlm;
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
-        gw[a][k] = (lamp * (tp[(2 + a) * pl + idp] * inlp) - lamm * (tp[(2 + a) * pl + idm] * inlm)) * S.i2dx;
+        gw[a][k] = (lamp * (gld(tp + (2 + a) * pl + idp) * inlp) - lamm * (gld(tp + (2 + a) * pl + idm) * inlm)) * S.i2dx;
     }
     // adjoints of the previous-step values this step wrote
     if (A.lp_in) {
       const real* lpi = reinterpret_cast<const real*>(A.lp_in);
-      lm.th00 += lpi[id];
+      lm.th00 += gld(lpi + id);
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
-        lm.th0[a] += lpi[(1 + a) * pl + id];
-        lm.w[a] += lpi[(1 + DIM + a) * pl + id];
+        lm.th0[a] += gld(lpi + (1 + a) * pl + id);
+        lm.w[a] += gld(lpi + (1 + DIM + a) * pl + id);
       }
     }
   }
@@ -580,30 +580,30 @@ __device__ __forceinline__ real lEn_slot(const AdjParams& A, int a, int sz, int 
   const real* rEn = reinterpret_cast<const real*>(A.rEn);
   const int id = aidx(P, sz, sx);
   if constexpr (DIM == 1) {
-    return lE[id] + rEn[id];
+    return gld(lE + id) + gld(rEn + id);
   } else {
     const real* lB = reinterpret_cast<const real*>(A.lB_in) + 2 * pl;  // B_y
     const real* rE = rEn + a * pl;
     const real cdt = S.dt * S.idx;
     if (a == 0) {
       if (!P.periodic && sx == P.n[1] - 1) return real(0);  // conducting wall
-      real v = lE[id] + real(0.5) * rE[id] + cdt * lB[id];
+      real v = gld(lE + id) + real(0.5) * gld(rE + id) + cdt * gld(lB + id);
       int xp = sx + 1;
       if (xp >= P.n[1]) xp = P.periodic ? 0 : -1;
       if (xp >= 0) {
         const int idp = aidx(P, sz, xp);
-        v += real(0.5) * rE[idp] - cdt * lB[idp];
+        v += real(0.5) * gld(rE + idp) - cdt * gld(lB + idp);
       }
       return v;
     } else {
-      real v = lE[pl + id] + real(0.5) * rE[id] - cdt * lB[id];
+      real v = gld(lE + pl + id) + real(0.5) * gld(rE + id) - cdt * gld(lB + id);
       int zp = sz + 1;
       if (zp >= P.n[0]) zp = P.periodic ? 0 : -1;
       if (zp >= 0) {
         const int idp = aidx(P, zp, sx);
-        v += real(0.5) * rE[idp] + cdt * lB[idp];
+        v += real(0.5) * gld(rE + idp) + cdt * gld(lB + idp);
       }
-      if (!P.periodic && sz == 0) v += real(0.5) * rE[id] + cdt * lB[id];
+      if (!P.periodic && sz == 0) v += real(0.5) * gld(rE + id) + cdt * gld(lB + id);
       return v;
     }
   }
@@ -662,14 +662,14 @@ __device__ __forceinline__ void adj_field_node(const AdjParams& A, const LSrc& s
       r2 = 0.0;
     } else {
       const real cdt = dt * S.idx;
-      real lBy = reinterpret_cast<const real*>(A.lB_in)[2 * pl + id] +
-                 reinterpret_cast<const real*>(A.rBn)[2 * pl + id];
+      real lBy = gld(reinterpret_cast<const real*>(A.lB_in) + 2 * pl + id) +
+                 gld(reinterpret_cast<const real*>(A.rBn) + 2 * pl + id);
       // E_z: offset axis x
       {
         const real lc = lEn_slot<DIM, real>(A, 0, z, x);
         lEo[id] = lc;
-        r0 = (double)(dt * lc) * A.Tx[x];
-        r2 = (double)(dt * lc) * A.Tx[P.n[1] + x];
+        r0 = (double)(dt * lc) * gld(A.Tx + x);
+        r2 = (double)(dt * lc) * gld(A.Tx + P.n[1] + x);
         real jsum = real(0.5) * lc;   // slot s = this node
         lBy -= cdt * lc;
         const Pre pr = preimage(x, P.n[1], +1, P.periodic);
@@ -719,13 +719,13 @@ __device__ __forceinline__ void adj_field_node(const AdjParams& A, const LSrc& s
           const int m = k == 0 ? aidx(P, pr.v[q], x) : aidx(P, z, pr.v[q]);
           const real c = sgn * S.i2dx;
           if constexpr (CL == CL_LEC) {
-            lm.Pi += c * S.mu * rG[k * pl + m];
+            lm.Pi += c * S.mu * gld(rG + k * pl + m);
           } else {
-            lm.th0[k] += c * rG[m];
+            lm.th0[k] += c * gld(rG + m);
 #pragma unroll
             for (int a = 0; a < DIM; ++a) {
-              lm.th[a][k] += c * rG[(1 + a) * pl + m];
-              lm.w[a] -= c * rG[(1 + DIM + a * DIM + k) * pl + m];
+              lm.th[a][k] += c * gld(rG + (1 + a) * pl + m);
+              lm.w[a] -= c * gld(rG + (1 + DIM + a * DIM + k) * pl + m);
             }
           }
         }
@@ -735,7 +735,7 @@ __device__ __forceinline__ void adj_field_node(const AdjParams& A, const LSrc& s
     real lA[K];
     const real* rA = reinterpret_cast<const real*>(A.rA);
 #pragma unroll
-    for (int k = 0; k < K; ++k) lA[k] = rA[k * pl + id];
+    for (int k = 0; k < K; ++k) lA[k] = gld(rA + k * pl + id);
     decode_adjoint<DIM, CL, real>(P, S, N, lm, lA);
 
     // ---- population adjoint of the previous state ----------------------------
