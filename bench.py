@@ -230,6 +230,31 @@ def _oracle_sample(cfg, budget_s=15.0):
     return ncell * nsteps / dt / 1e6, nsteps, dt
 
 
+def _slowest_rank_seconds(local_s, world, device):
+    """The timed region's length over all ranks: a barrier, then the maximum
+    of the ranks' times (the only collective; none on the data path)."""
+    if world <= 1:
+        return local_s
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_s], device=device, dtype=torch.float64)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _aggregate_mlups(ncell_per_rank, steps, world, seconds):
+    """Whole-job node updates per second (MLUPS): every rank advances its own
+    replica (or shard) by `steps` steps of ncell_per_rank nodes."""
+    return ncell_per_rank * steps * world / seconds / 1e6
+
+
+def _batch_shard(nruns, rank, world):
+    """Indices of the batched sweep's runs that rank `rank` of `world` owns:
+    whole runs, round-robin, so the ranks exchange nothing."""
+    return list(range(rank, nruns, world))
+
+
 def _batch_cfgs(nruns):
     """The first nruns of the batched sweep's 64 seeded draws, as run
     configurations."""
@@ -243,12 +268,24 @@ def _batch_cfgs(nruns):
 
 def run_batch_case(a):
     """--warmup then --steps batched steps of the sweep's first --batch-runs
-    runs (FP32); prints the timing as one JSON line."""
+    runs (FP32); prints the timing as one JSON line.  Under torchrun each
+    rank advances its own shard of whole runs (no data-path collective) and
+    rank 0 reports the whole job."""
     import torch
+    import torch.distributed as dist
 
     from paper_2309_04872_gb300 import lbpwfa as lb
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
     lb.load_library()
     draws, cfgs = _batch_cfgs(max(1, min(64, a.batch_runs)))
+    mine = _batch_shard(len(cfgs), rank, world)
+    draws = [draws[i] for i in mine]
+    cfgs = [cfgs[i] for i in mine]
     stream = torch.cuda.Stream()
     with lb.Batch(cfgs, "fp32", stream=stream.cuda_stream, tune=not a.no_tune) as b:
         info = b.info()
@@ -259,12 +296,22 @@ def run_batch_case(a):
         b.step(a.steps)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / max(1, a.steps)
-    print(json.dumps({"metric": "batched step timing", "workload": f"batch_2d_{len(cfgs)}runs_fp32",
-                      "runs": len(cfgs), "lec_runs": sum(1 for d in draws if d["closure"] == "lec"),
-                      "nodes": int(info.ncell), "steps": a.steps, "ms_per_step": round(ms, 4),
-                      "mlups": round(info.ncell / (ms * 1e-3) / 1e6, 2),
-                      "tile": {"lec": list(info.tile[0]), "warmc": list(info.tile[1])}}), flush=True)
+        seconds = e0.elapsed_time(e1) * 1e-3
+    seconds = _slowest_rank_seconds(seconds, world, torch.device("cuda", local))
+    nodes = torch.tensor([float(info.ncell)], dtype=torch.float64, device=torch.device("cuda", local))
+    if world > 1:
+        dist.all_reduce(nodes)
+    if rank == 0:
+        total_runs = max(1, min(64, a.batch_runs))
+        ms = seconds * 1e3 / max(1, a.steps)
+        print(json.dumps({"metric": "batched step timing", "workload": f"batch_2d_{total_runs}runs_fp32",
+                          "runs": total_runs, "n_gpus": world, "runs_on_rank0": len(cfgs),
+                          "nodes": int(nodes.item()), "steps": a.steps, "ms_per_step": round(ms, 4),
+                          "mlups": round(_aggregate_mlups(float(nodes.item()) / world, a.steps, world, seconds), 2),
+                          "tile_rank0": {"lec": list(info.tile[0]), "warmc": list(info.tile[1])}}), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def run_adjoint_case(a):
@@ -341,13 +388,8 @@ def run_ours(a):
         main = measure(a.precision, a.steps, a.warmup)
     clocks = clk.summary()
 
-    total_s = main["total_ms"] * 1e-3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = main["ncell"] * a.steps * world / total_s / 1e6
+    total_s = _slowest_rank_seconds(main["total_ms"] * 1e-3, world, dev)
+    value = _aggregate_mlups(main["ncell"], a.steps, world, total_s)
 
     out = {
         "metric": METRIC,
