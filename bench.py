@@ -41,6 +41,9 @@ METRIC = "MLUPS and % of HBM roofline per closure/precision; adjoint cost ratio 
 WORKLOAD_2D = dict(dim=2, n=(1024, 512), dx=0.05, courant=0.1, tau=0.53, closure="lec", dv=3, mu=1e-2,
                    alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=4.0, boundary="open", init_fields=True)
 WORKLOAD_NAME = "2d_lec_1024x512_fp32"
+# step kernel of each lbpwfa_info kernel_variant
+KERNEL_NAMES = {1: "lb_step_kernel", 2: "lb_step_tma2d_kernel", 3: "lb_step_persist2d_kernel",
+                4: "lb_step_march3d_kernel"}
 
 # the 1D configuration (launch-bound, 0.2 MB of state: reported as steps/s)
 CONFIG_1D = dict(dim=1, n=(2048,), dx=40 / 2048, courant=0.5, tau=0.52, closure="lec", dv=1, mu=1e-3,
@@ -72,10 +75,11 @@ def _args():
                          "sweep over --steps steps, for profiling")
     ap.add_argument("--batch-runs", type=int, default=64, help="batch_2d: runs of the sweep (1..64)")
     ap.add_argument("--no-tune", action="store_true", help="batch_2d: skip the tile autotuner")
-    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="0: automatic (2D LEC: persistent TMA CTAs in FP32 and FP16S, a TMA box per CTA "
-                         "in FP64), 1: plain global-memory pull kernel, 2: TMA box per CTA, "
-                         "3: persistent CTAs that refill their TMA box after the decode phase")
+                         "in FP64; 3D: marching columns), 1: plain global-memory pull kernel (3D: 32 x 4 x 4 "
+                         "tiles), 2: TMA box per CTA, 3: persistent CTAs that refill their TMA box after the "
+                         "decode phase, 4: 3D marching columns")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-precision mode table")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -381,8 +385,7 @@ def run_ours(a):
         gbs = info.bytes_per_update * info.ncell / (mean_ms * 1e-3) / 1e9
         return dict(mlups=mlups, ms=mean_ms, gbs=gbs, frac=gbs / hbm, bytes_per_update=info.bytes_per_update,
                     ncell=info.ncell, total_ms=sum(times), nonfinite=bad, times=times,
-                    kernel={3: "lb_step_persist2d_kernel", 1: "lb_step_kernel",
-                            2: "lb_step_tma2d_kernel"}[info.kernel_variant])
+                    kernel=KERNEL_NAMES[info.kernel_variant])
 
     with ClockSampler(local) as clk:
         main = measure(a.precision, a.steps, a.warmup)
@@ -538,7 +541,7 @@ def _configs(stream, flush, hbm):
             "mlups": round(info.ncell / (mean * 1e-3) / 1e6, 2), "ms_per_step": round(mean, 3),
             "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
             "bytes_per_update": info.bytes_per_update, "steps": len(times),
-            "kernel": {3: "lb_step_persist2d_kernel", 1: "lb_step_kernel", 2: "lb_step_tma2d_kernel"}[info.kernel_variant],
+            "kernel": KERNEL_NAMES[info.kernel_variant],
             "device_gb": round(info.device_bytes / 1e9, 2)}
     return res
 

@@ -114,8 +114,11 @@ typedef struct {
                               CTA (2D open boundaries);
                               3: LEC 2D with persistent CTAs, each refilling
                               its TMA box with its next tile as soon as the
-                              decode phase has read it.  All compute the
-                              same step. */
+                              decode phase has read it; 4: 3D columns of
+                              32 x 8 nodes marching up chunks of 32 planes,
+                              each plane decoded once per column (the
+                              automatic 3D choice; 1 gives 32 x 4 x 4 tiles).
+                              All compute the same step. */
 } lbpwfa_params;
 
 typedef struct {
@@ -130,7 +133,7 @@ typedef struct {
                               step kernel (populations + fields [+ WARMC
                               previous-step values]) */
   int kernel_variant;      /* step kernel in use: 1 plain, 2 TMA box per CTA,
-                              3 persistent TMA */
+                              3 persistent TMA, 4 3D marching columns */
 } lbpwfa_info_t;
 
 /* Create a run: validates *p, allocates all device state on the handle's

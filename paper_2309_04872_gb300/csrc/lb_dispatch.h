@@ -36,6 +36,12 @@ struct KernelSet {
   size_t tma_smem;
   cudaError_t (*prepare_tma)();
   void (*step_tma)(const StepParams&, const void* tensor_map, dim3 grid, cudaStream_t);
+  // 3D step marching columns of march_tz x march_tx nodes up chunks of
+  // march_yc planes; has_march == false outside 3D
+  bool has_march;
+  int march_tz, march_tx, march_yc;
+  cudaError_t (*prepare_march)();
+  void (*step_march)(const StepParams&, dim3 grid, cudaStream_t);
   // persistent TMA 2D step (LEC), per_ctas CTAs per SM; has_persist == false when not built;
   // persist_auto: the automatic kernel choice takes it
   bool has_persist, persist_auto;

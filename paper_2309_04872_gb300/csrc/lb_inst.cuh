@@ -18,6 +18,10 @@ template <int CL, int PR> struct Tile<3, CL, PR> {
   static constexpr int TZ = 32, TX = 4, TY = 4;
 };
 
+// 3D marching columns (the automatic 3D kernel): 32 x 8 nodes per column,
+// chunks of 32 planes.
+struct March3D { static constexpr int TZ = 32, TX = 8, YC = 32; };
+
 inline unsigned grid1(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 template <int DIM, int CL, int PR>
@@ -33,6 +37,18 @@ struct Impl {
   }
   static void step(const StepParams& P, dim3 grid, cudaStream_t s) {
     lb_step_kernel<DIM, CL, PR, T::TZ, T::TX, T::TY><<<grid, Cfg::NT, Cfg::smem_bytes_gkeep, s>>>(P);
+  }
+  using MC = StepCfg<3, CL, PR, March3D::TZ, March3D::TX, 1>;
+  static constexpr bool kMarch = DIM == 3;
+  static cudaError_t prepare_march() {
+    if constexpr (kMarch)
+      return cudaFuncSetAttribute(lb_step_march3d_kernel<CL, PR, March3D::TZ, March3D::TX, March3D::YC>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MC::smem_bytes);
+    return cudaErrorNotSupported;
+  }
+  static void step_march(const StepParams& P, dim3 grid, cudaStream_t s) {
+    if constexpr (kMarch)
+      lb_step_march3d_kernel<CL, PR, March3D::TZ, March3D::TX, March3D::YC><<<grid, MC::NT, MC::smem_bytes, s>>>(P);
   }
   static void init_fields(const AuxParams& A, void* E, void* B, void* Elo, void* Blo, cudaStream_t s) {
     init_fields_kernel<DIM, real><<<grid1(A.ncell, 256), 256, 0, s>>>(A, (real*)E, (real*)B, (real*)Elo, (real*)Blo);
@@ -90,6 +106,12 @@ struct Impl {
           P, *reinterpret_cast<const CUtensorMap*>(map), ntz, ntiles);
   }
   static void fill(KernelSet* ks) {
+    ks->has_march = kMarch;
+    ks->march_tz = March3D::TZ;
+    ks->march_tx = March3D::TX;
+    ks->march_yc = March3D::YC;
+    ks->prepare_march = &prepare_march;
+    ks->step_march = &step_march;
     ks->has_persist = kPersist;
     ks->persist_auto = kPersist && PC::automatic;
     ks->per_tz = PC::TZ;

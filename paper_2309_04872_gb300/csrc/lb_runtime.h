@@ -51,6 +51,7 @@ struct lbpwfa_s {
   std::string err;
   bool use_tma = false;
   bool use_persist = false;
+  bool use_march = false;  // 3D marching columns
   bool in_batch = false;  // owned by a batch: stepped only through lbpwfa_batch_step
   int num_sms = 0;
   alignas(64) CUtensorMap maps[2];

@@ -89,7 +89,7 @@ int validate(const lbpwfa_params* p) {
   if (p->dim >= 2 && !(p->sigma_r > 0.0)) return LBPWFA_ERR_INVALID;
   if (p->precision < LBPWFA_FP64 || p->precision > LBPWFA_FP16S) return LBPWFA_ERR_INVALID;
   if (p->boundary != LBPWFA_OPEN && p->boundary != LBPWFA_PERIODIC) return LBPWFA_ERR_INVALID;
-  if (p->kernel_variant < 0 || p->kernel_variant > 3) return LBPWFA_ERR_INVALID;
+  if (p->kernel_variant < 0 || p->kernel_variant > 4) return LBPWFA_ERR_INVALID;
   long long cells = 1;
   for (int a = 0; a < p->dim; ++a) cells *= p->n[a];
   if (cells > (1LL << 34)) return LBPWFA_ERR_INVALID;
@@ -297,7 +297,12 @@ int launch_step(lbpwfa_s* h, void* tape) {
                                : step_grid(h);
   StepParams P = step_params(h);
   P.tape = tape;
-  if (h->use_persist) {
+  if (h->use_march) {
+    const dim3 mg((unsigned)((h->n[0] + h->ks.march_tz - 1) / h->ks.march_tz),
+                  (unsigned)((h->n[1] + h->ks.march_tx - 1) / h->ks.march_tx),
+                  (unsigned)((h->n[2] + h->ks.march_yc - 1) / h->ks.march_yc));
+    h->ks.step_march(P, mg, h->stream);
+  } else if (h->use_persist) {
     const int ntz = (h->n[0] + h->ks.per_tz - 1) / h->ks.per_tz;
     const int ntiles = ntz * ((h->n[1] + h->ks.per_tx - 1) / h->ks.per_tx);
     const int slots = h->num_sms * h->ks.per_ctas;
@@ -438,6 +443,12 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  // 3D: marching columns unless the tiled kernel is asked for (variant 1)
+  h->use_march = dim == 3 && (p->kernel_variant == 0 || p->kernel_variant == 4) && h->ks.has_march;
+  if (h->use_march && h->ks.prepare_march() != cudaSuccess) {
+    cudaGetLastError();
+    h->use_march = false;
   }
   const bool tma_ok = dim == 2 && p->boundary == LBPWFA_OPEN;
   // automatic choice for LEC: the persistent refilling CTAs where the tile
@@ -669,7 +680,7 @@ int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info) {
   // FP32 fields: high and low parts
   const double field_words = (ne + nbf) * (h->real_sz == 4 ? 2.0 : 1.0);
   info->bytes_per_update = 2.0 * h->NPL * h->store_sz + 2.0 * (field_words + h->NPREV) * h->real_sz;
-  info->kernel_variant = h->use_persist ? 3 : (h->use_tma ? 2 : 1);
+  info->kernel_variant = h->use_march ? 4 : (h->use_persist ? 3 : (h->use_tma ? 2 : 1));
   return LBPWFA_OK;
 }
 

@@ -387,6 +387,29 @@ def test_2d_kernel_variants_agree(closure, prec, n):
             assert np.max(np.abs(out[v][1] - out[0][1])) <= _ROUNDOFF[prec] * fmax, variant
 
 
+# 3D: the marching-column kernel (automatic) against the 32 x 4 x 4 tiles;
+# 40 x 17 x 70 spans three chunks of 32 planes, the last one ragged
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+@pytest.mark.parametrize("n", [(37, 21, 13), (40, 17, 70)])
+def test_3d_marching_agrees_with_tiles(closure, prec, n):
+    cfg = _cfg(3, closure, "open", n=n)
+    orc = O.Oracle(cfg)
+    f, E, B = _random_state(orc, 91, cfg["mu"])
+    out = []
+    for variant, kv in ((0, 4), (1, 1)):
+        with lb.Run(cfg, prec, variant=variant) as run:
+            assert run.info().kernel_variant == kv
+            run.set_state(f, E, B)
+            run.step(7)
+            out.append((run.advected(), run.fields()))
+    rest = orc.rest_advected()[:, None]
+    dev = np.max(np.abs(out[1][0] - rest))
+    fmax = np.max(np.abs(out[1][1]))
+    assert np.max(np.abs(out[0][0] - out[1][0])) <= _ROUNDOFF[prec] * dev
+    assert np.max(np.abs(out[0][1] - out[1][1])) <= _ROUNDOFF[prec] * fmax
+
+
 @pytest.mark.parametrize("prec,tol,floor", [("fp64", 1e-12, 1e-13), ("fp32", 1e-4, 1e-7)])
 def test_plain_kernel_2d_parity(prec, tol, floor):
     cfg = _cfg(2, "lec", "open")
