@@ -46,12 +46,15 @@ STEP_KERNEL_SOURCES = ["lb_common.cuh", "lb_step.cuh", "lb_step_tma.cuh", "lb_in
 
 
 def step_kernel_digest() -> str:
+    """Digest of the step-kernel sources and compile flags, the same on every
+    machine (the include directory enters by name, not by its path)."""
     h = hashlib.sha256()
     for name in STEP_KERNEL_SOURCES:
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    flags = ["include" if f == INCLUDE else f for f in ARCH + NVCC_FLAGS]
+    h.update(" ".join(flags).encode())
     return h.hexdigest()
 
 
