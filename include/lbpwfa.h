@@ -154,8 +154,12 @@ int lbpwfa_step(lbpwfa_t h, int64_t nsteps);
  *   0 n, 1 u_z, 2 u_x, 3 u_y, 4 gamma, 5 p_z, 6 p_x, 7 p_y (gamma u),
  *   8 LEC rest-frame pressure P0 = mu (n/gamma)^(1+2/D) (0 for WARMC),
  *   9 lambda = n/h (WARMC; 0 for LEC),
- *   10..15 theta zz, xx, yy, zx, zy, xy (WARMC; 0 for LEC).
- * dst holds count >= popcount(mask & 0xFFFF) * ncell doubles, on the device
+ *   10..15 theta zz, xx, yy, zx, zy, xy (WARMC; 0 for LEC),
+ *   16 P_par, 17 P_perp: rest-frame pressures along and across z (App. A's
+ *   inversion of theta with r -> x, phi -> y: P_perp = theta_yy, P_par =
+ *   [theta_xx + theta_zz - theta^00 u^2 - theta_yy (1 + u_x^2)] /
+ *   (1 + u_z^2), theta^00 = u_i u_j theta_ij; 2D WARMC only, else 0).
+ * dst holds count >= popcount(mask & 0x3FFFF) * ncell doubles, on the device
  * when dst_is_device, else on the host.  Errors: INVALID, CUDA. */
 int lbpwfa_moments(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_is_device);
 

@@ -79,6 +79,8 @@ def lib():
         L.orc_advected.argtypes = [ctypes.c_void_p, _DP]
         L.orc_moments.restype = ctypes.c_int
         L.orc_moments.argtypes = [ctypes.c_void_p, ctypes.c_uint, _DP]
+        L.orc_rest_pressures.restype = None
+        L.orc_rest_pressures.argtypes = [_DP, _DP, _DP]
         L.orc_reduce.argtypes = [ctypes.c_void_p, _DP]
         L.orc_stencil.restype = ctypes.c_int
         L.orc_stencil.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP]
@@ -223,7 +225,7 @@ class Oracle:
         return A.reshape(self.K, self.ncell)
 
     def moments(self, mask: int) -> np.ndarray:
-        nb = bin(mask & 0xFFFF).count("1")
+        nb = bin(mask & 0x3FFFF).count("1")
         out = np.zeros(nb * self.ncell)
         lib().orc_moments(self._h, ctypes.c_uint(mask), _ptr(out))
         return out.reshape(nb, self.ncell)
@@ -292,6 +294,16 @@ def decode_warmc(dim: int, A):
     lib().orc_decode_warmc(int(dim), _ptr(a), _ptr(o))
     return dict(n=o[0], lam=o[1], u=o[2:5].copy(), gamma=o[5], th=o[6:15].reshape(3, 3).copy(),
                 th0=o[15:18].copy(), th00=o[18], w=o[19:22].copy())
+
+
+def rest_pressures(th, u):
+    """(P_par, P_perp) of a WARMC tensor theta^{ij} ([3][3], order z, x, y)
+    at 3-velocity u = (u_z, u_x, u_y): App. A's inversion, r -> x, phi -> y."""
+    th = np.ascontiguousarray(np.asarray(th, dtype=np.float64).reshape(9))
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(3))
+    out = np.zeros(2)
+    lib().orc_rest_pressures(_ptr(th), _ptr(u), _ptr(out))
+    return float(out[0]), float(out[1])
 
 
 def lec_source(mu, n, u, gradPi, E, B):

@@ -887,15 +887,32 @@ void orc_advected(const orc_state* S, double* A)
     }
 }
 
+/* Rest-frame pressures of the WARMC tensor (App. A, the axisymmetric
+ * inversion, read with r -> x and phi -> y, c = 1): P_perp = theta^{yy} and
+ * P_par = [theta^{xx} + theta^{zz} - theta^{00} u^2 - theta^{yy} (1 + u_x^2)]
+ * / (1 + u_z^2), with theta^{00} = u_i u_j theta^{ij} (the mass-shell rows).
+ * th is [3][3] in the order z, x, y; u = (u_z, u_x, u_y); out = {P_par,
+ * P_perp}.                                                                 */
+void orc_rest_pressures(const double* th, const double* u, double* out)
+{
+  double t00 = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) t00 += u[i] * u[j] * th[3 * i + j];
+  const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  out[1] = th[8];
+  out[0] = (th[4] + th[0] - t00 * u2 - th[8] * (1.0 + u[1] * u[1])) / (1.0 + u[0] * u[0]);
+}
+
 /* Bits: 0 n, 1 u_z, 2 u_x, 3 u_y, 4 gamma, 5 p_z, 6 p_x, 7 p_y (gamma u),
  * 8 LEC rest-frame pressure P0 = mu (n/gamma)^(1+2/D), 9 lambda (WARMC),
- * 10..15 theta zz, xx, yy, zx, zy, xy (WARMC).  Output [bit][cell] in
+ * 10..15 theta zz, xx, yy, zx, zy, xy (WARMC), 16 P_par and 17 P_perp
+ * (WARMC in 2D: orc_rest_pressures; 0 otherwise).  Output [bit][cell] in
  * increasing bit order.                                                    */
 int orc_moments(const orc_state* S, unsigned mask, double* dst)
 {
   long nc = S->ncell;
   int nout = 0;
-  for (int b = 0; b < 16; ++b) {
+  for (int b = 0; b < 18; ++b) {
     if (!(mask & (1u << b))) continue;
     for (long c = 0; c < nc; ++c) {
       orc_macro m; decode_node(S, c, &m);
@@ -917,6 +934,16 @@ int orc_moments(const orc_state* S, unsigned mask, double* dst)
         case 13: v = m.th[0][1]; break;
         case 14: v = m.th[0][2]; break;
         case 15: v = m.th[1][2]; break;
+        case 16:
+        case 17:
+          if (S->p.closure == ORC_WARMC && S->p.dim == 2) {
+            double th9[9], pr[2];
+            for (int i = 0; i < 3; ++i)
+              for (int j = 0; j < 3; ++j) th9[3 * i + j] = m.th[i][j];
+            orc_rest_pressures(th9, m.u, pr);
+            v = pr[b - 16];
+          }
+          break;
       }
       dst[(long)nout * nc + c] = v;
     }

@@ -55,6 +55,7 @@ void orc_get_state(const orc_state* S, double* f, double* E, double* B);
 void orc_step(orc_state* S, long nsteps);
 void orc_advected(const orc_state* S, double* A);
 int orc_moments(const orc_state* S, unsigned mask, double* dst);
+void orc_rest_pressures(const double* th, const double* u, double* out);
 void orc_reduce(const orc_state* S, double* out);
 
 /* pieces exposed for the pins */

@@ -230,8 +230,8 @@ __global__ void moments_kernel(AuxParams A, const typename Prec<PR>::store* fs, 
   unflatten(A, c, e);
   double Av[M::K];
   advected_d<DIM, CL, PR>(A, fs, e, Av);
-  double v[16];
-  for (int j = 0; j < 16; ++j) v[j] = 0.0;
+  double v[18];
+  for (int j = 0; j < 18; ++j) v[j] = 0.0;
   const double n = Av[0];
   v[0] = n;
   if constexpr (CL == CL_LEC) {
@@ -258,9 +258,20 @@ __global__ void moments_kernel(AuxParams A, const typename Prec<PR>::store* fs, 
       const int j = M::thidx(ta[q], tb[q]);
       v[10 + q] = j >= 0 ? Av[2 + DIM + j] / lam : 0.0;
     }
+    if constexpr (DIM == 2) {
+      // rest-frame pressures (App. A inversion, r -> x, phi -> y, c = 1):
+      // P_perp = theta^{yy}, P_par = [theta^{xx} + theta^{zz} - theta^{00}
+      // u^2 - theta^{yy} (1 + u_x^2)] / (1 + u_z^2), theta^{00} = u_i u_j
+      // theta^{ij} (mass-shell rows); theta^{xy} = theta^{zy} = 0 in 2D
+      const double tzz = v[10], txx = v[11], tyy = v[12], tzx = v[13];
+      const double t00 = u[0] * u[0] * tzz + u[1] * u[1] * txx + 2.0 * u[0] * u[1] * tzx;
+      const double u2 = u[0] * u[0] + u[1] * u[1];
+      v[16] = (txx + tzz - t00 * u2 - tyy * (1.0 + u[1] * u[1])) / (1.0 + u[0] * u[0]);
+      v[17] = tyy;
+    }
   }
   int o = 0;
-  for (int bit = 0; bit < 16; ++bit) {
+  for (int bit = 0; bit < 18; ++bit) {
     if (!(mask & (1u << bit))) continue;
     out[(long long)o * A.ncell + c] = v[bit];
     ++o;

@@ -527,9 +527,9 @@ int lbpwfa_advected(lbpwfa_t h, double* dst, size_t count, int dst_is_device) {
 
 int lbpwfa_moments(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_is_device) {
   if (!h || !dst) return LBPWFA_ERR_INVALID;
-  mask &= 0xFFFFu;
+  mask &= 0x3FFFFu;
   int nb = 0;
-  for (int b = 0; b < 16; ++b) nb += (mask >> b) & 1u;
+  for (int b = 0; b < 18; ++b) nb += (mask >> b) & 1u;
   const size_t need = (size_t)nb * h->ncell;
   if (nb == 0) return LBPWFA_OK;
   if (count < need) return LBPWFA_ERR_INVALID;

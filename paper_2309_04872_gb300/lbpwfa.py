@@ -23,6 +23,7 @@ _PREC = {"fp64": FP64, "fp32": FP32, "fp16s": FP16S}
 M_N, M_UZ, M_UX, M_UY, M_GAMMA, M_PZ, M_PX, M_PY = (1 << b for b in range(8))
 M_P0, M_LAMBDA = 1 << 8, 1 << 9
 M_TH_ZZ, M_TH_XX, M_TH_YY, M_TH_ZX, M_TH_ZY, M_TH_XY = (1 << b for b in range(10, 16))
+M_P_PAR, M_P_PERP = 1 << 16, 1 << 17
 F_EX, F_EY, F_EZ, F_BX, F_BY, F_BZ = (1 << b for b in range(6))
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
@@ -236,7 +237,7 @@ class Run:
         self._check(load_library().lbpwfa_synchronize(self._h), "lbpwfa_synchronize")
 
     def moments(self, mask: int, out=None):
-        nb = bin(mask & 0xFFFF).count("1")
+        nb = bin(mask & 0x3FFFF).count("1")
         if out is None:
             out = np.zeros((nb, self.ncell))
         ptr, dev, keep = _buf(out)

@@ -502,3 +502,51 @@ def test_gauss_law_2d_with_driver():
     inner = (slice(4, -4), slice(4, -30))
     res = np.linalg.norm((div - rho)[inner]) / np.linalg.norm(rho[inner])
     assert res < 0.02
+
+
+# ---------------------------------------------------------------------------
+# Rest-frame pressures of the WARMC tensor (App. A: P_perp = theta^{phi phi},
+# P_par from the spatial theta and u; here r -> x, phi -> y).  The pin builds
+# theta^{mu nu} independently from Eq. (double-boost): P_perp (U U - eta) +
+# Delta P Lambda_z Lambda_z for a boost in the (z, x) plane, whose rest frame
+# has P_par = P_perp + Delta P along z.
+# ---------------------------------------------------------------------------
+def _boosted_theta(pperp, dP, uz, ux):
+    v = np.array([uz, ux, 0.0])
+    g = 1.0 / np.sqrt(1.0 - v @ v)
+    eta = np.diag([1.0, -1.0, -1.0, -1.0])
+    U = g * np.array([1.0, uz, ux, 0.0])
+    L = np.zeros((4, 4))
+    L[0, 0] = g
+    L[0, 1:] = L[1:, 0] = g * v
+    L[1:, 1:] = np.eye(3) + (g - 1.0) * np.outer(v, v) / (v @ v)
+    Lz = L[:, 1]  # the rest frame's z axis
+    return pperp * (np.outer(U, U) - eta) + dP * np.outer(Lz, Lz)
+
+
+@pytest.mark.parametrize("pperp,dP,uz,ux", [(0.01, 0.003, 0.3, 0.2), (0.02, -0.005, -0.6, 0.4),
+                                            (0.005, 0.0, 0.1, -0.7), (0.03, 0.02, 0.85, 0.05)])
+def test_rest_pressures_invert_the_double_boost(pperp, dP, uz, ux):
+    th = _boosted_theta(pperp, dP, uz, ux)
+    # the construction obeys the mass-shell rows the decode uses
+    u = np.array([uz, ux, 0.0])
+    assert np.allclose(th[0, 1:], th[1:, 1:] @ u, rtol=0, atol=1e-15)
+    ppar, pp = O.rest_pressures(th[1:, 1:], u)
+    assert abs(pp - pperp) <= 1e-15
+    assert abs(ppar - (pperp + dP)) <= 1e-14
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+def test_rest_pressures_at_rest(dim, closure):
+    """An isotropic rest state has P_par = P_perp = theta^{xx} = theta^{zz};
+    the outputs exist for 2D WARMC only (zero elsewhere)."""
+    o = O.Oracle(_cfg(dim, closure))
+    m = o.moments((1 << 10) | (1 << 12) | (1 << 16) | (1 << 17))
+    th_zz, th_yy, ppar, pperp = m
+    if closure == "warmc" and dim == 2:
+        assert th_zz.min() > 0
+        assert np.allclose(pperp, th_yy, rtol=1e-15, atol=0)
+        assert np.allclose(ppar, th_zz, rtol=1e-14, atol=0)
+    else:
+        assert not ppar.any() and not pperp.any()
