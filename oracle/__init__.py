@@ -26,6 +26,7 @@ _lib = None
 
 LEC, WARMC = 0, 1
 OPEN, PERIODIC = 0, 1
+CARTESIAN, AXISYMMETRIC = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -52,6 +53,7 @@ class _Params(ctypes.Structure):
         ("z0", ctypes.c_double), ("profile", ctypes.POINTER(ctypes.c_double)),
         ("profile_len", ctypes.c_int), ("profile_dz", ctypes.c_double),
         ("boundary", ctypes.c_int), ("init_fields", ctypes.c_int),
+        ("geometry", ctypes.c_int),
     ]
 
 
@@ -126,12 +128,19 @@ def _boundary_code(b):
     return int(b)
 
 
+def _geometry_code(g):
+    if isinstance(g, str):
+        return {"cartesian": CARTESIAN, "axisymmetric": AXISYMMETRIC}[g.lower()]
+    return int(g)
+
+
 def make_params(cfg: dict):
     """Build the C parameter struct from a plain configuration dict.
 
     Keys: dim, n (z, x, y), dx, courant, tau, closure ('lec'|'warmc'), dv,
     mu, alpha, sigma_z, sigma_r, z0, profile (array or None), profile_dz,
-    boundary ('open'|'periodic'), init_fields (bool).
+    boundary ('open'|'periodic'), init_fields (bool), geometry
+    ('cartesian'|'axisymmetric'; axisymmetric: dim 2, open, x is r = j dx).
     The returned tuple keeps the profile buffer alive."""
     n = list(cfg["n"]) + [1, 1]
     prof = cfg.get("profile")
@@ -150,6 +159,7 @@ def make_params(cfg: dict):
         profile_dz=float(cfg.get("profile_dz", 0.0)),
         boundary=_boundary_code(cfg.get("boundary", "open")),
         init_fields=int(bool(cfg.get("init_fields", cfg["dim"] >= 2))),
+        geometry=_geometry_code(cfg.get("geometry", "cartesian")),
     )
     return p, prof_arr
 

@@ -39,6 +39,15 @@
  *    decoded quantities (zero on the first step after a state is set).
  *  - App. A spatial derivatives: second-order central differences; at the
  *    open boundary the missing neighbour is the nearest in-domain node.
+ *  - Axisymmetric geometry (Sec. 2.2 end, App. A): the 2D grid is (z, r) with
+ *    node j at r = j dx; j = 0 is the r = 0 boundary node.  After streaming
+ *    it takes the populations of node j = 1: as they are (Eq. open-bc) for
+ *    the sets even under r -> -r, with the mirrored direction (Eq.
+ *    reflective-bc) for the odd ones (n A_r; n lambda u_r, lambda theta^{rz}).
+ *    The 1/r terms of App. A are added to the sources at r > 0 and left out
+ *    at r = 0.  Yee slots as in 2D (E_z at r + dx/2, E_r and B_phi at r);
+ *    on the axis E_r = B_phi = 0, and the E_z slot below the axis mirrors
+ *    the one above it; (curl B)_z = d_r(r B_phi)/r.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -65,6 +74,7 @@ struct orc_state {
   int xi[ORC_MAXQ][3];
   double w[ORC_MAXQ];
   int thpair[6][2];
+  int mir[ORC_MAXQ];  /* velocity mirrored in x (r -> -r) */
   double Arest[11];
   double *f;          /* [K][Q][ncell] populations at time n (after streaming) */
   double *E, *B;      /* [3][ncell]: E at t_{n-1/2}, B at t_n */
@@ -338,6 +348,21 @@ static long index_of(const orc_state* S, const int* i)
 
 static int present(const orc_state* S, int axis) { return axis < S->p.dim; }
 
+static int axi(const orc_state* S) { return S->p.geometry == ORC_AXISYMMETRIC; }
+
+/* Axisymmetric: whether set k changes sign under r -> -r (an odd number of
+ * r indices: n A_r; n lambda u_r and lambda theta^{rz}). */
+static int odd_in_r(const orc_state* S, int k)
+{
+  if (S->p.closure == ORC_LEC) return k == 2;
+  if (k == 3) return 1;
+  if (k >= 2 + S->Ds) {
+    int j = k - 2 - S->Ds;
+    return (S->thpair[j][0] == 1) != (S->thpair[j][1] == 1);
+  }
+  return 0;
+}
+
 /* Node-quantity neighbour (macros, J, B): wrap (periodic) or clamp (open). */
 static long nb_node(const orc_state* S, long c, int axis, int delta)
 {
@@ -388,14 +413,24 @@ static int E_wall(const orc_state* S, long c, int a)
   int i[3]; coords(S, c, i);
   for (int b = 1; b < 3; ++b)
     if (b != a && present(S, b) && i[b] == S->n[b] - 1) return 1;
+  /* axisymmetric: E_r vanishes on the axis (odd under r -> -r) */
+  if (axi(S) && a == 1 && i[1] == 0) return 1;
   return 0;
+}
+
+/* Axisymmetric: B_phi vanishes on the axis. */
+static int B_axis(const orc_state* S, long c, int a)
+{
+  if (!axi(S) || a != 2) return 0;
+  int i[3]; coords(S, c, i);
+  return i[1] == 0;
 }
 
 static void node_pos(const orc_state* S, const int* i, double* pos /* z, x, y */)
 {
   double dx = S->p.dx;
   pos[0] = i[0] * dx;
-  pos[1] = (i[1] - 0.5 * (S->n[1] - 1)) * dx;
+  pos[1] = axi(S) ? i[1] * dx : (i[1] - 0.5 * (S->n[1] - 1)) * dx;
   pos[2] = (i[2] - 0.5 * (S->n[2] - 1)) * dx;
 }
 
@@ -429,6 +464,8 @@ orc_state* orc_create(const orc_params* p, int* status)
   if (!(p->mu >= 0)) return NULL;
   if (p->dim >= 2 && !(p->sigma_r > 0)) return NULL;
   if (!p->profile && !(p->sigma_z > 0)) return NULL;
+  if (p->geometry != ORC_CARTESIAN && p->geometry != ORC_AXISYMMETRIC) return NULL;
+  if (p->geometry == ORC_AXISYMMETRIC && (p->dim != 2 || p->boundary != ORC_OPEN)) return NULL;
 
   orc_state* S = (orc_state*)calloc(1, sizeof(orc_state));
   S->p = *p;
@@ -447,6 +484,9 @@ orc_state* orc_create(const orc_params* p, int* status)
   S->Q = orc_stencil(p->dim, xi, S->w);
   for (int i = 0; i < S->Q; ++i)
     for (int a = 0; a < 3; ++a) S->xi[i][a] = xi[3 * i + a];
+  for (int i = 0; i < S->Q; ++i)
+    for (int j = 0; j < S->Q; ++j)
+      if (S->xi[j][0] == S->xi[i][0] && S->xi[j][1] == -S->xi[i][1] && S->xi[j][2] == S->xi[i][2]) S->mir[i] = j;
   if (p->closure == ORC_LEC) {
     S->K = 1 + S->Ds;
     S->ntheta = 0;
@@ -525,7 +565,15 @@ static void init_fields(orc_state* S)
   for (long c = 0; c < nc; ++c) {
     int i[3]; coords(S, c, i);
     double pos[3]; node_pos(S, i, pos);
-    if (p->dim == 2) {
+    if (p->dim == 2 && axi(S)) {
+      /* E_r = -L sr^2 (1 - exp(-r^2/2sr^2)) / r at the E_r slot (z + dx/2, r),
+       * B_phi = E_r at the node (z, r), t = 0. */
+      double tE = -0.5 * S->dt, r = pos[1];
+      double s = r * r / (2.0 * sr * sr);
+      double fr = s > 0 ? -expm1(-s) / (2.0 * s) : 0.5;
+      S->E[1 * nc + c] = -driver_long(p, pos[0] + 0.5 * dx - p->z0 - tE) * r * fr;
+      S->B[2 * nc + c] = -driver_long(p, pos[0] - p->z0) * r * fr;
+    } else if (p->dim == 2) {
       /* E_x slot: (z + dx/2, x);  B_y at the node. */
       double tE = -0.5 * S->dt;
       double Lx = driver_long(p, pos[0] + 0.5 * dx - p->z0 - tE);
@@ -567,8 +615,10 @@ static void init_fields(orc_state* S)
     }
   }
   for (long c = 0; c < nc; ++c)
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
       if (E_wall(S, c, a)) S->E[(long)a * nc + c] = 0.0;
+      if (B_axis(S, c, a)) S->B[(long)a * nc + c] = 0.0;
+    }
 }
 
 /* Nearest bulk node of c (Eq. open-bc); identity for periodic domains. */
@@ -583,6 +633,16 @@ static long bulk_of(const orc_state* S, long c)
   return index_of(S, i);
 }
 
+/* Velocity whose population a boundary node c takes from its bulk node for
+ * set k: i itself (Eq. open-bc), or on the axis of an axisymmetric domain
+ * the mirrored velocity for sets odd under r -> -r (Eq. reflective-bc). */
+static int boundary_dir(const orc_state* S, long c, int k, int i)
+{
+  if (!axi(S) || !odd_in_r(S, k)) return i;
+  int ic[3]; coords(S, c, ic);
+  return ic[1] == 0 ? S->mir[i] : i;
+}
+
 void orc_set_state(orc_state* S, const double* f, const double* E, const double* B)
 {
   long nc = S->ncell;
@@ -590,8 +650,8 @@ void orc_set_state(orc_state* S, const double* f, const double* E, const double*
     for (int k = 0; k < S->K; ++k)
       for (int i = 0; i < S->Q; ++i)
         for (long c = 0; c < nc; ++c) {
-          size_t base = ((size_t)k * S->Q + i) * nc;
-          S->f[base + c] = f[base + bulk_of(S, c)];
+          size_t src = ((size_t)k * S->Q + boundary_dir(S, c, k, i)) * nc;
+          S->f[((size_t)k * S->Q + i) * nc + c] = f[src + bulk_of(S, c)];
         }
   }
   if (E || B) S->fields_from_driver = 0;
@@ -605,7 +665,7 @@ void orc_set_state(orc_state* S, const double* f, const double* E, const double*
     memcpy(S->B, B, sizeof(double) * 3 * nc);
     for (long c = 0; c < nc; ++c)
       for (int a = 0; a < 3; ++a)
-        if (!B_present(S, a)) S->B[(long)a * nc + c] = 0.0;
+        if (!B_present(S, a) || B_axis(S, c, a)) S->B[(long)a * nc + c] = 0.0;
   }
   S->have_prev = 0;
 }
@@ -672,7 +732,12 @@ static void node_fields(const orc_state* S, long c, double* En, double* Bn)
       for (int q = 0; q < (1 << no); ++q) {
         long cc = c;
         for (int j = 0; j < no && cc >= 0; ++j)
-          if (q & (1 << j)) cc = nb_E(S, cc, off[j], -1);
+          if (q & (1 << j)) {
+            long nb = nb_E(S, cc, off[j], -1);
+            /* axisymmetric: the E_z slot below the axis mirrors the one above */
+            if (nb < 0 && axi(S) && a == 0 && off[j] == 1) nb = cc;
+            cc = nb;
+          }
         s += Eget(S, S->En, a, cc);
       }
       En[a] = s / (double)(1 << no);
@@ -712,7 +777,11 @@ static void forward_stages(orc_state* S)
       int b = (a + 1) % 3, d = (a + 2) % 3;
       /* (curl B)_a = d_b B_d - d_d B_b at the E_a slot */
       double curl = 0.0;
-      if (present(S, b) && B_present(S, d))
+      if (a == 0 && axi(S)) {
+        /* (curl B)_z = (1/r) d_r (r B_phi) at r_{j+1/2}, B_phi at r_j, r_{j+1} */
+        double rl = i[1] * dx, rh = rl + dx, rm = rl + 0.5 * dx;
+        curl += (rh * S->B[(long)d * nc + nb_node(S, c, b, +1)] - rl * S->B[(long)d * nc + c]) / (rm * dx);
+      } else if (present(S, b) && B_present(S, d))
         curl += (S->B[(long)d * nc + nb_node(S, c, b, +1)] - S->B[(long)d * nc + c]) / dx;
       if (present(S, d) && B_present(S, b))
         curl -= (S->B[(long)b * nc + nb_node(S, c, d, +1)] - S->B[(long)b * nc + c]) / dx;
@@ -742,7 +811,7 @@ static void forward_stages(orc_state* S)
   for (long c = 0; c < nc; ++c) {
     for (int a = 0; a < 3; ++a) {
       long ia = (long)a * nc + c;
-      if (!B_present(S, a)) { S->Bn[ia] = 0.0; continue; }
+      if (!B_present(S, a) || B_axis(S, c, a)) { S->Bn[ia] = 0.0; continue; }
       int b = (a + 1) % 3, d = (a + 2) % 3;
       /* (curl E)_a = d_b E_d - d_d E_b at the B_a slot */
       double curl = 0.0;
@@ -798,6 +867,32 @@ static void forward_stages(orc_state* S)
       for (int j = 0; j < S->ntheta; ++j)
         Fk[2 + S->Ds + j] = Fth[S->thpair[j][0] * 3 + S->thpair[j][1]];
     }
+    if (axi(S)) {
+      int ic[3]; coords(S, c, ic);
+      if (ic[1] > 0) {
+        /* App. A: the 1/r terms of the cylindrical divergence (index 1 = r,
+         * 2 = phi, 0 = z; c = 1) */
+        double r = ic[1] * dx, ur = m->u[1];
+        if (p->closure == ORC_LEC) {
+          /* D(n) = -u_r n / r;  D(n A_a) = -u_r (n A_a) / r */
+          double A[3] = {0, 0, 0};
+          for (int k = 0; k < K; ++k)
+            for (int i = 0; i < Q; ++i) A[k] += S->f[((size_t)k * Q + i) * nc + c];
+          for (int k = 0; k < K; ++k) Fk[k] += -ur * A[k] / r;
+        } else {
+          double n = m->n, nl = m->n * m->lam;
+          Fk[0] += -n * ur / r;
+          Fk[1] += -nl * ur / r - m->th0[1] / r;
+          Fk[2] += -nl * m->u[0] * ur / r - m->th[0][1] / r;        /* n lambda u_z */
+          Fk[3] += -nl * ur * ur / r - (m->th[1][1] - m->th[2][2]) / r;  /* n lambda u_r */
+          for (int j = 0; j < S->ntheta; ++j) {
+            int a = S->thpair[j][0], b = S->thpair[j][1];
+            double coef = (a == 2 && b == 2) ? 3.0 : 1.0;  /* lambda theta^{phi phi}: 3 */
+            Fk[2 + S->Ds + j] += -coef * m->lam * m->th[a][b] * ur / r;
+          }
+        }
+      }
+    }
     for (int k = 0; k < K; ++k) S->F[(long)k * nc + c] = Fk[k];
   }
 
@@ -832,17 +927,18 @@ static void finish_step(orc_state* S)
   for (long c = 0; c < nc; ++c) {
     long cb = bulk_of(S, c);
     int ib[3]; coords(S, cb, ib);
-    for (int i = 0; i < Q; ++i) {
-      int src[3] = {ib[0], ib[1], ib[2]};
-      for (int a = 0; a < S->p.dim; ++a) {
-        int v = src[a] - S->xi[i][a], n = S->n[a];
-        if (p->boundary == ORC_PERIODIC) v = ((v % n) + n) % n;
-        src[a] = v;
+    for (int k = 0; k < K; ++k)
+      for (int i = 0; i < Q; ++i) {
+        int ii = boundary_dir(S, c, k, i);
+        int src[3] = {ib[0], ib[1], ib[2]};
+        for (int a = 0; a < S->p.dim; ++a) {
+          int v = src[a] - S->xi[ii][a], n = S->n[a];
+          if (p->boundary == ORC_PERIODIC) v = ((v % n) + n) % n;
+          src[a] = v;
+        }
+        long cs = index_of(S, src);
+        S->f[((size_t)k * Q + i) * nc + c] = S->fs[((size_t)k * Q + ii) * nc + cs];
       }
-      long cs = index_of(S, src);
-      for (int k = 0; k < K; ++k)
-        S->f[((size_t)k * Q + i) * nc + c] = S->fs[((size_t)k * Q + i) * nc + cs];
-    }
   }
 
   /* (6) */
@@ -1411,7 +1507,7 @@ static void adj_init_fields(const orc_state* S, const double* lE, const double* 
 double orc_adjoint_run(orc_state* S, long N, long witness, double* g3, double* gp,
                        double* lf0, double* lE0, double* lB0)
 {
-  if (S->p.dim > 2) return NAN;
+  if (S->p.dim > 2 || axi(S)) return NAN;
   long nc = S->ncell;
   int K = S->K, Q = S->Q;
   size_t fsz = (size_t)K * Q * nc, esz = 3 * (size_t)nc, psz = 7 * (size_t)nc;

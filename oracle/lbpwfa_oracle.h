@@ -19,6 +19,7 @@ extern "C" {
 
 enum { ORC_LEC = 0, ORC_WARMC = 1 };
 enum { ORC_OPEN = 0, ORC_PERIODIC = 1 };
+enum { ORC_CARTESIAN = 0, ORC_AXISYMMETRIC = 1 };
 
 typedef struct {
   int dim;                 /* 1, 2, 3 */
@@ -40,6 +41,9 @@ typedef struct {
   double profile_dz;
   int boundary;            /* ORC_OPEN or ORC_PERIODIC */
   int init_fields;         /* 1: v -> c driver field at t = 0 (2D, 3D) */
+  int geometry;            /* ORC_CARTESIAN, or ORC_AXISYMMETRIC (dim 2, open
+                              boundaries): the x axis is r >= 0, node j at
+                              r = j dx, y is the azimuth phi (Sec. 2.2, App. A) */
 } orc_params;
 
 typedef struct orc_state orc_state;
