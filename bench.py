@@ -43,7 +43,7 @@ WORKLOAD_2D = dict(dim=2, n=(1024, 512), dx=0.05, courant=0.1, tau=0.53, closure
 WORKLOAD_NAME = "2d_lec_1024x512_fp32"
 # step kernel of each lbpwfa_info kernel_variant
 KERNEL_NAMES = {1: "lb_step_kernel", 2: "lb_step_tma2d_kernel", 3: "lb_step_persist2d_kernel",
-                4: "lb_step_march3d_kernel"}
+                4: "lb_step_march3d_kernel", 5: "lb_step_axi_kernel"}
 
 # the 1D configuration (launch-bound, 0.2 MB of state: reported as steps/s)
 CONFIG_1D = dict(dim=1, n=(2048,), dx=40 / 2048, courant=0.5, tau=0.52, closure="lec", dv=1, mu=1e-3,
@@ -56,6 +56,13 @@ CONFIG_3D = dict(dim=3, n=(512, 256, 256), dx=0.05, courant=0.1, tau=0.53, closu
 CONFIG_ADJ = dict(dim=2, n=(512, 256), dx=0.05, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=5e-3,
                   alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=4.0, boundary="open", init_fields=True)
 ADJ_STEPS = 1000
+# the 3D3V axisymmetric configuration of Sec. 6 (Fig. 4): L_z = 30, L_r = 6 at
+# dz = dr = 0.01 (3000 x 600 nodes), dt = 0.001, tau = 0.53, mu = 0.04 (20 keV),
+# sigma_z = sigma_r = 25 um at n_i = 1e16 cm^-3 (0.47 k_p^-1), Q~ = 0.5
+# (alpha = Q~ / ((2 pi)^{3/2} sigma_z sigma_r^2))
+CONFIG_AXI = dict(dim=2, n=(3000, 600), dx=0.01, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=0.04,
+                  alpha=0.5 / ((2 * np.pi) ** 1.5 * 0.47 ** 3), sigma_z=0.47, sigma_r=0.47, z0=4.0,
+                  boundary="open", init_fields=True, geometry="axisymmetric")
 
 
 def _args():
@@ -66,13 +73,15 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
     ap.add_argument("--workload", default="2d_lec",
-                    choices=["2d_lec", "2d_warmc", "3d_warmc", "3d_warmc_128", "adjoint_2d_warmc", "batch_2d"],
+                    choices=["2d_lec", "2d_warmc", "3d_warmc", "3d_warmc_128", "adjoint_2d_warmc", "batch_2d",
+                             "axi_warmc", "axi_lec"],
                     help="2d_lec: 1024 x 512 LEC (default); 2d_warmc: the same grid with the warm-plasma "
                          "closure; 3d_warmc: 512 x 256 x 256 WARMC; "
                          "3d_warmc_128: 128^3 WARMC (small case for profiling); adjoint_2d_warmc: "
                          "forward + reverse sweep of the 512 x 256 WARMC adjoint case over --steps steps "
                          "(whole tape kept), for profiling; batch_2d: the first --batch-runs runs of the batched "
-                         "sweep over --steps steps, for profiling")
+                         "sweep over --steps steps, for profiling; axi_warmc, axi_lec: the 3000 x 600 "
+                         "axisymmetric (z, r) grid of the paper's 3D3V runs")
     ap.add_argument("--batch-runs", type=int, default=64, help="batch_2d: runs of the sweep (1..64)")
     ap.add_argument("--no-tune", action="store_true", help="batch_2d: skip the tile autotuner")
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
@@ -91,7 +100,8 @@ def _args():
 
 def _config_block(cfg, precision, extra=None):
     grid = "x".join(str(v) for v in cfg["n"])
-    d = {"workload": f"{cfg['dim']}d_{cfg['closure']}_{grid}_{precision}",
+    kind = "axi" if cfg.get("geometry") == "axisymmetric" else f"{cfg['dim']}d"
+    d = {"workload": f"{kind}_{cfg['closure']}_{grid}_{precision}",
          "grid": list(cfg["n"]), "dx": cfg["dx"], "courant": cfg["courant"], "tau": cfg["tau"],
          "closure": cfg["closure"], "D": cfg["dv"], "mu": cfg["mu"], "alpha": cfg["alpha"],
          "sigma_z": cfg["sigma_z"], "sigma_r": cfg["sigma_r"], "precision": precision,
@@ -360,7 +370,8 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     lb.load_library()
     cfg = {"2d_lec": WORKLOAD_2D, "2d_warmc": dict(WORKLOAD_2D, closure="warmc"), "3d_warmc": CONFIG_3D,
-           "3d_warmc_128": dict(CONFIG_3D, n=(128, 128, 128), z0=2.0)}[a.workload]
+           "3d_warmc_128": dict(CONFIG_3D, n=(128, 128, 128), z0=2.0), "axi_warmc": CONFIG_AXI,
+           "axi_lec": dict(CONFIG_AXI, closure="lec")}[a.workload]
     cfg = dict(cfg)
     stream = torch.cuda.Stream(device=dev)
     flush = (torch.empty(256 << 20, dtype=torch.uint8, device=dev),
@@ -527,6 +538,20 @@ def _configs(stream, flush, hbm):
                          "warmc": [round(v, 4) for v in info.tuned_ms[1] if v > 0]},
             "graph_steps": info.graph_steps, "steps": 96, "kernel": "lb_step_batch_kernel",
             "l2": "state larger than L2 (no flush)"}
+    # the axisymmetric 3D3V grid, both closures
+    for closure in ("warmc", "lec"):
+        for prec in ("fp32", "fp64"):
+            c = dict(CONFIG_AXI, closure=closure)
+            with lb.Run(c, prec, stream=stream.cuda_stream) as run:
+                info = run.info()
+                times = _time_steps(run, stream, 100 if prec == "fp64" else 300, 5, flush)
+            mean = sum(times) / len(times)
+            gbs = info.bytes_per_update * info.ncell / (mean * 1e-3) / 1e9
+            res[f"axi_{closure}_{prec}_3000x600"] = {
+                "mlups": round(info.ncell / (mean * 1e-3) / 1e6, 2), "ms_per_step": round(mean, 4),
+                "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
+                "bytes_per_update": info.bytes_per_update, "steps": len(times),
+                "kernel": KERNEL_NAMES[info.kernel_variant], "geometry": "axisymmetric (z, r)"}
     for prec in ("fp32", "fp64"):
         try:
             with lb.Run(CONFIG_3D, prec, stream=stream.cuda_stream) as run:

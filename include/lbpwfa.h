@@ -68,6 +68,7 @@ typedef enum {
 enum { LBPWFA_LEC = 0, LBPWFA_WARMC = 1 };
 enum { LBPWFA_FP64 = 0, LBPWFA_FP32 = 1, LBPWFA_FP16S = 2 };
 enum { LBPWFA_OPEN = 0, LBPWFA_PERIODIC = 1 };
+enum { LBPWFA_CARTESIAN = 0, LBPWFA_AXISYMMETRIC = 1 };
 
 /* Problem statement (Sec. 6, Eq. bunch-density and Qtilde). */
 typedef struct {
@@ -118,7 +119,24 @@ typedef struct {
                               32 x 8 nodes marching up chunks of 32 planes,
                               each plane decoded once per column (the
                               automatic 3D choice; 1 gives 32 x 4 x 4 tiles).
-                              All compute the same step. */
+                              All compute the same step.  Axisymmetric runs
+                              take 0 or 1 and always run the plain kernel
+                              with the axis rules (reported as 5). */
+  int geometry;            /* LBPWFA_CARTESIAN, or LBPWFA_AXISYMMETRIC: the
+                              3D3V axisymmetric (z, r) geometry of Sec. 2.2
+                              and App. A on a 2D grid (dim 2, open
+                              boundaries); x is r, node j at r = j dx, and
+                              j = 0 is the r = 0 boundary node, which takes
+                              the populations of node 1 as they are (Eq.
+                              open-bc) for the sets even under r -> -r and
+                              with the mirrored velocity (Eq. reflective-bc)
+                              for the odd ones (n A_r; n lambda u_r,
+                              lambda theta^{rz}).  Fields: E_z, E_r, B_phi
+                              in the slots of E_z, E_x, B_y; E_r = B_phi = 0
+                              on the axis; (curl B)_z = d_r(r B_phi)/r.  The
+                              1/r terms of App. A are added to the sources
+                              at r > 0.  Not available for batches or the
+                              adjoint (LBPWFA_ERR_INVALID). */
 } lbpwfa_params;
 
 typedef struct {

@@ -112,8 +112,8 @@ using namespace lbprt;
 
 extern "C" int lbpwfa_record(lbpwfa_t h, const lbpwfa_record_params* rp) {
   if (!h || !rp) return LBPWFA_ERR_INVALID;
-  if (h->in_batch || h->prm.dim > 2 || h->prm.precision == LBPWFA_FP16S) {
-    h->err = "lbpwfa_record: the adjoint covers single 1D/2D runs with FP64 or FP32 storage";
+  if (h->in_batch || h->prm.dim > 2 || h->prm.precision == LBPWFA_FP16S || h->prm.geometry != LBPWFA_CARTESIAN) {
+    h->err = "lbpwfa_record: the adjoint covers single Cartesian 1D/2D runs with FP64 or FP32 storage";
     return LBPWFA_ERR_INVALID;
   }
   if (rp->max_steps < 1 || rp->checkpoint_every < 0) return LBPWFA_ERR_INVALID;

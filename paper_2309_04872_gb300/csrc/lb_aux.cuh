@@ -21,6 +21,7 @@ struct AuxParams {
   const double* profile; int plen; double pdz;
   double xoff, yoff;
   double t;          // time of the stored populations
+  int axi;           // 2D axisymmetric (z, r): x is r = j dx, xoff = 0
 };
 
 __device__ __forceinline__ void unflatten(const AuxParams& A, long long c, int* e) {
@@ -78,7 +79,13 @@ __global__ void init_fields_kernel(AuxParams A, real* E, real* B, real* Elo, rea
   const double z = e[0] * dx, x = (e[1] - A.xoff) * dx, y = (e[2] - A.yoff) * dx;
   const double tE = -0.5 * A.dt;
   double Ev[3] = {0, 0, 0}, Bv[3] = {0, 0, 0};
-  if (DIM == 2) {
+  if (DIM == 2 && A.axi) {
+    // E_r = -L sr^2 (1 - exp(-r^2/2sr^2)) / r at the E_r slot (z + dx/2, r),
+    // B_phi = E_r at the node; both 0 on the axis
+    const double k = x * radial_factor(x * x, sr);
+    Ev[1] = -driver_long_d(A, z + 0.5 * dx - A.z0 - tE) * k;
+    Bv[2] = -driver_long_d(A, z - A.z0) * k;
+  } else if (DIM == 2) {
     const double k = sr * sqrt(M_PI / 2.0) * erf(x / (sqrt(2.0) * sr));
     Ev[1] = -driver_long_d(A, z + 0.5 * dx - A.z0 - tE) * k;   // E_x slot: z + dx/2
     Bv[2] = -driver_long_d(A, z - A.z0) * k;                   // B_y at the node
@@ -149,7 +156,9 @@ __global__ void import_pops_kernel(AuxParams A, const double* fin, typename Prec
   }
 }
 
-// Export f^n (FP64 [K][Q][ncell]) by pulling the stored post-collision values.
+// Export f^n (FP64 [K][Q][ncell]) by pulling the stored post-collision values
+// (on the axis of a (z, r) grid the odd sets take the mirrored velocity, as
+// the step's pull does).
 template <int DIM, int CL, int PR>
 __global__ void export_pops_kernel(AuxParams A, const typename Prec<PR>::store* fs, double* out) {
   using L = Lattice<DIM>;
@@ -162,8 +171,12 @@ __global__ void export_pops_kernel(AuxParams A, const typename Prec<PR>::store* 
   if (!A.periodic)
     for (int a = 0; a < DIM; ++a) b[a] = min(max(e[a], 1), A.n[a] - 2);
   for (int k = 0; k < M::K; ++k) {
+    bool mirror = false;
+    if constexpr (DIM == 2) mirror = A.axi && e[1] == 0 && odd_in_r<CL>(k);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
+    for (int j = 0; j < L::Q; ++j) {
+      // D2Q9 with x reversed: 3 <-> 4, 5 <-> 7, 6 <-> 8
+      const int i = !mirror ? j : (j == 3 ? 4 : j == 4 ? 3 : j == 5 ? 7 : j == 7 ? 5 : j == 6 ? 8 : j == 8 ? 6 : j);
       int s[3] = {b[0], b[1], b[2]};
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
@@ -175,7 +188,7 @@ __global__ void export_pops_kernel(AuxParams A, const typename Prec<PR>::store* 
           i == 0 ? (double)Codec<PR>::load0(fs + (long long)k * L::Q * A.plane, ps,
                                             fs + ((long long)M::K * L::Q + k) * A.plane, ps, A.inv_scale[k])
                  : (double)Codec<PR>::load(fs + ((long long)k * L::Q + i) * A.plane, ps, A.inv_scale[k]);
-      out[((long long)k * L::Q + i) * A.ncell + c] = L::w(i) * A.Arest[k] + dv;
+      out[((long long)k * L::Q + j) * A.ncell + c] = L::w(i) * A.Arest[k] + dv;
     }
   }
 }
@@ -310,9 +323,11 @@ __global__ void import_fields_kernel(AuxParams A, const double* Ein, const doubl
       const int b = (a + 1) % 3, d = (a + 2) % 3;
       bool wall = !A.periodic &&
                   ((b >= 1 && b < DIM && e[b] == A.n[b] - 1) || (d >= 1 && d < DIM && e[d] == A.n[d] - 1));
+      if (A.axi && a == 1 && e[1] == 0) wall = true;  // E_r on the axis
       put_field(E, Elo, a * A.plane + p, (e_present<DIM>(a) && !wall) ? Ein[a * A.ncell + c] : 0.0);
     }
-    if (Bin) put_field(B, Blo, a * A.plane + p, b_present<DIM>(a) ? Bin[a * A.ncell + c] : 0.0);
+    const bool axis_b = A.axi && a == 2 && e[1] == 0;  // B_phi on the axis
+    if (Bin) put_field(B, Blo, a * A.plane + p, (b_present<DIM>(a) && !axis_b) ? Bin[a * A.ncell + c] : 0.0);
   }
 }
 

@@ -36,6 +36,11 @@ struct KernelSet {
   size_t tma_smem;
   cudaError_t (*prepare_tma)();
   void (*step_tma)(const StepParams&, const void* tensor_map, dim3 grid, cudaStream_t);
+  // 2D axisymmetric (z, r) step on the plain kernel's tile; has_axi == false
+  // outside 2D
+  bool has_axi;
+  cudaError_t (*prepare_axi)();
+  void (*step_axi)(const StepParams&, dim3 grid, cudaStream_t);
   // 3D step marching columns of march_tz x march_tx nodes up chunks of
   // march_yc planes; has_march == false outside 3D
   bool has_march;

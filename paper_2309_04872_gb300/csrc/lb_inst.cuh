@@ -79,6 +79,16 @@ struct Impl {
   static void reduce_partial(const AuxParams& A, const void* src, double* partial, int nblk, cudaStream_t s) {
     reduce_partial_kernel<DIM, CL, PR><<<nblk, 256, 0, s>>>(A, (const store*)src, partial);
   }
+  static constexpr bool kAxi = DIM == 2;
+  static cudaError_t prepare_axi() {
+    if constexpr (kAxi)
+      return cudaFuncSetAttribute(lb_step_axi_kernel<CL, PR, T::TZ, T::TX>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes_gkeep);
+    return cudaErrorNotSupported;
+  }
+  static void step_axi(const StepParams& P, dim3 grid, cudaStream_t s) {
+    if constexpr (kAxi) lb_step_axi_kernel<CL, PR, T::TZ, T::TX><<<grid, Cfg::NT, Cfg::smem_bytes_gkeep, s>>>(P);
+  }
   using TC = TmaCfg2D<CL, PR>;
   static constexpr bool kTma = DIM == 2 && TC::enabled;
   static cudaError_t prepare_tma() {
@@ -106,6 +116,9 @@ struct Impl {
           P, *reinterpret_cast<const CUtensorMap*>(map), ntz, ntiles);
   }
   static void fill(KernelSet* ks) {
+    ks->has_axi = kAxi;
+    ks->prepare_axi = &prepare_axi;
+    ks->step_axi = &step_axi;
     ks->has_march = kMarch;
     ks->march_tz = March3D::TZ;
     ks->march_tx = March3D::TX;

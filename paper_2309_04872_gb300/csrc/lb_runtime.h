@@ -52,6 +52,7 @@ struct lbpwfa_s {
   bool use_tma = false;
   bool use_persist = false;
   bool use_march = false;  // 3D marching columns
+  bool use_axi = false;    // 2D axisymmetric (z, r) kernel
   bool in_batch = false;  // owned by a batch: stepped only through lbpwfa_batch_step
   int num_sms = 0;
   alignas(64) CUtensorMap maps[2];

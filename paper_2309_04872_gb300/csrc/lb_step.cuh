@@ -92,13 +92,33 @@ struct StepCfg {
   __host__ __device__ static constexpr int stride(int a) { return a == 0 ? 1 : (a == 1 ? RZ : RZ * RX); }
 };
 
+// Axisymmetric (z, r) grids: whether set k changes sign under r -> -r (an odd
+// number of r indices: n A_r; n lambda u_r and lambda theta^{rz}).
+template <int CL>
+__host__ __device__ constexpr bool odd_in_r(int k) {
+  if constexpr (CL == CL_LEC) {
+    return k == 2;
+  } else {
+    using M = Model<2, CL>;
+    if (k == 3) return true;
+    if (k >= 4) return (M::tha(k - 4) == 1) != (M::thb(k - 4) == 1);
+    return false;
+  }
+}
+
 // Deviations of the pulled populations f^n_ki - w_i A_rest,k at node
 // (z, x, y) (already inside the domain), straight from global memory.
-template <int DIM, int CL, int PR, bool EDGE>
+// AXI: (z, r) grid whose x = 0 row is the r = 0 boundary node; it takes the
+// pulled populations of its bulk node as they are (Eq. open-bc) for the
+// sets even under r -> -r and with the mirrored velocity (Eq. reflective-bc)
+// for the odd ones.
+template <int DIM, int CL, int PR, bool EDGE, bool AXI = false>
 __device__ __forceinline__ void pulled_dev(const StepParams& P, int z, int x, int y, int k,
                                            typename Prec<PR>::real* df) {
   using L = Lattice<DIM>;
   using store = typename Prec<PR>::store;
+  static_assert(!AXI || DIM == 2, "axisymmetric grids are (z, r)");
+  const bool mirror = AXI && EDGE && x == 0 && odd_in_r<CL>(k);
   if (EDGE && !P.periodic) {
     z = min(max(z, 1), P.n[0] - 2);
     if (DIM >= 2) x = min(max(x, 1), P.n[1] - 2);
@@ -124,11 +144,20 @@ __device__ __forceinline__ void pulled_dev(const StepParams& P, int z, int x, in
       df[i] = Codec<PR>::load(f, i * pl + cell_index32(P, sz, sx, sy), is);
     }
   }
+  if constexpr (AXI) {
+    if (mirror) {
+      // D2Q9 order (0, +z, -z, +x, -x, +z+x, -z-x, +z-x, -z+x): x reversed
+      typename Prec<PR>::real t;
+      t = df[3]; df[3] = df[4]; df[4] = t;
+      t = df[5]; df[5] = df[7]; df[7] = t;
+      t = df[6]; df[6] = df[8]; df[8] = t;
+    }
+  }
 }
 
 // Population source reading the stored post-collision array in global memory
 // (any boundary rule).
-template <int DIM, int CL, int PR, bool SHARED_KEEP = false>
+template <int DIM, int CL, int PR, bool SHARED_KEEP = false, bool AXI = false>
 struct GlobalPull {
   // the step keeps the own node's populations in shared memory for the
   // collision (sets too wide for registers) instead of pulling them again
@@ -136,7 +165,7 @@ struct GlobalPull {
   const StepParams& P;
   template <bool EDGE>
   __device__ __forceinline__ void get(int z, int x, int y, int k, typename Prec<PR>::real* df) const {
-    pulled_dev<DIM, CL, PR, EDGE>(P, z, x, y, k, df);
+    pulled_dev<DIM, CL, PR, EDGE, AXI>(P, z, x, y, k, df);
   }
 };
 
@@ -342,7 +371,10 @@ __device__ __forceinline__ real driver_at(const StepParams& P, const StepConst<r
 
 // E_a^{n+1/2} at the slot of node e (region index r): dual-grid curl of B^n,
 // n u_a averaged over the nodes around the slot, driver current for a = z.
-template <int DIM, int CL, int PR, int TZ, int TX, int TY, bool EDGE>
+// AXI: (z, r) grid with node j at r = j dx: E_r vanishes on the axis and
+// (curl B)_z = (1/r) d_r (r B_phi) at r_{j+1/2}, which is the Cartesian
+// difference plus (B_{j+1} + B_j) / ((2j + 1) dx).
+template <int DIM, int CL, int PR, int TZ, int TX, int TY, bool EDGE, bool AXI = false>
 __device__ __forceinline__ void e_slot(const StepParams& P, const StepConst<typename Prec<PR>::real>& S,
                                        const typename Prec<PR>::real* smac, typename Prec<PR>::real* sE,
                                        const typename Prec<PR>::real* sdrv, int oz, int ox, int oy,
@@ -361,6 +393,7 @@ __device__ __forceinline__ void e_slot(const StepParams& P, const StepConst<type
       bool wall = false;
       if (b >= 1 && axis_present<DIM>(b) && e[b] == P.n[b] - 1) wall = true;
       if (d >= 1 && axis_present<DIM>(d) && e[d] == P.n[d] - 1) wall = true;
+      if (AXI && a == 1 && e1 == 0) wall = true;
       if (wall) {
         sE[a * NR + r] = real(0);
         if (C::CF) sE[(C::NEC + a) * NR + r] = real(0);
@@ -372,6 +405,10 @@ __device__ __forceinline__ void e_slot(const StepParams& P, const StepConst<type
       curl += diff2(F.Bp[d][b], F.Bp_lo[d][b], F.Bc[d], F.Bc_lo[d]) * S.idx;
     if (axis_present<DIM>(d) && b_present<DIM>(b))
       curl -= diff2(F.Bp[b][d], F.Bp_lo[b][d], F.Bc[b], F.Bc_lo[b]) * S.idx;
+    if constexpr (AXI) {
+      if (a == 0)
+        curl += ((F.Bp[2][1] + F.Bp_lo[2][1]) + (F.Bc[2] + F.Bc_lo[2])) * (S.idx / real(2 * e1 + 1));
+    }
     real J = 0;
     if (a < DIM) {
       const bool ob = axis_present<DIM>(b), od = axis_present<DIM>(d);
@@ -478,12 +515,18 @@ struct NoHook {
 // ry = 0 (it was the previous plane's own and low-face slots).  A node's
 // values are moved and decoded by the same thread, so phase A needs no
 // extra barrier.
+// AXI (2D): the (z, r) grid of App. A, node j at r = j dx with j = 0 the
+// r = 0 boundary node (see pulled_dev, e_slot): B_phi stays 0 on the axis,
+// the E_z slot below the axis mirrors the one above it, and the 1/r terms
+// of App. A join the sources at r > 0 (left out on the axis, where they
+// are singular).
 template <int DIM, int CL, int PR, int TZ, int TX, int TY, bool EDGE, class Pull, class Hook = NoHook,
-          bool MARCH = false>
+          bool MARCH = false, bool AXI = false>
 __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* smem, const Pull& pull,
                                           FieldPF<typename Prec<PR>::real>& F, int tile_z, int tile_x,
                                           int tile_y, const Hook& after_decode = Hook(), bool first_plane = true) {
   static_assert(!MARCH || (DIM == 3 && TY == 1), "marching walks one-plane 3D tiles");
+  static_assert(!AXI || DIM == 2, "axisymmetric grids are (z, r)");
   using C = StepCfg<DIM, CL, PR, TZ, TX, TY>;
   using M = Model<DIM, CL>;
   using L = Lattice<DIM>;
@@ -493,7 +536,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   constexpr int K = M::K, Q = L::Q;
   constexpr bool KEEP = K * Q <= 32;  // own node's pulled populations stay in registers
   // ... or, for global pulls of wider sets, in shared memory
-  constexpr bool SKEEP = C::SKEEP_OK && std::is_same<Pull, GlobalPull<DIM, CL, PR, true>>::value;
+  constexpr bool SKEEP = C::SKEEP_OK && (std::is_same<Pull, GlobalPull<DIM, CL, PR, true>>::value ||
+                                         std::is_same<Pull, GlobalPull<DIM, CL, PR, true, true>>::value);
 
   const StepConst<real>& S = consts<real>(P);
   real* smac = reinterpret_cast<real*>(smem);  // [NM][NR]
@@ -647,7 +691,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   if constexpr (!EarlyFields<DIM>::value) {
     if (own_inside) load_fields<DIM, real, EDGE>(P, gz, gx, gy, cell_index32(P, gz, gx, gy), F);
   }
-  if (own_inside) e_slot<DIM, CL, PR, TZ, TX, TY, EDGE>(P, S, smac, sE, sdrv, oz, ox, oy, r_own, gz, gx, gy, F);
+  if (own_inside) e_slot<DIM, CL, PR, TZ, TX, TY, EDGE, AXI>(P, S, smac, sE, sdrv, oz, ox, oy, r_own, gz, gx, gy, F);
   {
     // low-side halo slots: region cells with rz = 0 (or rx = 0, ry = 0) in
     // [0, TZ] x [0, TX] x [0, TY]
@@ -674,7 +718,9 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
           if (DIM >= 2) e1 = wrap_or_clamp(e1, P.n[1], 1);
           if (DIM >= 3) e2 = wrap_or_clamp(e2, P.n[2], 1);
         } else {
-          // transverse ghost: conducting wall; z ghost: the nearest slot
+          // transverse ghost: conducting wall; z ghost: the nearest slot;
+          // below the axis (AXI): the mirror image of the slot above it
+          if (AXI && e1 < 0) { r_eff += RZ; e1 = 0; }
           const bool trans_out = (DIM >= 2 && (e1 < 0 || e1 >= P.n[1])) || (DIM >= 3 && (e2 < 0 || e2 >= P.n[2]));
           if (trans_out) {
 #pragma unroll
@@ -685,7 +731,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
               }
             continue;
           }
-          if (e0 < 0) { r_eff = r + 1; e0 = 0; }
+          if (e0 < 0) { r_eff += 1; e0 = 0; }
           if (e0 >= P.n[0]) continue;  // never read
         }
       }
@@ -697,13 +743,15 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       } else {
         load_fields<DIM, real, EDGE>(P, e0, e1, e2, id, G);
       }
-      e_slot<DIM, CL, PR, TZ, TX, TY, EDGE>(P, S, smac, sE, sdrv, oz, ox, oy, r_eff, e0, e1, e2, G);
+      e_slot<DIM, CL, PR, TZ, TX, TY, EDGE, AXI>(P, S, smac, sE, sdrv, oz, ox, oy, r_eff, e0, e1, e2, G);
       if (r_eff != r) {
 #pragma unroll
         for (int a = 0; a < 3; ++a)
           if (e_present<DIM>(a)) {
-            sE[a * NR + r] = sE[a * NR + r_eff];
-            if (C::CF) sE[(C::NEC + a) * NR + r] = sE[(C::NEC + a) * NR + r_eff];
+            // below the axis E_r (never read there) is zero
+            const bool zero = AXI && a == 1 && r_eff - r >= RZ;
+            sE[a * NR + r] = zero ? real(0) : sE[a * NR + r_eff];
+            if (C::CF) sE[(C::NEC + a) * NR + r] = zero ? real(0) : sE[(C::NEC + a) * NR + r_eff];
           }
       }
     }
@@ -753,7 +801,11 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       real curl = 0;
       if (axis_present<DIM>(b) && e_present<DIM>(d)) curl += Ed(d, r, r - C::stride(b)) * S.idx;
       if (axis_present<DIM>(d) && e_present<DIM>(b)) curl -= Ed(b, r, r - C::stride(d)) * S.idx;
-      if constexpr (C::CF) {
+      if (AXI && gx == 0) {
+        // B_phi vanishes on the axis
+        gst(Bout + a * pl + id, real(0));
+        if constexpr (C::CF) gst(Bout_lo + a * pl + id, real(0));
+      } else if constexpr (C::CF) {
         real hi = F.Bc[a], lo = F.Bc_lo[a];
         two_float_add(hi, lo, -(dt * curl));
         gst(Bout + a * pl + id, hi);
@@ -868,6 +920,26 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
     }
   };
 
+  // AXI: the 1/r terms of the cylindrical divergence of App. A (r = x,
+  // phi = y, c = 1), written with the set's advected value A_k: -A_k u_r / r
+  // for every set (3 A_k u_r / r for lambda theta^{phi phi}), plus
+  // theta^{0r} / r (n lambda), theta^{rz} / r (n lambda u_z) and
+  // (theta^{rr} - theta^{phi phi}) / r (n lambda u_r); zero on the axis.
+  real ir = 0;
+  if constexpr (AXI) ir = gx > 0 ? S.idx / real(gx) : real(0);
+  auto geo = [&](int k, real A) -> real {
+    if constexpr (CL == CL_LEC) {
+      return -u[1] * A * ir;
+    } else {
+      real cf = real(1), extra = real(0);
+      if (k == 1) extra = th0[1];
+      else if (k == 2) extra = th[0][1];
+      else if (k == 3) extra = th[1][1] - th[2][2];
+      else if (k >= 2 + DIM && M::tha(k - 2 - DIM) == 2 && M::thb(k - 2 - DIM) == 2) cf = real(3);
+      return -(cf * A * u[1] + extra) * ir;
+    }
+  };
+
   // ---------------- collide + store (deviation form) ----------------------
   // f* - w A_rest = df (1 - 1/tau) + (f^eq - w A_rest)/tau + w dt F, with
   // f^eq - w A_rest = w (dA + A P_i), P_i = 3 cu + 9/2 cu^2 - 3/2 u^2 split
@@ -903,7 +975,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       dA = set_moment<Q>(df);
     }
     const real A = Arest_k + dA;
-    const real dtF = dtF_of();
+    real dtF = dtF_of();
+    if constexpr (AXI) dtF += dt * geo(k, A);
     store* fk = fout + (size_t)k * Q * (size_t)P.plane;
     real moved = 0;
 #pragma unroll
@@ -998,6 +1071,25 @@ lb_step_kernel(const __grid_constant__ StepParams P) {
   } else {
     if constexpr (EarlyFields<DIM>::value) prefetch_own<DIM, real, true, TZ, TX, TY>(P, F, bz, bx, by);
     step_body<DIM, CL, PR, TZ, TX, TY, true>(P, smem_raw, pull, F, bz, bx, by);
+  }
+}
+
+// Axisymmetric (z, r) step: the plain 2D kernel with the AXI rules of
+// step_body (r = 0 boundary node, cylindrical curl and 1/r sources).
+template <int CL, int PR, int TZ, int TX>
+__global__ void __launch_bounds__(TZ* TX) lb_step_axi_kernel(const __grid_constant__ StepParams P) {
+  using real = typename Prec<PR>::real;
+  using Pull = GlobalPull<2, CL, PR, StepCfg<2, CL, PR, TZ, TX, 1>::SKEEP_OK, true>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Pull pull{P};
+  FieldPF<real> F;
+  const int bz = blockIdx.x, bx = blockIdx.y;
+  if (tile_is_bulk<2, TZ, TX, 1>(P, bz, bx, 0)) {
+    prefetch_own<2, real, false, TZ, TX, 1>(P, F, bz, bx, 0);
+    step_body<2, CL, PR, TZ, TX, 1, false, Pull, NoHook, false, true>(P, smem_raw, pull, F, bz, bx, 0);
+  } else {
+    prefetch_own<2, real, true, TZ, TX, 1>(P, F, bz, bx, 0);
+    step_body<2, CL, PR, TZ, TX, 1, true, Pull, NoHook, false, true>(P, smem_raw, pull, F, bz, bx, 0);
   }
 }
 

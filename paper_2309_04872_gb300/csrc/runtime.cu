@@ -90,6 +90,11 @@ int validate(const lbpwfa_params* p) {
   if (p->precision < LBPWFA_FP64 || p->precision > LBPWFA_FP16S) return LBPWFA_ERR_INVALID;
   if (p->boundary != LBPWFA_OPEN && p->boundary != LBPWFA_PERIODIC) return LBPWFA_ERR_INVALID;
   if (p->kernel_variant < 0 || p->kernel_variant > 4) return LBPWFA_ERR_INVALID;
+  if (p->geometry != LBPWFA_CARTESIAN && p->geometry != LBPWFA_AXISYMMETRIC) return LBPWFA_ERR_INVALID;
+  // axisymmetric (z, r): 2D, open boundaries, the plain kernel's tile
+  if (p->geometry == LBPWFA_AXISYMMETRIC &&
+      (p->dim != 2 || p->boundary != LBPWFA_OPEN || p->kernel_variant > 1))
+    return LBPWFA_ERR_INVALID;
   long long cells = 1;
   for (int a = 0; a < p->dim; ++a) cells *= p->n[a];
   if (cells > (1LL << 34)) return LBPWFA_ERR_INVALID;
@@ -120,7 +125,8 @@ AuxParams aux_params(const lbpwfa_s* h) {
   A.profile = h->profile_d;
   A.plen = (int)h->profile_h.size();
   A.pdz = h->prm.profile_dz;
-  A.xoff = 0.5 * (h->n[1] - 1);
+  A.axi = h->use_axi ? 1 : 0;
+  A.xoff = h->use_axi ? 0.0 : 0.5 * (h->n[1] - 1);  // axisymmetric: node j at r = j dx
   A.yoff = 0.5 * (h->n[2] - 1);
   A.t = h->step * h->dt;
   return A;
@@ -149,7 +155,7 @@ void fill_consts(const lbpwfa_s* h, StepConst<real>& c) {
   c.alpha = (real)h->prm.alpha;
   c.inv2sz2 = (real)(h->prm.sigma_z > 0 ? 1.0 / (2.0 * h->prm.sigma_z * h->prm.sigma_z) : 0.0);
   c.inv2sr2 = (real)(h->prm.sigma_r > 0 ? 1.0 / (2.0 * h->prm.sigma_r * h->prm.sigma_r) : 0.0);
-  c.xoff = (real)(0.5 * (h->n[1] - 1));
+  c.xoff = (real)(h->use_axi ? 0.0 : 0.5 * (h->n[1] - 1));
   c.yoff = (real)(0.5 * (h->n[2] - 1));
   c.pdz_inv = (real)(h->prm.profile_dz > 0 ? 1.0 / h->prm.profile_dz : 0.0);
   c.phalf = (real)(0.5 * ((double)h->profile_h.size() - 1.0));
@@ -297,7 +303,9 @@ int launch_step(lbpwfa_s* h, void* tape) {
                                : step_grid(h);
   StepParams P = step_params(h);
   P.tape = tape;
-  if (h->use_march) {
+  if (h->use_axi) {
+    h->ks.step_axi(P, grid, h->stream);
+  } else if (h->use_march) {
     const dim3 mg((unsigned)((h->n[0] + h->ks.march_tz - 1) / h->ks.march_tz),
                   (unsigned)((h->n[1] + h->ks.march_tx - 1) / h->ks.march_tx),
                   (unsigned)((h->n[2] + h->ks.march_yc - 1) / h->ks.march_yc));
@@ -444,13 +452,19 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
   }
+  // axisymmetric (z, r) grids: the plain kernel with the axis rules
+  h->use_axi = p->geometry == LBPWFA_AXISYMMETRIC;
+  if (h->use_axi) {
+    cudaError_t e = h->ks.has_axi ? h->ks.prepare_axi() : cudaErrorNotSupported;
+    if (e != cudaSuccess) { fail_cuda(h, e, "cudaFuncSetAttribute"); lbpwfa_destroy(h); return LBPWFA_ERR_CUDA; }
+  }
   // 3D: marching columns unless the tiled kernel is asked for (variant 1)
   h->use_march = dim == 3 && (p->kernel_variant == 0 || p->kernel_variant == 4) && h->ks.has_march;
   if (h->use_march && h->ks.prepare_march() != cudaSuccess) {
     cudaGetLastError();
     h->use_march = false;
   }
-  const bool tma_ok = dim == 2 && p->boundary == LBPWFA_OPEN;
+  const bool tma_ok = dim == 2 && p->boundary == LBPWFA_OPEN && !h->use_axi;
   // automatic choice for LEC: the persistent refilling CTAs where the tile
   // table marks them faster, else one TMA box per CTA; WARMC's 72-plane box
   // leaves two CTAs per SM and the global-memory pull is faster there
@@ -680,7 +694,7 @@ int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info) {
   // FP32 fields: high and low parts
   const double field_words = (ne + nbf) * (h->real_sz == 4 ? 2.0 : 1.0);
   info->bytes_per_update = 2.0 * h->NPL * h->store_sz + 2.0 * (field_words + h->NPREV) * h->real_sz;
-  info->kernel_variant = h->use_march ? 4 : (h->use_persist ? 3 : (h->use_tma ? 2 : 1));
+  info->kernel_variant = h->use_axi ? 5 : (h->use_march ? 4 : (h->use_persist ? 3 : (h->use_tma ? 2 : 1)));
   return LBPWFA_OK;
 }
 
@@ -711,7 +725,8 @@ struct CkptHeader {
   char magic[8];
   int32_t version;
   int32_t dim, n0, n1, n2, closure, dv, precision, boundary, K, Q, have_prev;
-  int32_t from_driver, pad_;  // E, B still the driver's initial fields
+  int32_t from_driver;  // E, B still the driver's initial fields
+  int32_t geometry;     // LBPWFA_CARTESIAN (0 in files written before it existed) or AXISYMMETRIC
   int64_t step;
   double dx, courant, tau, mu, alpha, sigma_z, sigma_r, z0;
   uint64_t pop_bytes, fld_bytes, prev_bytes;
@@ -727,6 +742,7 @@ int lbpwfa_save(lbpwfa_t h, const char* path) {
   H.closure = h->prm.closure; H.dv = h->prm.dv; H.precision = h->prm.precision; H.boundary = h->prm.boundary;
   H.K = h->K; H.Q = h->Q; H.have_prev = h->have_prev; H.step = h->step;
   H.from_driver = h->fields_from_driver ? 1 : 0;
+  H.geometry = h->prm.geometry;
   H.dx = h->prm.dx; H.courant = h->prm.courant; H.tau = h->prm.tau; H.mu = h->prm.mu;
   H.alpha = h->prm.alpha; H.sigma_z = h->prm.sigma_z; H.sigma_r = h->prm.sigma_r; H.z0 = h->prm.z0;
   H.pop_bytes = h->f[h->cur].bytes; H.fld_bytes = h->E[h->cur].bytes; H.prev_bytes = h->prev.bytes;
@@ -761,7 +777,7 @@ int lbpwfa_load(lbpwfa_t h, const char* path) {
   }
   const bool match = H.dim == h->prm.dim && H.n0 == h->n[0] && H.n1 == h->n[1] && H.n2 == h->n[2] &&
                      H.closure == h->prm.closure && H.dv == h->prm.dv && H.precision == h->prm.precision &&
-                     H.boundary == h->prm.boundary && H.K == h->K && H.Q == h->Q &&
+                     H.boundary == h->prm.boundary && H.geometry == h->prm.geometry && H.K == h->K && H.Q == h->Q &&
                      H.pop_bytes == h->f[0].bytes && H.fld_bytes == h->E[0].bytes && H.prev_bytes == h->prev.bytes &&
                      H.dx == h->prm.dx && H.courant == h->prm.courant && H.tau == h->prm.tau && H.mu == h->prm.mu;
   if (!match) { std::fclose(fp); return LBPWFA_ERR_IO; }
@@ -1128,7 +1144,8 @@ int lbpwfa_batch_create(const lbpwfa_params* p, int nruns, int flags, lbpwfa_bat
   for (int i = 0; i < nruns; ++i) {
     int st = validate(&p[i]);
     if (st != LBPWFA_OK) return st;
-    if (p[i].dim != 2 || p[i].precision != p[0].precision) return LBPWFA_ERR_INVALID;
+    if (p[i].dim != 2 || p[i].precision != p[0].precision || p[i].geometry != LBPWFA_CARTESIAN)
+      return LBPWFA_ERR_INVALID;
   }
   lbpwfa_batch_s* b = new lbpwfa_batch_s();
   b->precision = p[0].precision;

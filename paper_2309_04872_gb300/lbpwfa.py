@@ -18,6 +18,7 @@ from . import build as _build
 LEC, WARMC = 0, 1
 FP64, FP32, FP16S = 0, 1, 2
 OPEN, PERIODIC = 0, 1
+CARTESIAN, AXISYMMETRIC = 0, 1
 _PREC = {"fp64": FP64, "fp32": FP32, "fp16s": FP16S}
 
 M_N, M_UZ, M_UX, M_UY, M_GAMMA, M_PZ, M_PX, M_PY = (1 << b for b in range(8))
@@ -46,6 +47,7 @@ class Params(ctypes.Structure):
         ("profile", ctypes.POINTER(ctypes.c_double)), ("profile_len", ctypes.c_int),
         ("profile_dz", ctypes.c_double), ("precision", ctypes.c_int), ("boundary", ctypes.c_int),
         ("init_fields", ctypes.c_int), ("stream", ctypes.c_void_p), ("kernel_variant", ctypes.c_int),
+        ("geometry", ctypes.c_int),
     ]
 
 
@@ -137,7 +139,8 @@ def _code(v, table):
 def make_params(cfg: dict, precision="fp64", stream=None, variant=0):
     """Parameter struct from a configuration dict (same keys as the oracle's:
     dim, n, dx, courant, tau, closure, dv, mu, alpha, sigma_z, sigma_r, z0,
-    profile, profile_dz, boundary, init_fields)."""
+    profile, profile_dz, boundary, init_fields, geometry ('cartesian' |
+    'axisymmetric'))."""
     n = list(cfg["n"]) + [1, 1]
     prof = cfg.get("profile")
     keep = None
@@ -165,6 +168,7 @@ def make_params(cfg: dict, precision="fp64", stream=None, variant=0):
     p.init_fields = int(bool(cfg.get("init_fields", p.dim >= 2)))
     p.stream = stream
     p.kernel_variant = int(variant)
+    p.geometry = _code(cfg.get("geometry", "cartesian"), {"cartesian": CARTESIAN, "axisymmetric": AXISYMMETRIC})
     return p, keep
 
 

@@ -60,12 +60,18 @@ def test_invalid_parameters_rejected_before_any_device_work(lib_path):
     base = dict(dim=2, n=(16, 8), dx=0.05, courant=0.1, tau=0.53, closure="lec", dv=3, mu=1e-2,
                 alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=1.0)
     bad = [dict(tau=0.5), dict(courant=0.8), dict(n=(2, 8)), dict(dim=4, n=(8, 8, 8)), dict(dv=2),
-           dict(mu=-1e-3), dict(sigma_z=0.0), dict(sigma_r=-1.0), dict(dx=0.0), dict(closure=5)]
+           dict(mu=-1e-3), dict(sigma_z=0.0), dict(sigma_r=-1.0), dict(dx=0.0), dict(closure=5),
+           dict(geometry=2), dict(geometry="axisymmetric", dim=3, n=(8, 8, 8)),
+           dict(geometry="axisymmetric", boundary="periodic")]
     for b in bad:
         p, keep = lbpwfa.make_params({**base, **b})
         h = ctypes.c_void_p()
         assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1, b
         assert not h.value
+    # axisymmetric runs take the plain kernel only (variants 0 and 1)
+    p, keep = lbpwfa.make_params({**base, "geometry": "axisymmetric"}, variant=3)
+    h = ctypes.c_void_p()
+    assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1
     p, keep = lbpwfa.make_params(base, precision=7)
     h = ctypes.c_void_p()
     assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1

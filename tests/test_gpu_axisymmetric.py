@@ -1,0 +1,138 @@
+"""Parity of the axisymmetric (z, r) CUDA path with the FP64 oracle (Sec. 2.2
+and App. A: the r = 0 boundary node with Eq. open-bc / reflective-bc, the
+1/r source terms, the cylindrical Yee curl), through the C ABI, on the same
+seeded inputs.  Bounds as in the Cartesian parity tests: FP64 to 1e-12
+relative; FP32 and FP16S storage to the unit round-off of the stored
+deviations times the field-source amplification."""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import inputs
+from tests.test_gpu_parity import _check, _compare
+
+pytestmark = pytest.mark.gpu
+
+lb = pytest.importorskip("paper_2309_04872_gb300.lbpwfa")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lb.load_library()
+
+
+def _cfg(closure, n=(77, 45), **kw):
+    cfg = dict(dim=2, n=n, dx=0.05, courant=0.1, tau=0.53, closure=closure, dv=3, mu=1e-2, alpha=0.2,
+               sigma_z=0.6, sigma_r=0.3, z0=0.3 * n[0] * 0.05, boundary="open", init_fields=True,
+               geometry="axisymmetric")
+    cfg.update(kw)
+    return cfg
+
+
+def _random_state(o, seed, mu):
+    base = o.rest_advected()
+    amp = np.abs(base) * 0.05
+    if o.cfg["closure"] == "lec":
+        amp[1:] = 0.02
+    else:
+        amp[2:4] = 0.02
+        for j in range(o.K - 4):
+            if base[4 + j] == 0.0:
+                amp[4 + j] = 0.05 * mu
+    f = inputs.random_populations(seed, o.K, o.Q, o.ncell, base, amp)
+    E, B = inputs.random_fields(seed + 1, o.ncell, 0.01)
+    return f, E, B
+
+
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+def test_axi_fp64_random_state_parity(closure):
+    """Random state (every set perturbed, odd ones included), 25 steps: the
+    advected scalars, fields, populations (the axis node's mirrored sets as
+    exported) and every decoded moment to 1e-12."""
+    cfg = _cfg(closure)
+    orc = O.Oracle(cfg)
+    f, E, B = _random_state(orc, 321, cfg["mu"])
+    orc.set_state(f, E, B)
+    with lb.Run(cfg, "fp64") as run:
+        run.set_state(f, E, B)
+        assert run.info().kernel_variant == 5
+        _compare(run, orc, 1e-12, label="t0")
+        orc.step(25)
+        run.step(25)
+        _compare(run, orc, 1e-12, label="t25")
+        f_g, _, _ = run.get_state()
+        f_o, _, _ = orc.get_state()
+        _check(f_g, f_o, 0.0, 1e-12, 1e-8, 1e-13, "populations")
+        m_g = run.moments(0x3FFFF)
+        m_o = orc.moments(0x3FFFF)
+        for b in range(18):
+            if np.abs(m_o[b]).max() == 0:
+                assert np.abs(m_g[b]).max() == 0, b
+                continue
+            rest = 1.0 if b in (0, 4) else 0.0
+            _check(m_g[b], m_o[b], rest, 1e-12, 1e-8, 1e-13, f"moment bit {b}")
+
+
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+def test_axi_fp64_driver_from_rest_parity(closure):
+    """The driver's initial v -> c field in (z, r) and 150 steps from rest."""
+    cfg = _cfg(closure, mu=0.04)
+    orc = O.Oracle(cfg)
+    with lb.Run(cfg, "fp64") as run:
+        _compare(run, orc, 1e-12, label="t0")
+        orc.step(150)
+        run.step(150)
+        _compare(run, orc, 1e-12, label="t150")
+
+
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+@pytest.mark.parametrize("prec,tol,floor", [("fp32", 1e-4, 1e-7), ("fp16s", 2e-2, 1e-4)])
+def test_axi_reduced_precision_parity(closure, prec, tol, floor):
+    cfg = _cfg(closure, mu=0.04)
+    orc = O.Oracle(cfg)
+    orc.step(100)
+    with lb.Run(cfg, prec) as run:
+        run.step(100)
+        _compare(run, orc, tol, ptol=tol, floor=floor, label=prec)
+
+
+def test_axi_variant_one_is_the_same_kernel():
+    cfg = _cfg("warmc")
+    outs = []
+    for v in (0, 1):
+        with lb.Run(cfg, "fp32", variant=v) as run:
+            assert run.info().kernel_variant == 5
+            run.step(20)
+            outs.append(run.get_state())
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_axi_rejects_batch_and_adjoint():
+    cfg = _cfg("lec")
+    with pytest.raises(Exception):
+        lb.Batch([cfg, cfg], "fp64")
+    with lb.Run(cfg, "fp64") as run:
+        with pytest.raises(Exception):
+            run.record(10)
+
+
+def test_axi_fp64_paper_grid_matches_oracle():
+    """The 3D3V axisymmetric grid of Sec. 6 (L_r = 6, L_z = 30 at dz = dr =
+    0.01: 3000 x 600 nodes), WARMC mu = 0.04, sigma_z = sigma_r = 25 um at
+    n_i = 1e16 cm^-3 (0.47 k_p^-1), Q~ = 0.5 (Eq. Qtilde with D = 3:
+    alpha = Q~ / ((2 pi)^{3/2} sigma_z sigma_r^2)), C = 0.1, tau = 0.53: the
+    bench's grid and launch configuration, compared in full after 8 steps."""
+    sz, sr = 0.47, 0.47
+    alpha = 0.5 / ((2 * np.pi) ** 1.5 * sz * sr * sr)
+    cfg = dict(dim=2, n=(3000, 600), dx=0.01, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=0.04,
+               alpha=alpha, sigma_z=sz, sigma_r=sr, z0=4.0, boundary="open", init_fields=True,
+               geometry="axisymmetric")
+    orc = O.Oracle(cfg)
+    orc.step(8)
+    with lb.Run(cfg, "fp64") as run:
+        run.step(8)
+        _compare(run, orc, 1e-12, label="axi paper grid")
