@@ -185,6 +185,29 @@ int lbpwfa_moments(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst
  * E at t_{n-1/2}, B at t_n, on the dual Yee grid described above. */
 int lbpwfa_fields(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_is_device);
 
+/* Wake diagnostic on the device (the dispersion measurement of Sec. 6,
+ * Fig. 3): least-squares fit of q = A cos(k xi + phi) along one grid line in
+ * z, over the co-moving window xi_lo <= xi <= xi_hi with xi = z - z_d(t),
+ * z_d = z0 + t the driver centre (t = t_n for the density, t_{n-1/2} for the
+ * stored E).  q is E_z (LBPWFA_FIT_EZ, the slots of the line) or n - 1
+ * (LBPWFA_FIT_N).  For each k of the uniform grid k_lo .. k_hi (nk points)
+ * the residual R(k) of the best a cos + b sin is formed from FP64 sums in a
+ * fixed order; the grid minimum is refined by the parabola through it and
+ * its neighbours and refitted there.
+ * line: transverse indices (x, y) of the line (ignored for absent axes).
+ * out (host, 5 doubles): k, A, phi, rms residual, points in the window.
+ * Uses the handle's device scratch buffer; LBPWFA_ERR_INVALID for a line
+ * outside the grid, nk outside [3, 65536] or an empty k or xi range. */
+enum { LBPWFA_FIT_EZ = 0, LBPWFA_FIT_N = 1 };
+typedef struct {
+  int quantity;
+  int line[2];
+  double xi_lo, xi_hi;
+  double k_lo, k_hi;
+  int nk;
+} lbpwfa_fit_params;
+int lbpwfa_line_fit(lbpwfa_t h, const lbpwfa_fit_params* fp, double* out);
+
 /* Advected scalars A_k = sum_i f_ki (Eq. disc-moments-ade), FP64,
  * [K][ncell]; count >= K * ncell. */
 int lbpwfa_advected(lbpwfa_t h, double* dst, size_t count, int dst_is_device);

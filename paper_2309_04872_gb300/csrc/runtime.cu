@@ -19,6 +19,7 @@
 #include "lb_aux.cuh"
 #include "lb_batch_dispatch.h"
 #include "lb_batch_types.cuh"
+#include "lb_diag.cuh"
 #include "lb_dispatch.h"
 #include "lb_runtime.h"
 
@@ -589,6 +590,49 @@ int lbpwfa_fields(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_
   }
   if (!dst_is_device) return deliver(h, out, dst, need * sizeof(double), 0);
   return LBPWFA_OK;
+}
+
+int lbpwfa_line_fit(lbpwfa_t h, const lbpwfa_fit_params* fp, double* out) {
+  if (!h || !fp || !out) return LBPWFA_ERR_INVALID;
+  if (fp->quantity != LBPWFA_FIT_EZ && fp->quantity != LBPWFA_FIT_N) return LBPWFA_ERR_INVALID;
+  const int dim = h->prm.dim;
+  const int ix = dim >= 2 ? fp->line[0] : 0, iy = dim >= 3 ? fp->line[1] : 0;
+  if (ix < 0 || ix >= h->n[1] || iy < 0 || iy >= h->n[2]) return LBPWFA_ERR_INVALID;
+  if (fp->nk < 3 || fp->nk > 65536) return LBPWFA_ERR_INVALID;
+  if (!std::isfinite(fp->k_lo) || !std::isfinite(fp->k_hi) || !(fp->k_hi > fp->k_lo)) return LBPWFA_ERR_INVALID;
+  if (!std::isfinite(fp->xi_lo) || !std::isfinite(fp->xi_hi) || !(fp->xi_hi > fp->xi_lo)) return LBPWFA_ERR_INVALID;
+  const size_t nres = (size_t)fp->nk + 8;
+  int r = ensure_scratch(h, ((size_t)h->ncell + nres) * sizeof(double));
+  if (r != LBPWFA_OK) return r;
+  double* q = (double*)h->scratch.p;
+  double* res = q + h->ncell;
+  AuxParams A = aux_params(h);
+  if (fp->quantity == LBPWFA_FIT_N) {
+    h->ks.moments(A, h->f[h->cur].p, 1u, q, h->stream);
+  } else {
+    h->ks.export_fields(A, h->E[h->cur].p, h->B[h->cur].p, lo_of(h, h->E[h->cur]), lo_of(h, h->B[h->cur]), 1,
+                        make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0), q, h->stream);
+  }
+  CK_LAUNCH(h, "line_fit export");
+  FitLine L{};
+  L.q = q;
+  L.base = (long long)h->n[0] * ((long long)ix + (long long)h->n[1] * iy);
+  L.nz = h->n[0];
+  // the populations are at t_n, the stored E at t_{n-1/2}
+  const double t = fp->quantity == LBPWFA_FIT_N ? (double)h->step * h->dt : ((double)h->step - 0.5) * h->dt;
+  L.zd = h->prm.z0 + t;
+  L.dx = h->prm.dx;
+  L.offset = fp->quantity == LBPWFA_FIT_N ? 1.0 : 0.0;
+  L.xi_lo = fp->xi_lo;
+  L.xi_hi = fp->xi_hi;
+  L.k_lo = fp->k_lo;
+  L.dk = (fp->k_hi - fp->k_lo) / (double)(fp->nk - 1);
+  L.nk = fp->nk;
+  fit_scan_kernel<<<fp->nk, kFitThreads, 0, h->stream>>>(L, res);
+  CK_LAUNCH(h, "fit_scan_kernel");
+  fit_pick_kernel<<<1, kFitThreads, 0, h->stream>>>(L, res, res + fp->nk);
+  CK_LAUNCH(h, "fit_pick_kernel");
+  return deliver(h, res + fp->nk, out, 5 * sizeof(double), 0);
 }
 
 int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double* B, int src_is_device) {

@@ -51,6 +51,15 @@ class Params(ctypes.Structure):
     ]
 
 
+class FitParams(ctypes.Structure):
+    _fields_ = [("quantity", ctypes.c_int), ("line", ctypes.c_int * 2), ("xi_lo", ctypes.c_double),
+                ("xi_hi", ctypes.c_double), ("k_lo", ctypes.c_double), ("k_hi", ctypes.c_double),
+                ("nk", ctypes.c_int)]
+
+
+FIT_EZ, FIT_N = 0, 1
+
+
 class Info(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("Q", ctypes.c_int), ("ncell", ctypes.c_int64),
                 ("step", ctypes.c_int64), ("dt", ctypes.c_double), ("time", ctypes.c_double),
@@ -81,7 +90,7 @@ EXPORTED = ["lbpwfa_create", "lbpwfa_step", "lbpwfa_moments", "lbpwfa_fields", "
             "lbpwfa_load", "lbpwfa_set_stream", "lbpwfa_synchronize", "lbpwfa_destroy",
             "lbpwfa_status_string", "lbpwfa_last_error", "lbpwfa_reduce_noalloc",
             "lbpwfa_batch_create", "lbpwfa_batch_step", "lbpwfa_batch_member", "lbpwfa_batch_info",
-            "lbpwfa_batch_destroy", "lbpwfa_record", "lbpwfa_adjoint_step"]
+            "lbpwfa_batch_destroy", "lbpwfa_record", "lbpwfa_adjoint_step", "lbpwfa_line_fit"]
 
 
 def library_path() -> str:
@@ -104,6 +113,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbpwfa_step.argtypes = [vp, ctypes.c_int64]
     L.lbpwfa_moments.argtypes = [vp, ctypes.c_uint32, vp, ctypes.c_size_t, ctypes.c_int]
     L.lbpwfa_fields.argtypes = [vp, ctypes.c_uint32, vp, ctypes.c_size_t, ctypes.c_int]
+    L.lbpwfa_line_fit.argtypes = [vp, ctypes.POINTER(FitParams), _DP]
     L.lbpwfa_advected.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
     L.lbpwfa_set_state.argtypes = [vp, vp, vp, vp, ctypes.c_int]
     L.lbpwfa_get_state.argtypes = [vp, vp, vp, vp, ctypes.c_int]
@@ -247,6 +257,18 @@ class Run:
         ptr, dev, keep = _buf(out)
         self._check(load_library().lbpwfa_moments(self._h, mask, ptr, nb * self.ncell, dev), "lbpwfa_moments")
         return out
+
+    def line_fit(self, quantity="ez", line=(0, 0), xi=(-25.0, -5.0), k=(0.5, 1.5, 201)):
+        """Least-squares sinusoid fit along one grid line in z (lbpwfa_line_fit):
+        returns dict(k, amplitude, phase, rms, points)."""
+        fp = FitParams()
+        fp.quantity = {"ez": FIT_EZ, "n": FIT_N}[quantity]
+        fp.line[0], fp.line[1] = int(line[0]), int(line[1])
+        fp.xi_lo, fp.xi_hi = float(xi[0]), float(xi[1])
+        fp.k_lo, fp.k_hi, fp.nk = float(k[0]), float(k[1]), int(k[2])
+        out = (ctypes.c_double * 5)()
+        self._check(load_library().lbpwfa_line_fit(self._h, ctypes.byref(fp), out), "lbpwfa_line_fit")
+        return dict(k=out[0], amplitude=out[1], phase=out[2], rms=out[3], points=int(out[4]))
 
     def fields(self, mask: int = 0x3F, out=None):
         nb = bin(mask & 0x3F).count("1")
