@@ -120,8 +120,10 @@ typedef struct {
                               each plane decoded once per column (the
                               automatic 3D choice; 1 gives 32 x 4 x 4 tiles).
                               All compute the same step.  Axisymmetric runs
-                              take 0 or 1 and always run the plain kernel
-                              with the axis rules (reported as 5). */
+                              take 0, 1 or 3: LEC in FP32 and FP16S runs the
+                              persistent kernel with the axis rules (3,
+                              automatic), the rest the plain kernel with
+                              them (reported as 5). */
   int geometry;            /* LBPWFA_CARTESIAN, or LBPWFA_AXISYMMETRIC: the
                               3D3V axisymmetric (z, r) geometry of Sec. 2.2
                               and App. A on a 2D grid (dim 2, open

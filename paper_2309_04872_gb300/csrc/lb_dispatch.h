@@ -55,6 +55,9 @@ struct KernelSet {
   size_t per_smem;
   cudaError_t (*prepare_persist)();
   void (*step_persist)(const StepParams&, const void* tensor_map, int grid, int ntz, int ntiles, cudaStream_t);
+  // the same kernel with the axisymmetric rules (axisymmetric LEC runs)
+  cudaError_t (*prepare_persist_axi)();
+  void (*step_persist_axi)(const StepParams&, const void* tensor_map, int grid, int ntz, int ntiles, cudaStream_t);
 };
 
 bool kernels_f64(int dim, int closure, KernelSet* ks);

@@ -115,6 +115,18 @@ struct Impl {
       lb_step_persist2d_kernel<CL, PR><<<grid, PC::TZ * PC::TX, PC::smem_bytes, s>>>(
           P, *reinterpret_cast<const CUtensorMap*>(map), ntz, ntiles);
   }
+  static cudaError_t prepare_persist_axi() {
+    if constexpr (kPersist)
+      return cudaFuncSetAttribute(lb_step_persist2d_kernel<CL, PR, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PC::smem_bytes);
+    return cudaErrorNotSupported;
+  }
+  static void step_persist_axi(const StepParams& P, const void* map, int grid, int ntz, int ntiles,
+                               cudaStream_t s) {
+    if constexpr (kPersist)
+      lb_step_persist2d_kernel<CL, PR, true><<<grid, PC::TZ * PC::TX, PC::smem_bytes, s>>>(
+          P, *reinterpret_cast<const CUtensorMap*>(map), ntz, ntiles);
+  }
   static void fill(KernelSet* ks) {
     ks->has_axi = kAxi;
     ks->prepare_axi = &prepare_axi;
@@ -136,6 +148,8 @@ struct Impl {
     ks->per_smem = PC::smem_bytes;
     ks->prepare_persist = &prepare_persist;
     ks->step_persist = &step_persist;
+    ks->prepare_persist_axi = &prepare_persist_axi;
+    ks->step_persist_axi = &step_persist_axi;
     ks->has_tma = kTma;
     ks->tma_tz = TC::TZ;
     ks->tma_tx = TC::TX;

@@ -175,7 +175,9 @@ struct PersistCfg2D {
   static constexpr size_t smem_bytes = 128 + box_pad + 16 + Body::smem_bytes;
 };
 
-template <int CL, int PR>
+// AXI: the x = 0 row is the r = 0 boundary node of an axisymmetric grid; its
+// odd sets take the mirrored velocity (as pulled_dev).
+template <int CL, int PR, bool AXI = false>
 struct SmemPullBox2D {
   using T = PersistCfg2D<CL, PR>;
   using real = typename Prec<PR>::real;
@@ -186,6 +188,7 @@ struct SmemPullBox2D {
   template <bool EDGE>
   __device__ __forceinline__ void get(int z, int x, int, int k, real* df) const {
     using L = Lattice<2>;
+    const bool mirror = AXI && EDGE && x == 0 && odd_in_r<CL>(k);
     const int bz = (EDGE ? min(max(z, 1), P.n[0] - 2) : z) - oz;
     const int bx = (EDGE ? min(max(x, 1), P.n[1] - 2) : x) - ox;
     const float is = P.inv_scale[k];
@@ -201,6 +204,15 @@ struct SmemPullBox2D {
       const store* lo = box + ((size_t)T::KQ + k) * T::BX * T::BZ;
       df[0] = Codec<PR>::join(bk[bx * T::BZ + bz], lo[bx * T::BZ + bz], is);
     }
+    if constexpr (AXI) {
+      if (mirror) {
+        // D2Q9 with x reversed: 3 <-> 4, 5 <-> 7, 6 <-> 8
+        real t;
+        t = df[3]; df[3] = df[4]; df[4] = t;
+        t = df[5]; df[5] = df[7]; df[7] = t;
+        t = df[6]; df[6] = df[8]; df[8] = t;
+      }
+    }
   }
 };
 
@@ -211,7 +223,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-template <int CL, int PR>
+// AXI: the axisymmetric (z, r) step (the axis rules and 1/r sources of
+// step_body's AXI mode).
+template <int CL, int PR, bool AXI = false>
 __global__ void __launch_bounds__(PersistCfg2D<CL, PR>::TZ* PersistCfg2D<CL, PR>::TX, PersistCfg2D<CL, PR>::MINB)
 lb_step_persist2d_kernel(const StepParams P, const __grid_constant__ CUtensorMap tmap, int ntz, int ntiles) {
   using T = PersistCfg2D<CL, PR>;
@@ -259,9 +273,11 @@ lb_step_persist2d_kernel(const StepParams P, const __grid_constant__ CUtensorMap
         tma_load_3d(box, &tmap, bar, (tn % ntz) * T::TZ - T::HZ, (tn / ntz) * T::TX - 2, 0);
       }
     };
-    SmemPullBox2D<CL, PR> pull{P, box, tz * T::TZ - T::HZ, tx * T::TX - 2};
-    if (bulk) step_body<2, CL, PR, T::TZ, T::TX, 1, false>(P, body, pull, F, tz, tx, 0, refill);
-    else step_body<2, CL, PR, T::TZ, T::TX, 1, true>(P, body, pull, F, tz, tx, 0, refill);
+    using Pull = SmemPullBox2D<CL, PR, AXI>;
+    using Hook = decltype(refill);
+    Pull pull{P, box, tz * T::TZ - T::HZ, tx * T::TX - 2};
+    if (bulk) step_body<2, CL, PR, T::TZ, T::TX, 1, false, Pull, Hook, false, AXI>(P, body, pull, F, tz, tx, 0, refill);
+    else step_body<2, CL, PR, T::TZ, T::TX, 1, true, Pull, Hook, false, AXI>(P, body, pull, F, tz, tx, 0, refill);
     __syncthreads();  // the records and E slots are free for the next tile
   }
 }

@@ -92,9 +92,9 @@ int validate(const lbpwfa_params* p) {
   if (p->boundary != LBPWFA_OPEN && p->boundary != LBPWFA_PERIODIC) return LBPWFA_ERR_INVALID;
   if (p->kernel_variant < 0 || p->kernel_variant > 4) return LBPWFA_ERR_INVALID;
   if (p->geometry != LBPWFA_CARTESIAN && p->geometry != LBPWFA_AXISYMMETRIC) return LBPWFA_ERR_INVALID;
-  // axisymmetric (z, r): 2D, open boundaries, the plain kernel's tile
+  // axisymmetric (z, r): 2D, open boundaries, the plain (1) or persistent (3) kernel
   if (p->geometry == LBPWFA_AXISYMMETRIC &&
-      (p->dim != 2 || p->boundary != LBPWFA_OPEN || p->kernel_variant > 1))
+      (p->dim != 2 || p->boundary != LBPWFA_OPEN || p->kernel_variant == 2 || p->kernel_variant == 4))
     return LBPWFA_ERR_INVALID;
   long long cells = 1;
   for (int a = 0; a < p->dim; ++a) cells *= p->n[a];
@@ -304,19 +304,20 @@ int launch_step(lbpwfa_s* h, void* tape) {
                                : step_grid(h);
   StepParams P = step_params(h);
   P.tape = tape;
-  if (h->use_axi) {
+  if (h->use_persist) {
+    const int ntz = (h->n[0] + h->ks.per_tz - 1) / h->ks.per_tz;
+    const int ntiles = ntz * ((h->n[1] + h->ks.per_tx - 1) / h->ks.per_tx);
+    const int slots = h->num_sms * h->ks.per_ctas;
+    const int pgrid = ntiles < slots ? ntiles : slots;
+    if (h->use_axi) h->ks.step_persist_axi(P, &h->maps[h->cur], pgrid, ntz, ntiles, h->stream);
+    else h->ks.step_persist(P, &h->maps[h->cur], pgrid, ntz, ntiles, h->stream);
+  } else if (h->use_axi) {
     h->ks.step_axi(P, grid, h->stream);
   } else if (h->use_march) {
     const dim3 mg((unsigned)((h->n[0] + h->ks.march_tz - 1) / h->ks.march_tz),
                   (unsigned)((h->n[1] + h->ks.march_tx - 1) / h->ks.march_tx),
                   (unsigned)((h->n[2] + h->ks.march_yc - 1) / h->ks.march_yc));
     h->ks.step_march(P, mg, h->stream);
-  } else if (h->use_persist) {
-    const int ntz = (h->n[0] + h->ks.per_tz - 1) / h->ks.per_tz;
-    const int ntiles = ntz * ((h->n[1] + h->ks.per_tx - 1) / h->ks.per_tx);
-    const int slots = h->num_sms * h->ks.per_ctas;
-    const int pgrid = ntiles < slots ? ntiles : slots;
-    h->ks.step_persist(P, &h->maps[h->cur], pgrid, ntz, ntiles, h->stream);
   } else if (h->use_tma) {
     h->ks.step_tma(P, &h->maps[h->cur], grid, h->stream);
   } else {
@@ -465,14 +466,14 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
     cudaGetLastError();
     h->use_march = false;
   }
-  const bool tma_ok = dim == 2 && p->boundary == LBPWFA_OPEN && !h->use_axi;
+  const bool tma_ok = dim == 2 && p->boundary == LBPWFA_OPEN;
   // automatic choice for LEC: the persistent refilling CTAs where the tile
   // table marks them faster, else one TMA box per CTA; WARMC's 72-plane box
   // leaves two CTAs per SM and the global-memory pull is faster there
   const bool persist_auto = p->kernel_variant == 0 && p->closure == LBPWFA_LEC && h->ks.persist_auto;
   h->use_persist = (p->kernel_variant == 3 || persist_auto) && tma_ok && h->ks.has_persist && h->num_sms > 0;
   if (h->use_persist) {
-    cudaError_t e = h->ks.prepare_persist();
+    cudaError_t e = h->use_axi ? h->ks.prepare_persist_axi() : h->ks.prepare_persist();
     bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0], h->ks.per_box) &&
               make_pop_map(h, h->f[1].p, &h->maps[1], h->ks.per_box);
     if (!ok) {
@@ -481,7 +482,7 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
     }
   }
   const bool tma_auto = p->kernel_variant == 0 && p->closure == LBPWFA_LEC;
-  h->use_tma = !h->use_persist && (tma_auto || p->kernel_variant == 2) && tma_ok && h->ks.has_tma;
+  h->use_tma = !h->use_persist && !h->use_axi && (tma_auto || p->kernel_variant == 2) && tma_ok && h->ks.has_tma;
   if (h->use_tma) {
     cudaError_t e = h->ks.prepare_tma();
     bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0], h->ks.tma_box) &&
@@ -738,7 +739,7 @@ int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info) {
   // FP32 fields: high and low parts
   const double field_words = (ne + nbf) * (h->real_sz == 4 ? 2.0 : 1.0);
   info->bytes_per_update = 2.0 * h->NPL * h->store_sz + 2.0 * (field_words + h->NPREV) * h->real_sz;
-  info->kernel_variant = h->use_axi ? 5 : (h->use_march ? 4 : (h->use_persist ? 3 : (h->use_tma ? 2 : 1)));
+  info->kernel_variant = h->use_persist ? 3 : (h->use_axi ? 5 : (h->use_march ? 4 : (h->use_tma ? 2 : 1)));
   return LBPWFA_OK;
 }
 

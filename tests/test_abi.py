@@ -68,10 +68,11 @@ def test_invalid_parameters_rejected_before_any_device_work(lib_path):
         h = ctypes.c_void_p()
         assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1, b
         assert not h.value
-    # axisymmetric runs take the plain kernel only (variants 0 and 1)
-    p, keep = lbpwfa.make_params({**base, "geometry": "axisymmetric"}, variant=3)
-    h = ctypes.c_void_p()
-    assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1
+    # axisymmetric runs take the plain or the persistent kernel (variants 0, 1, 3)
+    for v in (2, 4):
+        p, keep = lbpwfa.make_params({**base, "geometry": "axisymmetric"}, variant=v)
+        h = ctypes.c_void_p()
+        assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1
     p, keep = lbpwfa.make_params(base, precision=7)
     h = ctypes.c_void_p()
     assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1

@@ -111,6 +111,35 @@ def test_axi_variant_one_is_the_same_kernel():
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp16s", "fp64"])
+@pytest.mark.parametrize("n", [(131, 37), (700, 300)])
+def test_axi_lec_persistent_and_plain_agree(prec, n):
+    """Axisymmetric LEC on the persistent TMA kernel (automatic in FP32 and
+    FP16S; variant 3) and on the plain kernel (variant 1): the same step, to
+    the storage precision's round-off of the largest deviation from rest
+    (700 x 300 has more tiles than persistent CTAs, so boxes are refilled)."""
+    cfg = _cfg("lec", n=n, mu=0.04)
+    orc = O.Oracle(cfg)
+    f, E, B = _random_state(orc, 5 + n[0], cfg["mu"])
+    outs = []
+    for v in (3, 1):
+        with lb.Run(cfg, prec, variant=v) as run:
+            assert run.info().kernel_variant == (3 if v == 3 else 5)
+            run.set_state(f, E, B)
+            run.step(17)
+            outs.append((run.advected(), run.get_state()[1]))
+    if prec != "fp64":
+        with lb.Run(cfg, prec) as run:
+            assert run.info().kernel_variant == 3
+    rest = orc.rest_advected()
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for k in range(orc.K):
+        d = np.abs(outs[0][0][k] - outs[1][0][k]).max()
+        assert d <= tol * max(np.abs(outs[1][0][k] - rest[k]).max(), 1e-30), k
+    dE = np.abs(outs[0][1] - outs[1][1]).max()
+    assert dE <= tol * np.abs(outs[1][1]).max()
+
+
 def test_axi_rejects_batch_and_adjoint():
     cfg = _cfg("lec")
     with pytest.raises(Exception):
@@ -136,3 +165,41 @@ def test_axi_fp64_paper_grid_matches_oracle():
     with lb.Run(cfg, "fp64") as run:
         run.step(8)
         _compare(run, orc, 1e-12, label="axi paper grid")
+
+
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+@pytest.mark.parametrize("n", [(3, 3), (3, 40), (40, 3), (33, 9), (65, 17)])
+def test_axi_edge_sizes(closure, n):
+    """Grids down to 3 x 3 (every node a boundary node, the axis node's bulk
+    node also the outer boundary's), single and ragged tiles, from a random
+    state: FP64 parity after 9 steps."""
+    cfg = _cfg(closure, n=n)
+    orc = O.Oracle(cfg)
+    f, E, B = _random_state(orc, 77 + n[0] + n[1], cfg["mu"])
+    orc.set_state(f, E, B)
+    with lb.Run(cfg, "fp64") as run:
+        run.set_state(f, E, B)
+        run.step(0)
+        orc.step(9)
+        run.step(9)
+        _compare(run, orc, 1e-12, label=f"axi {n}")
+
+
+def test_axi_checkpoint_roundtrip_and_geometry_check(tmp_path):
+    cfg = _cfg("warmc")
+    path = str(tmp_path / "axi.ckpt")
+    with lb.Run(cfg, "fp32") as run:
+        run.step(20)
+        run.save(path)
+        run.step(15)
+        want = run.get_state()
+    with lb.Run(cfg, "fp32") as run:
+        run.load(path)
+        run.step(15)
+        got = run.get_state()
+    for a, b in zip(want, got):
+        assert np.array_equal(a, b)
+    # the same grid in Cartesian geometry refuses the file
+    with lb.Run(dict(cfg, geometry="cartesian"), "fp32") as run:
+        with pytest.raises(lb.LbpwfaError):
+            run.load(path)
