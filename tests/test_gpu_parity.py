@@ -201,6 +201,22 @@ def test_fp64_2d_full_size_matches_oracle():
         _compare(run, orc, 1e-12, label="2d full")
 
 
+@pytest.mark.parametrize("prec,tol,floor", [("fp32", 1e-4, 1e-7), ("fp16s", 2e-2, 1e-4)])
+def test_reduced_precision_2d_full_size_in_the_bench_launch(prec, tol, floor):
+    """The bench's headline grid and launch: 1024 x 512 LEC on the persistent
+    TMA kernel (the automatic choice in FP32 and FP16S), against the FP64
+    oracle after 30 steps, with the reduced-precision bounds of the driver
+    parity tests."""
+    cfg = dict(dim=2, n=(1024, 512), dx=0.05, courant=0.1, tau=0.53, closure="lec", dv=3, mu=1e-2,
+               alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=4.0, boundary="open", init_fields=True)
+    orc = O.Oracle(cfg)
+    orc.step(30)
+    with lb.Run(cfg, prec) as run:
+        assert run.info().kernel_variant == 3
+        run.step(30)
+        _compare(run, orc, tol, ptol=tol, floor=floor, label=f"2d full {prec}")
+
+
 def test_fp64_3d_reduced_grid_matches_oracle():
     """3D WARMC on a reduced grid (64 x 32 x 32) with the 3D driver
     (alpha = 1, sigma_z = 0.7, sigma_r = 0.3, mu = 1e-2)."""
