@@ -210,6 +210,18 @@ typedef struct {
 } lbpwfa_fit_params;
 int lbpwfa_line_fit(lbpwfa_t h, const lbpwfa_fit_params* fp, double* out);
 
+/* Gauss's law residual (Sec. 6: not imposed; it holds up to the LB's
+ * numerical diffusion), FP64 on the device.  On the dual cells centred at
+ * (z_{i+1/2}, x_{j+1/2}, y_{k+1/2}) the Yee slots give div E (axisymmetric:
+ * the radial term (r_{j+1} E_r(j+1) - r_j E_r(j)) / (r_{j+1/2} dx)); rho =
+ * -(nbar - 1) - n_b with nbar the mean density of the cell's corner nodes
+ * (at t_n) and n_b the driver at the centre at t_{n-1/2}, the time of the
+ * stored E.  lo[a] <= i < hi[a] per present axis, 0 <= lo < hi <= n[a] - 1.
+ * out (host, 3 doubles): sum (div E - rho)^2, sum rho^2, cells.  Fixed
+ * block partition and tree: repeated calls return identical bits.  Uses the
+ * handle's device scratch buffer. */
+int lbpwfa_gauss_residual(lbpwfa_t h, const int* lo, const int* hi, double* out);
+
 /* Advected scalars A_k = sum_i f_ki (Eq. disc-moments-ade), FP64,
  * [K][ncell]; count >= K * ncell. */
 int lbpwfa_advected(lbpwfa_t h, double* dst, size_t count, int dst_is_device);

@@ -636,6 +636,47 @@ int lbpwfa_line_fit(lbpwfa_t h, const lbpwfa_fit_params* fp, double* out) {
   return deliver(h, res + fp->nk, out, 5 * sizeof(double), 0);
 }
 
+int lbpwfa_gauss_residual(lbpwfa_t h, const int* lo, const int* hi, double* out) {
+  if (!h || !lo || !hi || !out) return LBPWFA_ERR_INVALID;
+  const int dim = h->prm.dim;
+  GaussArgs G{};
+  G.dim = dim;
+  G.ncells = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      if (lo[a] < 0 || hi[a] > h->n[a] - 1 || lo[a] >= hi[a]) return LBPWFA_ERR_INVALID;
+      G.lo[a] = lo[a];
+      G.hi[a] = hi[a];
+    } else {
+      G.lo[a] = 0;
+      G.hi[a] = 1;
+    }
+    G.ncells *= G.hi[a] - G.lo[a];
+  }
+  constexpr int nblk = 256;
+  int r = ensure_scratch(h, (4 * (size_t)h->ncell + 2 * nblk + 4) * sizeof(double));
+  if (r != LBPWFA_OK) return r;
+  double* nbuf = (double*)h->scratch.p;
+  double* Ebuf = nbuf + h->ncell;
+  double* part = Ebuf + 3 * (size_t)h->ncell;
+  double* res = part + 2 * nblk;
+  AuxParams A = aux_params(h);
+  h->ks.moments(A, h->f[h->cur].p, 1u, nbuf, h->stream);
+  CK_LAUNCH(h, "gauss_residual density");
+  h->ks.export_fields(A, h->E[h->cur].p, h->B[h->cur].p, lo_of(h, h->E[h->cur]), lo_of(h, h->B[h->cur]), 3,
+                      make_int4(0, 1, 2, 0), make_int4(0, 0, 0, 0), Ebuf, h->stream);
+  CK_LAUNCH(h, "gauss_residual fields");
+  A.t = ((double)h->step - 0.5) * h->dt;  // the stored E is at t_{n-1/2}
+  G.A = A;
+  G.n = nbuf;
+  G.E = Ebuf;
+  gauss_partial_kernel<<<nblk, 256, 0, h->stream>>>(G, part);
+  CK_LAUNCH(h, "gauss_partial_kernel");
+  gauss_final_kernel<<<1, 32, 0, h->stream>>>(part, nblk, G.ncells, res);
+  CK_LAUNCH(h, "gauss_final_kernel");
+  return deliver(h, res, out, 3 * sizeof(double), 0);
+}
+
 int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double* B, int src_is_device) {
   if (!h) return LBPWFA_ERR_INVALID;
   AuxParams A = aux_params(h);

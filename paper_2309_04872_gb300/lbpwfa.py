@@ -90,7 +90,8 @@ EXPORTED = ["lbpwfa_create", "lbpwfa_step", "lbpwfa_moments", "lbpwfa_fields", "
             "lbpwfa_load", "lbpwfa_set_stream", "lbpwfa_synchronize", "lbpwfa_destroy",
             "lbpwfa_status_string", "lbpwfa_last_error", "lbpwfa_reduce_noalloc",
             "lbpwfa_batch_create", "lbpwfa_batch_step", "lbpwfa_batch_member", "lbpwfa_batch_info",
-            "lbpwfa_batch_destroy", "lbpwfa_record", "lbpwfa_adjoint_step", "lbpwfa_line_fit"]
+            "lbpwfa_batch_destroy", "lbpwfa_record", "lbpwfa_adjoint_step", "lbpwfa_line_fit",
+            "lbpwfa_gauss_residual"]
 
 
 def library_path() -> str:
@@ -114,6 +115,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbpwfa_moments.argtypes = [vp, ctypes.c_uint32, vp, ctypes.c_size_t, ctypes.c_int]
     L.lbpwfa_fields.argtypes = [vp, ctypes.c_uint32, vp, ctypes.c_size_t, ctypes.c_int]
     L.lbpwfa_line_fit.argtypes = [vp, ctypes.POINTER(FitParams), _DP]
+    L.lbpwfa_gauss_residual.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _DP]
     L.lbpwfa_advected.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
     L.lbpwfa_set_state.argtypes = [vp, vp, vp, vp, ctypes.c_int]
     L.lbpwfa_get_state.argtypes = [vp, vp, vp, vp, ctypes.c_int]
@@ -269,6 +271,15 @@ class Run:
         out = (ctypes.c_double * 5)()
         self._check(load_library().lbpwfa_line_fit(self._h, ctypes.byref(fp), out), "lbpwfa_line_fit")
         return dict(k=out[0], amplitude=out[1], phase=out[2], rms=out[3], points=int(out[4]))
+
+    def gauss_residual(self, lo, hi):
+        """Gauss's law residual over the dual cells lo <= index < hi
+        (lbpwfa_gauss_residual): dict(res2, rho2, cells)."""
+        a = (ctypes.c_int * 3)(*(list(lo) + [0, 0, 0])[:3])
+        b = (ctypes.c_int * 3)(*(list(hi) + [1, 1, 1])[:3])
+        out = (ctypes.c_double * 3)()
+        self._check(load_library().lbpwfa_gauss_residual(self._h, a, b, out), "lbpwfa_gauss_residual")
+        return dict(res2=out[0], rho2=out[1], cells=int(out[2]))
 
     def fields(self, mask: int = 0x3F, out=None):
         nb = bin(mask & 0x3F).count("1")

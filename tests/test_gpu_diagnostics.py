@@ -91,3 +91,56 @@ def test_warm_dispersion_1d3v_on_the_gpu(closure, mu):
     paper = -5 * mu / 6 if closure == "lec" else mu / 2
     assert abs(_COLD[closure] - 1.0) < 2e-4
     assert abs(shift - paper) < 2.5 * mu * mu
+
+
+@pytest.mark.parametrize("case", ["1d", "2d", "3d", "axi"])
+def test_gauss_residual_matches_the_oracle_definition(case):
+    """The device reduction against the oracle's definition on the same
+    exported density and fields, after a driven FP64 run."""
+    cfgs = {
+        "1d": dict(dim=1, n=(301,), dx=0.05, courant=0.5, tau=0.53, closure="lec", dv=1, mu=1e-2, alpha=0.1,
+                   sigma_z=0.6, z0=3.0, boundary="open"),
+        "2d": dict(dim=2, n=(77, 45), dx=0.05, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=1e-2, alpha=0.2,
+                   sigma_z=0.6, sigma_r=0.3, z0=1.2, boundary="open", init_fields=True),
+        "3d": dict(dim=3, n=(37, 21, 13), dx=0.05, courant=0.08, tau=0.53, closure="lec", dv=3, mu=1e-2,
+                   alpha=0.2, sigma_z=0.6, sigma_r=0.3, z0=0.6, boundary="open", init_fields=True),
+        "axi": dict(dim=2, n=(77, 45), dx=0.05, courant=0.1, tau=0.53, closure="lec", dv=3, mu=1e-2, alpha=0.2,
+                    sigma_z=0.6, sigma_r=0.3, z0=1.2, boundary="open", init_fields=True, geometry="axisymmetric"),
+    }
+    cfg = cfgs[case]
+    dim = cfg["dim"]
+    lo = [2, 1, 1][:dim]
+    hi = [v - 2 for v in cfg["n"]]
+    with lb.Run(cfg, "fp64") as run:
+        run.step(40)
+        g = run.gauss_residual(lo, hi)
+        n = run.moments(lb.M_N)[0]
+        E = run.fields(lb.F_EZ | lb.F_EX | lb.F_EY)  # returned in bit order: E_x, E_y, E_z
+        E = np.stack([E[2], E[0], E[1]])
+        t = (run.info().step - 0.5) * run.info().dt
+    r2, rho2, cells = D.gauss_residual(cfg, n, E, t, lo, hi)
+    assert g["cells"] == cells
+    assert abs(g["res2"] - r2) <= 1e-11 * r2
+    assert abs(g["rho2"] - rho2) <= 1e-11 * rho2
+    assert g["rho2"] > 0
+
+
+def test_gauss_law_of_a_driven_run_on_the_gpu():
+    """Sec. 6: Gauss's law holds to the LB diffusion (tau = 0.505, 300
+    steps, FP32 storage): residual within 2% of |rho|, as for the oracle."""
+    cfg = dict(dim=2, n=(96, 48), dx=0.1, courant=0.1, tau=0.505, closure="lec", dv=3,
+               mu=1e-3, alpha=0.05, sigma_z=0.8, sigma_r=0.6, z0=3.0, boundary="open", init_fields=True)
+    with lb.Run(cfg, "fp32") as run:
+        run.step(300)
+        g = run.gauss_residual([4, 4], [65, 43])
+    assert g["cells"] == 61 * 39
+    assert np.sqrt(g["res2"] / g["rho2"]) < 0.02
+
+
+def test_gauss_residual_rejects_bad_ranges():
+    cfg = dict(dim=2, n=(20, 10), dx=0.1, courant=0.1, tau=0.53, closure="lec", dv=3, mu=1e-3, alpha=0.05,
+               sigma_z=0.8, sigma_r=0.6, z0=1.0, boundary="open")
+    with lb.Run(cfg, "fp32") as run:
+        for lo, hi in (([0, 0], [20, 9]), ([3, 3], [3, 5]), ([-1, 0], [5, 5])):
+            with pytest.raises(lb.LbpwfaError):
+                run.gauss_residual(lo, hi)
