@@ -452,6 +452,9 @@ def run_ours(a):
                                              "kernel": r["kernel"]}
         out["modes"] = modes
         out["precision_vs_fp64"] = _precision_table(cfg, stream)
+        # the same check on the axisymmetric path (600 x 120 nodes of the 3D3V configuration's spacing 0.05)
+        out["precision_vs_fp64_axisymmetric"] = _precision_table(
+            dict(CONFIG_AXI, n=(600, 120), dx=0.05, z0=3.0), stream)
 
     if rank == 0 and not a.no_configs and a.workload == "2d_lec":
         out["configs_measured"] = _configs(stream, flush, hbm)
@@ -540,7 +543,7 @@ def _configs(stream, flush, hbm):
             "l2": "state larger than L2 (no flush)"}
     # the axisymmetric 3D3V grid, both closures
     for closure in ("warmc", "lec"):
-        for prec in ("fp32", "fp64"):
+        for prec in ("fp32", "fp16s", "fp64"):
             c = dict(CONFIG_AXI, closure=closure)
             with lb.Run(c, prec, stream=stream.cuda_stream) as run:
                 info = run.info()

@@ -203,3 +203,24 @@ def test_axi_checkpoint_roundtrip_and_geometry_check(tmp_path):
     with lb.Run(dict(cfg, geometry="cartesian"), "fp32") as run:
         with pytest.raises(lb.LbpwfaError):
             run.load(path)
+
+
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+def test_axi_reduced_precision_wake_after_2000_steps(closure):
+    """The precision targets on the axisymmetric path: relative L2 error of
+    n - 1 and E_z against the FP64 path after 2000 steps, FP32 storage within
+    1e-6, FP16-shifted storage within 1e-3 (600 x 120 nodes, dz = dr = 0.05,
+    mu = 0.04, Q~ = 0.5 bunch of sigma_z = sigma_r = 0.47)."""
+    alpha = 0.5 / ((2 * np.pi) ** 1.5 * 0.47 ** 3)
+    cfg = _cfg(closure, n=(600, 120), mu=0.04, alpha=alpha, sigma_z=0.47, sigma_r=0.47, z0=3.0)
+    out = {}
+    for prec in ("fp64", "fp32", "fp16s"):
+        with lb.Run(cfg, prec) as run:
+            run.step(2000)
+            out[prec] = (run.moments(lb.M_N)[0] - 1.0, run.fields(lb.F_EZ)[0])
+    n_ref, e_ref = out["fp64"]
+    for prec, tol in (("fp32", 1e-6), ("fp16s", 1e-3)):
+        n1, ez = out[prec]
+        en = np.linalg.norm(n1 - n_ref) / np.linalg.norm(n_ref)
+        ee = np.linalg.norm(ez - e_ref) / np.linalg.norm(e_ref)
+        assert en <= tol and ee <= tol, (prec, en, ee)
