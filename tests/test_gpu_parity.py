@@ -58,7 +58,7 @@ def _random_state(o, seed, mu):
 
 
 def _check(got, ref, rest, tol, ptol, floor, what):
-    """Relative error of the quantity itself (the spec definition), and
+    """Relative error of the quantity itself (how the precision targets are stated), and
     a second bound on its perturbation from the rest value with an absolute
     floor: the oracle keeps plain populations, whose sum drifts by the
     round-off of sum_i w_i != 1 (a few 1e-16 per step), while the CUDA path
