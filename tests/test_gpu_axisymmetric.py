@@ -224,3 +224,29 @@ def test_axi_reduced_precision_wake_after_2000_steps(closure):
         en = np.linalg.norm(n1 - n_ref) / np.linalg.norm(n_ref)
         ee = np.linalg.norm(ez - e_ref) / np.linalg.norm(e_ref)
         assert en <= tol and ee <= tol, (prec, en, ee)
+
+
+@pytest.mark.parametrize("closure,mu,window,tol,C", [("lec", 0.0, 6.0, 0.035, 0.5), ("lec", 0.04, 4.0, 0.045, 0.15),
+                                                      ("warmc", 1e-3, 6.0, 0.035, 0.5)])
+def test_axi_fp32_wake_matches_the_hankel_solution(closure, mu, window, tol, C):
+    """App. B on the GPU path in FP32 storage (LEC on the persistent kernel):
+    n - 1 at r = 0.3, 0.6, 1.0 against the order-0 Hankel solution by
+    quadrature, with the oracle pins' grid (dz = dr = 0.1, tau = 0.505) and
+    bounds."""
+    from oracle import linear_theory as LT
+    cfg = dict(dim=2, n=(200, 70), dx=0.1, courant=C, tau=0.505, closure=closure, dv=3, mu=mu, alpha=1e-3,
+               sigma_z=0.6, sigma_r=0.5, z0=3.0, boundary="open", init_fields=True, geometry="axisymmetric")
+    with lb.Run(cfg, "fp32") as run:
+        N = int(round(14.0 / run.info().dt))
+        run.step(N)
+        n1 = run.moments(lb.M_N)[0].reshape(70, 200) - 1.0
+        dt = run.info().dt
+    xi = np.arange(200) * 0.1 - N * dt
+    sel = (xi > 3.0 - window) & (xi < 3.0 + 1.5)
+    cs2, ae2, ab2 = LT.coefficients(closure, mu)
+    radii = [0.3, 0.6, 1.0]
+    th = LT.hankel_n1(radii, xi[sel], 1e-3, 0.6, 0.5, 3.0, cs2, ae2, ab2)
+    for m, r in enumerate(radii):
+        j = int(round(r / 0.1))
+        e = np.linalg.norm(n1[j, sel] - th[m]) / np.linalg.norm(th[m])
+        assert e <= tol, (r, e)
