@@ -74,3 +74,23 @@ def hankel_n1(r, xi, alpha, sigma_z, sigma_r, xi_d, cs2, ae2, ab2, nw=3000, h=0.
     n_hat = -(ab2 / (1.0 - cs2)) * nb_hat[:, None] * S    # [w][g]
     n1g = (sp.j0(np.outer(r, w)) * (w * dw)[None, :]) @ n_hat
     return np.stack([np.interp(xi, g, row) for row in n1g])
+
+
+def fit_cs2(n1, radii, xi, alpha, sigma_z, sigma_r, xi_d, ae2, ab2, bounds=(1e-4, 0.3), nw=1500):
+    """The acoustic speed squared c_s^2 that makes the order-0 Hankel
+    solution closest (relative L2 over the given radii and co-moving
+    positions) to a wake map n1[radius][xi], with a_e^2 and a_b^2 held
+    fixed: c_s shapes the Mach cone of the warm wake (Sec. 6, Fig. 6:
+    c_s = c sin(Theta)), so the fit measures it from the whole cone rather
+    than from one contour of it.  Bounded scalar minimisation (scipy);
+    returns (c_s^2, misfit)."""
+    from scipy.optimize import minimize_scalar
+    n1 = np.asarray(n1, dtype=np.float64)
+    scale = np.linalg.norm(n1)
+
+    def misfit(cs2):
+        th = hankel_n1(radii, xi, alpha, sigma_z, sigma_r, xi_d, cs2, ae2, ab2, nw=nw)
+        return np.linalg.norm(n1 - th) / scale
+
+    r = minimize_scalar(misfit, bounds=bounds, method="bounded", options={"xatol": 1e-5})
+    return float(r.x), float(r.fun)

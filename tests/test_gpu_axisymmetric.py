@@ -250,3 +250,38 @@ def test_axi_fp32_wake_matches_the_hankel_solution(closure, mu, window, tol, C):
         j = int(round(r / 0.1))
         e = np.linalg.norm(n1[j, sel] - th[m]) / np.linalg.norm(th[m])
         assert e <= tol, (r, e)
+
+
+def test_axi_fp32_acoustic_speed_against_temperature():
+    """Fig. 6 on the GPU path (FP32 storage): c_s^2 fitted from the warm wake
+    map (the Hankel solution's c_s^2 that matches the map best, which sets
+    the Mach cone, c_s = c sin Theta) at mu = 0.01 and 0.04.  LEC within 12%
+    of App. B's 5 mu / 3 (its O(mu) form; the enthalpy factor 1 + 5 mu / 2 is
+    the rest), the WARMC faster than the LEC at each temperature (App. B:
+    3 mu against 5 mu / 3), c_s^2 growing with mu, misfits below 6%."""
+    from oracle import linear_theory as LT
+    fitted = {}
+    for closure in ("lec", "warmc"):
+        for mu in (0.01, 0.04):
+            C = 0.15 if closure == "warmc" else 0.2
+            cfg = dict(dim=2, n=(160, 50), dx=0.1, courant=C, tau=0.505, closure=closure, dv=3, mu=mu, alpha=1e-3,
+                       sigma_z=0.47, sigma_r=0.47, z0=3.0, boundary="open", init_fields=True,
+                       geometry="axisymmetric")
+            with lb.Run(cfg, "fp32") as run:
+                N = int(round(11.0 / run.info().dt))
+                run.step(N)
+                n1 = run.moments(lb.M_N)[0].reshape(50, 160) - 1.0
+                zd = 3.0 + N * run.info().dt
+            xi = np.arange(160) * 0.1 - zd
+            sel = (xi > -6.0) & (xi < 1.5)
+            radii = np.arange(16) * 0.1
+            ae2 = 1.0 - 2.5 * mu
+            cs2, mis = LT.fit_cs2(n1[:16][:, sel], radii, xi[sel], 1e-3, 0.47, 0.47, 0.0, ae2, ae2)
+            assert mis < 0.06, (closure, mu, mis)
+            fitted[closure, mu] = cs2
+    for mu in (0.01, 0.04):
+        lec, warmc = fitted["lec", mu], fitted["warmc", mu]
+        assert abs(lec / (5.0 * mu / 3.0) - 1.0) < 0.12, (mu, lec)
+        assert 1.4 < warmc / lec < 2.0, (mu, warmc, lec)
+    for closure in ("lec", "warmc"):
+        assert 3.0 < fitted[closure, 0.04] / fitted[closure, 0.01] < 5.0

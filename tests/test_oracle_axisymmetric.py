@@ -204,3 +204,15 @@ def test_axisymmetric_uniform_field_drives_a_uniform_oscillation():
     inner = uz[: nr - 20, 1:-1]
     assert abs(inner.mean()) > 1e-4
     assert np.abs(inner - inner.mean()).max() <= 1e-12 * abs(inner.mean())
+
+
+@pytest.mark.parametrize("cs2", [0.02, 0.07, 0.12])
+def test_cs2_fit_recovers_the_model_speed(cs2):
+    """The c_s^2 fit (Fig. 6 diagnostic) on a map that the Hankel solution
+    itself generated, at a_e^2 = 0.9: the generating value to 1e-3."""
+    radii = np.arange(0, 16) * 0.1
+    xi = np.arange(-6.0, 1.5, 0.1)
+    n1 = LT.hankel_n1(radii, xi, 1e-3, 0.47, 0.47, 0.0, cs2, 0.9, 0.9, nw=1500)
+    got, mis = LT.fit_cs2(n1, radii, xi, 1e-3, 0.47, 0.47, 0.0, 0.9, 0.9)
+    assert abs(got - cs2) <= 1e-3 * cs2 + 2e-5
+    assert mis < 1e-3
