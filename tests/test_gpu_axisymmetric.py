@@ -285,3 +285,29 @@ def test_axi_fp32_acoustic_speed_against_temperature():
         assert 1.4 < warmc / lec < 2.0, (mu, warmc, lec)
     for closure in ("lec", "warmc"):
         assert 3.0 < fitted[closure, 0.04] / fitted[closure, 0.01] < 5.0
+
+
+def test_axi_fp32_pressure_anisotropy_near_the_bunch():
+    """Fig. 7 on the GPU path: WARMC, mu = 0.04, Q~ = 0.5, 25 um bunch,
+    (z, r) grid of 30 x 6 k_p^-1 at dz = dr = 0.02, after the bunch has
+    travelled 20 k_p^-1.  Ahead of the bunch the plasma is at rest and
+    isotropic (P_par = P_perp); within 1.5 k_p^-1 of it |P_par / P_perp - 1|
+    is of the order of 10% (5-20%); 8-16 k_p^-1 behind it (away from where
+    the bunch started) it is smaller than at the bunch."""
+    sz = sr = 0.47
+    alpha = 0.5 / ((2 * np.pi) ** 1.5 * sz * sr * sr)
+    nz, nr, dx = 1500, 300, 0.02
+    cfg = _cfg("warmc", n=(nz, nr), dx=dx, mu=0.04, alpha=alpha, sigma_z=sz, sigma_r=sr, z0=4.0)
+    with lb.Run(cfg, "fp32") as run:
+        N = int(round(20.0 / run.info().dt))
+        run.step(N)
+        zd = 4.0 + N * run.info().dt
+        ppar, pperp = (v.reshape(nr, nz) for v in run.moments(lb.M_P_PAR | lb.M_P_PERP))
+    an = np.abs(ppar / pperp - 1.0)
+    xi = np.arange(nz) * dx - zd
+    near = an[:, np.abs(xi) < 1.5].max()
+    far = an[:, (xi >= -16.0) & (xi < -8.0) & (xi + zd > 9.0)].max()
+    ahead = an[:, xi > 2.0].max()
+    assert ahead < 1e-5
+    assert 0.05 < near < 0.20, near
+    assert far < near, (far, near)
