@@ -78,3 +78,10 @@ def test_invalid_parameters_rejected_before_any_device_work(lib_path):
     assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1
     assert lib.lbpwfa_create(None, ctypes.byref(h)) == -1
     assert lib.lbpwfa_step(None, 1) == -1
+    # the diagnostics check their handle and arguments on the host
+    fp = lbpwfa.FitParams()
+    out = (ctypes.c_double * 5)()
+    assert lib.lbpwfa_line_fit(None, ctypes.byref(fp), out) == -1
+    lo = (ctypes.c_int * 3)(0, 0, 0)
+    hi = (ctypes.c_int * 3)(1, 1, 1)
+    assert lib.lbpwfa_gauss_residual(None, lo, hi, out) == -1
