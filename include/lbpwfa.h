@@ -137,8 +137,9 @@ typedef struct {
                               in the slots of E_z, E_x, B_y; E_r = B_phi = 0
                               on the axis; (curl B)_z = d_r(r B_phi)/r.  The
                               1/r terms of App. A are added to the sources
-                              at r > 0.  Not available for batches or the
-                              adjoint (LBPWFA_ERR_INVALID). */
+                              at r > 0.  Batches may mix both geometries;
+                              the adjoint takes Cartesian runs only
+                              (LBPWFA_ERR_INVALID). */
 } lbpwfa_params;
 
 typedef struct {

@@ -19,17 +19,20 @@ __device__ __forceinline__ double batch_zeta0(double z0, long long s, double dt)
   return __dadd_rn(z0, __dmul_rn((double)s, dt));
 }
 
-template <int CL, int PR, int TZ, int TX>
+// AXI: an axisymmetric (z, r) run (the axis rules and 1/r sources of
+// step_body's AXI mode).
+template <int CL, int PR, int TZ, int TX, bool AXI>
 __device__ __forceinline__ void batch_item(const StepParams& P, unsigned char* smem, int tz, int tx) {
   using real = typename Prec<PR>::real;
-  GlobalPull<2, CL, PR> pull{P};
+  using Pull = GlobalPull<2, CL, PR, false, AXI>;
+  Pull pull{P};
   FieldPF<real> F;
   if (tile_is_bulk<2, TZ, TX, 1>(P, tz, tx, 0)) {
     prefetch_own<2, real, false, TZ, TX, 1>(P, F, tz, tx, 0);
-    step_body<2, CL, PR, TZ, TX, 1, false>(P, smem, pull, F, tz, tx, 0);
+    step_body<2, CL, PR, TZ, TX, 1, false, Pull, NoHook, false, AXI>(P, smem, pull, F, tz, tx, 0);
   } else {
     prefetch_own<2, real, true, TZ, TX, 1>(P, F, tz, tx, 0);
-    step_body<2, CL, PR, TZ, TX, 1, true>(P, smem, pull, F, tz, tx, 0);
+    step_body<2, CL, PR, TZ, TX, 1, true, Pull, NoHook, false, AXI>(P, smem, pull, F, tz, tx, 0);
   }
 }
 
@@ -45,7 +48,7 @@ template <int PR, int TZ, int TX, int CL>
 __global__ void __launch_bounds__(TZ* TX, (BatchCfg<PR, TZ, TX, CL>::MINB)) lb_step_batch_kernel(const BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) StepParams Ps;
-  __shared__ int s_ntz;
+  __shared__ int s_ntz, s_axi;
   const long long step = *A.step;
   const int parity = (int)(step & 1);
   // the CTA's items are mostly consecutive tiles of one run: the run's launch
@@ -69,12 +72,15 @@ __global__ void __launch_bounds__(TZ* TX, (BatchCfg<PR, TZ, TX, CL>::MINB)) lb_s
         Ps.cf.zeta0 = (float)z;
         Ps.have_prev = step > R->prev_from ? 1 : 0;
         s_ntz = R->ntz;
+        s_axi = R->axi;
       }
       __syncthreads();
       run = w.x;
     }
     const int tz = w.y % s_ntz, tx = w.y / s_ntz;
-    batch_item<CL, PR, TZ, TX>(Ps, smem_raw, tz, tx);
+    // the run's geometry is uniform over the CTA
+    if (s_axi) batch_item<CL, PR, TZ, TX, true>(Ps, smem_raw, tz, tx);
+    else batch_item<CL, PR, TZ, TX, false>(Ps, smem_raw, tz, tx);
     __syncthreads();  // Ps and the records are reused by the next item
     w = wn;
   }

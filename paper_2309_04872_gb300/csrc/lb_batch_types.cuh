@@ -11,7 +11,7 @@ struct BatchRun {
   long long prev_from;  // WARMC backward differences restart: active when step > prev_from
   int closure;      // CL_LEC or CL_WARMC
   int ntz, ntx;     // tiles along z and x
-  int pad_;
+  int axi;          // 1: axisymmetric (z, r) run
 };
 
 struct BatchArgs {

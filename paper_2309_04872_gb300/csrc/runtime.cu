@@ -1044,6 +1044,7 @@ int batch_build(lbpwfa_batch_s* b, const int* c) {
     R.dt = h->dt;
     R.prev_from = h->have_prev ? -1 : b->step;
     R.closure = cl;
+    R.axi = h->use_axi ? 1 : 0;
     R.ntz = (h->n[0] + tz - 1) / tz;
     R.ntx = (h->n[1] + tx - 1) / tx;
     for (int t = 0; t < R.ntz * R.ntx; ++t) items[cl].push_back(make_int2((int)i, t));
@@ -1230,8 +1231,7 @@ int lbpwfa_batch_create(const lbpwfa_params* p, int nruns, int flags, lbpwfa_bat
   for (int i = 0; i < nruns; ++i) {
     int st = validate(&p[i]);
     if (st != LBPWFA_OK) return st;
-    if (p[i].dim != 2 || p[i].precision != p[0].precision || p[i].geometry != LBPWFA_CARTESIAN)
-      return LBPWFA_ERR_INVALID;
+    if (p[i].dim != 2 || p[i].precision != p[0].precision) return LBPWFA_ERR_INVALID;
   }
   lbpwfa_batch_s* b = new lbpwfa_batch_s();
   b->precision = p[0].precision;

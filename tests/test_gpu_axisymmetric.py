@@ -140,10 +140,8 @@ def test_axi_lec_persistent_and_plain_agree(prec, n):
     assert dE <= tol * np.abs(outs[1][1]).max()
 
 
-def test_axi_rejects_batch_and_adjoint():
+def test_axi_rejects_the_adjoint():
     cfg = _cfg("lec")
-    with pytest.raises(Exception):
-        lb.Batch([cfg, cfg], "fp64")
     with lb.Run(cfg, "fp64") as run:
         with pytest.raises(Exception):
             run.record(10)

@@ -140,3 +140,46 @@ def test_batch_rejects_mixed_inputs():
         lb.Batch([runs[0], dict(runs[1], dim=3, n=(16, 16, 16))], "fp32")
     with pytest.raises(lb.LbpwfaError):
         lb.Batch(runs, "fp16s")
+
+
+def _mixed_geometry_runs():
+    """Axisymmetric (z, r) runs of both closures beside a Cartesian one."""
+    base = dict(dim=2, dx=0.05, courant=0.1, tau=0.53, dv=3, sigma_r=0.3, boundary="open", init_fields=True)
+    return [
+        dict(base, n=(131, 37), closure="lec", mu=4e-2, alpha=0.3, sigma_z=0.6, z0=2.0, geometry="axisymmetric"),
+        dict(base, n=(96, 40), closure="warmc", mu=4e-2, alpha=0.3, sigma_z=0.5, z0=1.5, geometry="axisymmetric"),
+        dict(base, n=(77, 45), closure="lec", mu=1e-2, alpha=0.2, sigma_z=0.6, z0=1.2),
+    ]
+
+
+def test_batch_axisymmetric_members_match_single_runs():
+    """Axisymmetric and Cartesian runs in one batch (the per-run geometry
+    picks the step body): FP32 members agree with the single runs' plain
+    kernels to round-off after 70 steps."""
+    runs = _mixed_geometry_runs()
+    with lb.Batch(runs, "fp32", tune=False) as b:
+        b.step(70)
+        got = [(m.advected(), m.fields()) for m in b.members]
+    for cfg, (A, F) in zip(runs, got):
+        with lb.Run(cfg, "fp32", variant=1) as r:
+            r.step(70)
+            rest = O.Oracle(cfg).rest_advected()
+            _same_to_roundoff(A, r.advected(), rest, "advected")
+            _same_to_roundoff(F, r.fields(), None, "fields")
+
+
+def test_batch_axisymmetric_fp64_matches_oracle():
+    runs = _mixed_geometry_runs()
+    with lb.Batch(runs, "fp64", tune=False) as b:
+        b.step(40)
+        for cfg, m in zip(runs, b.members):
+            o = O.Oracle(cfg)
+            o.step(40)
+            A = m.advected()
+            Ao = o.advected()
+            rest = o.rest_advected()
+            for k in range(o.K):
+                d = np.linalg.norm(A[k] - Ao[k])
+                assert d <= 1e-12 * np.linalg.norm(Ao[k]) + 1e-13 * np.sqrt(Ao[k].size)
+                if rest[k] != 0:
+                    assert d <= 1e-9 * np.linalg.norm(Ao[k] - rest[k]) + 1e-13 * abs(rest[k]) * np.sqrt(Ao[k].size)
