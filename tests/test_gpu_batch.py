@@ -183,3 +183,34 @@ def test_batch_axisymmetric_fp64_matches_oracle():
                 assert d <= 1e-12 * np.linalg.norm(Ao[k]) + 1e-13 * np.sqrt(Ao[k].size)
                 if rest[k] != 0:
                     assert d <= 1e-9 * np.linalg.norm(Ao[k] - rest[k]) + 1e-13 * abs(rest[k]) * np.sqrt(Ao[k].size)
+
+
+def test_batched_temperature_sweep_acoustic_speed():
+    """Fig. 6 as one batched sweep: six axisymmetric runs (mu = 0.01, 0.02,
+    0.04, both closures; FP32) advanced together, c_s^2 fitted from each
+    member's wake map with App. B's Hankel solution.  LEC within 12% of
+    5 mu / 3 (its O(mu) form), the WARMC faster than the LEC at every mu,
+    c_s^2 increasing with mu for both."""
+    from oracle import linear_theory as LT
+    mus = (0.01, 0.02, 0.04)
+    runs = [dict(dim=2, n=(160, 50), dx=0.1, courant=0.15, tau=0.505, closure=cl, dv=3, mu=mu, alpha=1e-3,
+                 sigma_z=0.47, sigma_r=0.47, z0=3.0, boundary="open", init_fields=True, geometry="axisymmetric")
+            for cl in ("lec", "warmc") for mu in mus]
+    N = int(round(11.0 / (0.15 * 0.1)))
+    with lb.Batch(runs, "fp32", tune=False) as b:
+        b.step(N)
+        maps = [m.moments(lb.M_N)[0].reshape(50, 160) - 1.0 for m in b.members]
+    xi = np.arange(160) * 0.1 - (3.0 + N * 0.015)
+    sel = (xi > -6.0) & (xi < 1.5)
+    radii = np.arange(16) * 0.1
+    cs2 = {}
+    for cfg, n1 in zip(runs, maps):
+        ae2 = 1.0 - 2.5 * cfg["mu"]
+        c, mis = LT.fit_cs2(n1[:16][:, sel], radii, xi[sel], 1e-3, 0.47, 0.47, 0.0, ae2, ae2)
+        assert mis < 0.06, (cfg["closure"], cfg["mu"], mis)
+        cs2[cfg["closure"], cfg["mu"]] = c
+    for mu in mus:
+        assert abs(cs2["lec", mu] / (5.0 * mu / 3.0) - 1.0) < 0.12, (mu, cs2["lec", mu])
+        assert cs2["warmc", mu] > 1.3 * cs2["lec", mu], mu
+    for cl in ("lec", "warmc"):
+        assert cs2[cl, 0.01] < cs2[cl, 0.02] < cs2[cl, 0.04]
