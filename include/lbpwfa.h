@@ -357,8 +357,9 @@ typedef struct {
 } lbpwfa_batch_info_t;
 
 /* Create nruns >= 1 runs from p[0..nruns-1], each validated as by
- * lbpwfa_create.  Every run must be 2D with the same precision; closures,
- * grids and driver parameters may differ.  flags bit 0: skip the autotuner
+ * lbpwfa_create.  Every run must be 2D with the same precision (FP64, FP32
+ * or FP16S storage); closures, geometries, grids and driver parameters may
+ * differ.  flags bit 0: skip the autotuner
  * (use the first candidate tile).  The autotuner times each candidate tile,
  * closure by closure, over a few steps and restores the rest state; when the environment
  * variable LBPWFA_TUNE_CACHE names a JSON file, choices are read from and

@@ -1,55 +1,18 @@
-// Instances of the batched step kernel: FP32 and FP64 storage, each closure,
-// three candidate tiles for the autotuner.
+// Dispatch of the batched step kernels (instances in lb_batch_f32.cu,
+// lb_batch_f64.cu, lb_batch_f16s.cu) and the step counter.
 #include "lb_batch.cuh"
 #include "lb_batch_dispatch.h"
 
 namespace lbp {
 
-namespace {
-template <int PR, int TZ, int TX, int CL>
-struct BatchImpl {
-  using Cfg = BatchCfg<PR, TZ, TX, CL>;
-  static cudaError_t prepare() {
-    return cudaFuncSetAttribute(lb_step_batch_kernel<PR, TZ, TX, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Cfg::smem_bytes);
-  }
-  static void launch(const BatchArgs& A, int grid, cudaStream_t s) {
-    lb_step_batch_kernel<PR, TZ, TX, CL><<<grid, TZ * TX, Cfg::smem_bytes, s>>>(A);
-  }
-  static int occupancy() {
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lb_step_batch_kernel<PR, TZ, TX, CL>, TZ * TX, Cfg::smem_bytes);
-    return n;
-  }
-};
-
-template <int PR, int CL>
-void fill_closure(BatchKernelSet* ks, int c) {
-  ks->prepare[c][0] = &BatchImpl<PR, 32, 8, CL>::prepare;
-  ks->prepare[c][1] = &BatchImpl<PR, 64, 4, CL>::prepare;
-  ks->prepare[c][2] = &BatchImpl<PR, 16, 16, CL>::prepare;
-  ks->launch[c][0] = &BatchImpl<PR, 32, 8, CL>::launch;
-  ks->launch[c][1] = &BatchImpl<PR, 64, 4, CL>::launch;
-  ks->launch[c][2] = &BatchImpl<PR, 16, 16, CL>::launch;
-  ks->occupancy[c][0] = &BatchImpl<PR, 32, 8, CL>::occupancy;
-  ks->occupancy[c][1] = &BatchImpl<PR, 64, 4, CL>::occupancy;
-  ks->occupancy[c][2] = &BatchImpl<PR, 16, 16, CL>::occupancy;
-}
-
-template <int PR>
-void fill(BatchKernelSet* ks) {
-  ks->ncand = 3;
-  ks->tz[0] = 32; ks->tx[0] = 8;
-  ks->tz[1] = 64; ks->tx[1] = 4;
-  ks->tz[2] = 16; ks->tx[2] = 16;
-  fill_closure<PR, CL_LEC>(ks, CL_LEC);
-  fill_closure<PR, CL_WARMC>(ks, CL_WARMC);
-}
-}  // namespace
+void batch_kernels_f32(BatchKernelSet* ks);
+void batch_kernels_f64(BatchKernelSet* ks);
+void batch_kernels_f16s(BatchKernelSet* ks);
 
 bool batch_kernels(int precision, BatchKernelSet* ks) {
-  if (precision == PR_F32) { fill<PR_F32>(ks); return true; }
-  if (precision == PR_F64) { fill<PR_F64>(ks); return true; }
+  if (precision == PR_F32) { batch_kernels_f32(ks); return true; }
+  if (precision == PR_F64) { batch_kernels_f64(ks); return true; }
+  if (precision == PR_F16S) { batch_kernels_f16s(ks); return true; }
   return false;
 }
 

@@ -39,9 +39,9 @@ __device__ __forceinline__ void batch_item(const StepParams& P, unsigned char* s
 template <int PR, int TZ, int TX, int CL>
 struct BatchCfg {
   static constexpr size_t smem_bytes = StepCfg<2, CL, PR, TZ, TX, 1>::smem_bytes;
-  // resident CTAs the register budget is held to in FP32: three for LEC (as
-  // the single-run LEC kernel runs), two for WARMC
-  static constexpr int MINB = PR == PR_F32 ? (CL == CL_LEC ? 3 : 2) : 1;
+  // resident CTAs the register budget is held to in FP32 and FP16S: three
+  // for LEC (as the single-run LEC kernel runs), two for WARMC
+  static constexpr int MINB = (PR == PR_F32 || PR == PR_F16S) ? (CL == CL_LEC ? 3 : 2) : 1;
 };
 
 template <int PR, int TZ, int TX, int CL>

@@ -1235,9 +1235,10 @@ int lbpwfa_batch_create(const lbpwfa_params* p, int nruns, int flags, lbpwfa_bat
   }
   lbpwfa_batch_s* b = new lbpwfa_batch_s();
   b->precision = p[0].precision;
-  if (!batch_kernels(b->precision == LBPWFA_FP64 ? PR_F64 : (b->precision == LBPWFA_FP32 ? PR_F32 : -1), &b->bk)) {
+  const int bpr = b->precision == LBPWFA_FP64 ? PR_F64 : (b->precision == LBPWFA_FP32 ? PR_F32 : PR_F16S);
+  if (!batch_kernels(bpr, &b->bk)) {
     delete b;
-    return LBPWFA_ERR_INVALID;  // batched FP16S storage is not built
+    return LBPWFA_ERR_INVALID;
   }
   if (p[0].stream) {
     b->stream = (cudaStream_t)p[0].stream;

@@ -138,8 +138,25 @@ def test_batch_rejects_mixed_inputs():
     runs = _runs()
     with pytest.raises(lb.LbpwfaError):
         lb.Batch([runs[0], dict(runs[1], dim=3, n=(16, 16, 16))], "fp32")
-    with pytest.raises(lb.LbpwfaError):
-        lb.Batch(runs, "fp16s")
+
+
+def test_batch_fp16s_members_match_single_runs():
+    """FP16-shifted storage in a batch (Cartesian and axisymmetric runs):
+    members agree with the single runs' plain kernels to the storage's
+    round-off, 1e-3 of each set's largest deviation after 70 steps (a fused
+    multiply-add taken differently can flip one binary16 rounding)."""
+    runs = _runs()[:2] + _mixed_geometry_runs()[:2]
+    with lb.Batch(runs, "fp16s", tune=False) as b:
+        b.step(70)
+        got = [m.advected() for m in b.members]
+    for cfg, A in zip(runs, got):
+        with lb.Run(cfg, "fp16s", variant=1) as r:
+            r.step(70)
+            ref = r.advected()
+        rest = O.Oracle(cfg).rest_advected()
+        for k in range(ref.shape[0]):
+            scale = np.abs(ref[k] - rest[k]).max()
+            assert np.abs(A[k] - ref[k]).max() <= 1e-3 * scale + 1e-30, (cfg["closure"], k)
 
 
 def _mixed_geometry_runs():
