@@ -520,27 +520,28 @@ def _configs(stream, flush, hbm):
                                    "note": "state is L2-resident and launch-bound; no flush"}
     # the batched sweep: 64 uneven 2D runs, both closures, one launch per closure and step
     draws, cfgs = _batch_cfgs(64)
-    with lb.Batch(cfgs, "fp32", stream=stream.cuda_stream, tune=True) as b:
-        info = b.info()
-        b.step(32)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.step(96)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / 96
-        gbs = info.bytes_per_step / (ms * 1e-3) / 1e9
-        nlec = sum(1 for d in draws if d["closure"] == "lec")
-        res["batch_64x2d_fp32"] = {
-            "mlups": round(info.ncell / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
-            "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
-            "nodes": int(info.ncell), "runs": 64, "lec_runs": nlec, "warmc_runs": 64 - nlec,
-            "tile": {"lec": list(info.tile[0]), "warmc": list(info.tile[1])},
-            "tuned_ms": {"lec": [round(v, 4) for v in info.tuned_ms[0] if v > 0],
-                         "warmc": [round(v, 4) for v in info.tuned_ms[1] if v > 0]},
-            "graph_steps": info.graph_steps, "steps": 96, "kernel": "lb_step_batch_kernel",
-            "l2": "state larger than L2 (no flush)"}
+    for bprec in ("fp32", "fp16s"):
+        with lb.Batch(cfgs, bprec, stream=stream.cuda_stream, tune=True) as b:
+            info = b.info()
+            b.step(32)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(96)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 96
+            gbs = info.bytes_per_step / (ms * 1e-3) / 1e9
+            nlec = sum(1 for d in draws if d["closure"] == "lec")
+            res[f"batch_64x2d_{bprec}"] = {
+                "mlups": round(info.ncell / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
+                "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
+                "nodes": int(info.ncell), "runs": 64, "lec_runs": nlec, "warmc_runs": 64 - nlec,
+                "tile": {"lec": list(info.tile[0]), "warmc": list(info.tile[1])},
+                "tuned_ms": {"lec": [round(v, 4) for v in info.tuned_ms[0] if v > 0],
+                             "warmc": [round(v, 4) for v in info.tuned_ms[1] if v > 0]},
+                "graph_steps": info.graph_steps, "steps": 96, "kernel": "lb_step_batch_kernel",
+                "l2": "state larger than L2 (no flush)"}
     # the axisymmetric 3D3V grid, both closures
     for closure in ("warmc", "lec"):
         for prec in ("fp32", "fp16s", "fp64"):
