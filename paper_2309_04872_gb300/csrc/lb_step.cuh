@@ -86,7 +86,7 @@ struct StepCfg {
   // instead of pulling them again (2D WARMC 4.2 -> 5.6 GLUPS; in FP16S, and
   // in the batch kernel, measured slower); its launch reserves
   // smem_bytes_gkeep
-  static constexpr bool SKEEP_OK = DIM == 2 && M::K * M::Q > 32 && PR == PR_F32;
+  static constexpr bool SKEEP_OK = false;
   static constexpr int NKEEP = SKEEP_OK ? M::K * M::Q * NT : 0;
   static constexpr size_t smem_bytes_gkeep = smem_bytes + (size_t)NKEEP * sizeof(real);
   __host__ __device__ static constexpr int stride(int a) { return a == 0 ? 1 : (a == 1 ? RZ : RZ * RX); }
@@ -1056,8 +1056,17 @@ __device__ __forceinline__ void prefetch_own(const StepParams& P, FieldPF<real>&
 
 // Plain variant: populations pulled straight from global memory (any
 // dimension, open or periodic boundaries).
+// Resident CTAs the register budget of the plain kernel is held to: the 2D
+// WARMC in reduced precision runs three per SM (85 registers), which hides
+// more of its pull latency than two with its 72 own populations kept in
+// shared memory (1024 x 512, FP32: 5.94 against 5.67 GLUPS).
+template <int DIM, int CL, int PR>
+struct PlainMinBlocks {
+  static constexpr int value = (DIM == 2 && CL == CL_WARMC && PR != PR_F64) ? 3 : 1;
+};
+
 template <int DIM, int CL, int PR, int TZ, int TX, int TY>
-__global__ void __launch_bounds__(TZ* TX* TY)
+__global__ void __launch_bounds__(TZ* TX* TY, (PlainMinBlocks<DIM, CL, PR>::value))
 lb_step_kernel(const __grid_constant__ StepParams P) {
   using real = typename Prec<PR>::real;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1077,7 +1086,8 @@ lb_step_kernel(const __grid_constant__ StepParams P) {
 // Axisymmetric (z, r) step: the plain 2D kernel with the AXI rules of
 // step_body (r = 0 boundary node, cylindrical curl and 1/r sources).
 template <int CL, int PR, int TZ, int TX>
-__global__ void __launch_bounds__(TZ* TX) lb_step_axi_kernel(const __grid_constant__ StepParams P) {
+__global__ void __launch_bounds__(TZ* TX, (PlainMinBlocks<2, CL, PR>::value))
+lb_step_axi_kernel(const __grid_constant__ StepParams P) {
   using real = typename Prec<PR>::real;
   using Pull = GlobalPull<2, CL, PR, StepCfg<2, CL, PR, TZ, TX, 1>::SKEEP_OK, true>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
