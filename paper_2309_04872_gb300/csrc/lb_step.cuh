@@ -80,12 +80,12 @@ struct StepCfg {
   static constexpr int NHALO_E = DIM == 2 ? (TZ + 1) * (TX + 1) - TZ * TX : 0;
   static constexpr int NSTAGE = NHALO_E * (CF ? 10 : 5);
   static constexpr size_t smem_bytes = ((size_t)(M::NM + NE_SLOTS) * NR + NDRV + NSCR + NSTAGE) * sizeof(real);
-  // 2D sets too wide for registers (WARMC, K*Q = 72) in FP32 storage: the
-  // single-run kernel, which pulls from global memory, keeps the own node's
-  // populations in a shared-memory column [K*Q][NT] for the collision
-  // instead of pulling them again (2D WARMC 4.2 -> 5.6 GLUPS; in FP16S, and
-  // in the batch kernel, measured slower); its launch reserves
-  // smem_bytes_gkeep
+  // Sets too wide for registers (2D WARMC, K*Q = 72) could keep the own
+  // node's populations in a shared-memory column [K*Q][NT] for the
+  // collision instead of pulling them again (launch reserving
+  // smem_bytes_gkeep).  Off: it holds the kernel to two CTAs per SM, and
+  // three CTAs per SM that pull again measure faster (1024 x 512 FP32: 5.94
+  // against 5.67 GLUPS; 4.2 with neither).
   static constexpr bool SKEEP_OK = false;
   static constexpr int NKEEP = SKEEP_OK ? M::K * M::Q * NT : 0;
   static constexpr size_t smem_bytes_gkeep = smem_bytes + (size_t)NKEEP * sizeof(real);
