@@ -1059,10 +1059,12 @@ __device__ __forceinline__ void prefetch_own(const StepParams& P, FieldPF<real>&
 // Resident CTAs the register budget of the plain kernel is held to: the 2D
 // WARMC in reduced precision runs three per SM (85 registers), which hides
 // more of its pull latency than two with its 72 own populations kept in
-// shared memory (1024 x 512, FP32: 5.94 against 5.67 GLUPS).
+// shared memory (1024 x 512, FP32: 5.94 against 5.67 GLUPS).  0 leaves the
+// budget to the compiler, as a bound without a block count does (writing 1
+// instead changes its register choice: FP64 2D WARMC 181 -> 255).
 template <int DIM, int CL, int PR>
 struct PlainMinBlocks {
-  static constexpr int value = (DIM == 2 && CL == CL_WARMC && PR != PR_F64) ? 3 : 1;
+  static constexpr int value = (DIM == 2 && CL == CL_WARMC && PR != PR_F64) ? 3 : 0;
 };
 
 template <int DIM, int CL, int PR, int TZ, int TX, int TY>
