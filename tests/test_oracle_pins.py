@@ -12,7 +12,7 @@ import pytest
 from scipy.optimize import curve_fit
 
 import oracle as O
-from tests import inputs
+from tests import inputs, paper_values
 
 
 # ---------------------------------------------------------------------------
@@ -417,7 +417,7 @@ def test_warm_dispersion_1d3v(closure, mu):
     assert abs(k2_cold - 1.0) < 2e-4
     amp, k, ph, *_ = _wake_1d(mu, 1e-3, closure=closure, dv=3, C=0.25)
     shift = k * k - k2_cold
-    paper = -5 * mu / 6 if closure == "lec" else mu / 2
+    paper = float(paper_values.dispersion()[closure][2]) * mu
     assert abs(shift - paper) < 2.5 * mu * mu
     # sign of the thermal correction: LEC lengthens, WARMC shortens the wave
     if closure == "lec":
