@@ -21,7 +21,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbpwfa_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
-_LIB_PATH = os.path.join(_BUILD, "liblbpwfa_oracle.so")
+# ORC_PLANT=n builds and loads a copy of the oracle with planted mistake n
+# (the PLANTED sites of the C file), for the test that the pins catch it
+_PLANT = os.environ.get("ORC_PLANT", "").strip()
+if _PLANT and not _PLANT.isdigit():
+    raise ValueError(f"ORC_PLANT must be a mistake number, not {_PLANT!r}")
+_LIB_PATH = os.path.join(_BUILD, f"liblbpwfa_oracle_plant{_PLANT}.so" if _PLANT else "liblbpwfa_oracle.so")
 _lib = None
 
 LEC, WARMC = 0, 1
@@ -38,7 +43,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fopenmp",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"] + ([f"-DORC_PLANT={_PLANT}"] if _PLANT else [])
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

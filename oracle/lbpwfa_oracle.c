@@ -55,6 +55,15 @@
 
 #include "lbpwfa_oracle.h"
 
+/* Planted mistakes, for the test that the pins catch each of them (tests/
+ * test_oracle_mutants.py builds the oracle once per mistake with
+ * -DORC_PLANT=n).  Without that define PLANTED(n, right, wrong) is `right`
+ * and the oracle is exactly the scheme as written. */
+#ifndef ORC_PLANT
+#define ORC_PLANT 0
+#endif
+#define PLANTED(n, right, wrong) (ORC_PLANT == (n) ? (wrong) : (right))
+
 #define ORC_MAXQ 19
 
 typedef struct {
@@ -140,7 +149,7 @@ static double feq_one(double wi, double A, const int* xi, const double* ul)
   double cu = xi[0] * ul[0] + xi[1] * ul[1] + xi[2] * ul[2];
   double usq = ul[0] * ul[0] + ul[1] * ul[1] + ul[2] * ul[2];
   double nu2 = 1.0 / 3.0;
-  return wi * A * (1.0 + cu / nu2 + (cu * cu) / (2.0 * nu2 * nu2) - usq / (2.0 * nu2));
+  return wi * A * (1.0 + cu / nu2 + (cu * cu) / PLANTED(1, 2.0 * nu2 * nu2, nu2 * nu2) - usq / (2.0 * nu2));
 }
 
 void orc_equilibrium(int dim, double A, const double* u_phys, double courant, double* feq)
@@ -166,7 +175,7 @@ int orc_decode_lec(int Ds, int D, double mu, const double* A,
   int it;
   for (it = 0; it < 64; ++it) {
     double g = sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-    double H = 1.0 + (1.0 + 0.5 * D) * mu * pow(n / g, e);
+    double H = 1.0 + PLANTED(8, 1.0 + 0.5 * D, 1.0 + 2.0 / D) * mu * pow(n / g, e);
     double dmax = 0.0, pmax = 0.0;
     for (int a = 0; a < 3; ++a) {
       double pn = p0[a] / H;
@@ -249,7 +258,7 @@ void orc_lec_source(double mu, double n, const double* u, const double* gradPi,
     double uxB = 0.0;
     for (int k = 0; k < 3; ++k)
       for (int l = 0; l < 3; ++l) uxB += eps3(a, k, l) * u[k] * B[l];
-    Fp[a] = -mu * gradPi[a] - n * (E[a] + uxB);
+    Fp[a] = -mu * gradPi[a] - n * (E[a] + PLANTED(5, uxB, -uxB));
   }
 }
 
@@ -285,7 +294,7 @@ void orc_warmc_source(double n, const double* u, const double* th /*[3][3]*/,
       double em = E[a] * th0[b] + E[b] * th0[a];
       for (int k = 0; k < 3; ++k)
         for (int l = 0; l < 3; ++l)
-          em += eps3(a, k, l) * th[b * 3 + k] * B[l] + eps3(b, k, l) * th[a * 3 + k] * B[l];
+          em += eps3(a, k, l) * th[b * 3 + k] * B[l] + PLANTED(6, eps3(b, k, l) * th[a * 3 + k] * B[l], 0.0);
       F_th[a * 3 + b] = s - em;
     }
 }
@@ -780,7 +789,8 @@ static void forward_stages(orc_state* S)
       if (a == 0 && axi(S)) {
         /* (curl B)_z = (1/r) d_r (r B_phi) at r_{j+1/2}, B_phi at r_j, r_{j+1} */
         double rl = i[1] * dx, rh = rl + dx, rm = rl + 0.5 * dx;
-        curl += (rh * S->B[(long)d * nc + nb_node(S, c, b, +1)] - rl * S->B[(long)d * nc + c]) / (rm * dx);
+        curl += PLANTED(9, (rh * S->B[(long)d * nc + nb_node(S, c, b, +1)] - rl * S->B[(long)d * nc + c]) / (rm * dx),
+                        (S->B[(long)d * nc + nb_node(S, c, b, +1)] - S->B[(long)d * nc + c]) / dx);
       } else if (present(S, b) && B_present(S, d))
         curl += (S->B[(long)d * nc + nb_node(S, c, b, +1)] - S->B[(long)d * nc + c]) / dx;
       if (present(S, d) && B_present(S, b))
@@ -802,7 +812,7 @@ static void forward_stages(orc_state* S)
         for (int j = 0; j < no; ++j) q[off[j]] += 0.5 * dx;
         J += driver_density(p, q[0], q[1], q[2], t);
       }
-      S->En[ia] = S->E[ia] + dt * (curl + J);
+      S->En[ia] = S->E[ia] + dt * PLANTED(3, curl + J, curl - J);
     }
   }
 
@@ -819,7 +829,7 @@ static void forward_stages(orc_state* S)
         curl += (Eget(S, S->En, d, c) - Eget(S, S->En, d, nb_E(S, c, b, -1))) / dx;
       if (present(S, d) && E_present(S, b))
         curl -= (Eget(S, S->En, b, c) - Eget(S, S->En, b, nb_E(S, c, d, -1))) / dx;
-      S->Bn[ia] = S->B[ia] - dt * curl;
+      S->Bn[ia] = S->B[ia] + PLANTED(4, -dt, dt) * curl;
     }
   }
 
@@ -878,13 +888,13 @@ static void forward_stages(orc_state* S)
           double A[3] = {0, 0, 0};
           for (int k = 0; k < K; ++k)
             for (int i = 0; i < Q; ++i) A[k] += S->f[((size_t)k * Q + i) * nc + c];
-          for (int k = 0; k < K; ++k) Fk[k] += -ur * A[k] / r;
+          for (int k = 0; k < K; ++k) Fk[k] += PLANTED(11, -ur, ur) * A[k] / r;
         } else {
           double n = m->n, nl = m->n * m->lam;
           Fk[0] += -n * ur / r;
           Fk[1] += -nl * ur / r - m->th0[1] / r;
           Fk[2] += -nl * m->u[0] * ur / r - m->th[0][1] / r;        /* n lambda u_z */
-          Fk[3] += -nl * ur * ur / r - (m->th[1][1] - m->th[2][2]) / r;  /* n lambda u_r */
+          Fk[3] += -nl * ur * ur / r - PLANTED(10, m->th[1][1] - m->th[2][2], m->th[1][1] + m->th[2][2]) / r;  /* n lambda u_r */
           for (int j = 0; j < S->ntheta; ++j) {
             int a = S->thpair[j][0], b = S->thpair[j][1];
             double coef = (a == 2 && b == 2) ? 3.0 : 1.0;  /* lambda theta^{phi phi}: 3 */
@@ -909,7 +919,7 @@ static void forward_stages(orc_state* S)
       for (int i = 0; i < Q; ++i) {
         size_t ix = ((size_t)k * Q + i) * nc + c;
         double fe = feq_one(S->w[i], A, S->xi[i], ul);
-        S->fs[ix] = S->f[ix] - (S->f[ix] - fe) / tau + S->w[i] * dt * S->F[(long)k * nc + c];
+        S->fs[ix] = S->f[ix] - (S->f[ix] - fe) / tau + S->w[i] * PLANTED(7, dt, 1.0) * S->F[(long)k * nc + c];
       }
     }
   }
@@ -932,7 +942,7 @@ static void finish_step(orc_state* S)
         int ii = boundary_dir(S, c, k, i);
         int src[3] = {ib[0], ib[1], ib[2]};
         for (int a = 0; a < S->p.dim; ++a) {
-          int v = src[a] - S->xi[ii][a], n = S->n[a];
+          int v = PLANTED(2, src[a] - S->xi[ii][a], src[a] + S->xi[ii][a]), n = S->n[a];
           if (p->boundary == ORC_PERIODIC) v = ((v % n) + n) % n;
           src[a] = v;
         }
@@ -1269,7 +1279,7 @@ static void adj_step(orc_state* S, orc_adj* J, double* g3, double* gp)
         double l = J->lF[(long)(1 + a) * nc + c];
         if (l == 0.0) continue;
         long cp = nb_node(S, c, a, +1), cm = nb_node(S, c, a, -1);
-        J->lm[cp].Pi -= p->mu * l / (2.0 * dx);
+        J->lm[cp].Pi -= PLANTED(12, 1.0, -1.0) * p->mu * l / (2.0 * dx);
         J->lm[cm].Pi += p->mu * l / (2.0 * dx);
         double uxB = 0.0;
         for (int k = 0; k < 3; ++k)
@@ -1281,7 +1291,7 @@ static void adj_step(orc_state* S, orc_adj* J, double* g3, double* gp)
             lBn[q] -= m->n * e3 * m->u[k] * l;
           }
         lm->n -= (En[a] + uxB) * l;
-        lEn[a] -= m->n * l;
+        lEn[a] -= PLANTED(13, m->n, 0.0) * l;
       }
     } else {
       double lnl = J->lF[1 * nc + c];
