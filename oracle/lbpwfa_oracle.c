@@ -217,7 +217,7 @@ void orc_decode_warmc(int dim, const double* A, double* out /* see header */)
   double n = A[0], nl = A[1];
   double lam = nl / n;
   double u[3] = {0, 0, 0};
-  for (int a = 0; a < Ds; ++a) u[a] = A[2 + a] / nl;
+  for (int a = 0; a < Ds; ++a) u[a] = A[2 + a] / PLANTED(15, nl, n);
   double th[3][3] = {{0}};
   for (int j = 0; j < np; ++j) {
     double v = A[2 + Ds + j] / lam;
@@ -326,7 +326,7 @@ static double driver_long(const orc_params* p, double zeta)
 
 static double driver_density(const orc_params* p, double z, double x, double y, double t)
 {
-  double L = driver_long(p, z - p->z0 - t);
+  double L = driver_long(p, z - p->z0 + PLANTED(14, -t, t));
   double r2 = 0.0;
   if (p->dim >= 2) r2 += x * x;
   if (p->dim >= 3) r2 += y * y;

@@ -45,6 +45,10 @@ MUTANTS = {
          [J + "test_adjoint_driver_parameters", J + "test_adjoint_starting_state"]),
     13: ("adjoint: the electric-field adjoint of the LEC Lorentz force dropped",
          [J + "test_adjoint_driver_parameters", J + "test_adjoint_starting_state"]),
+    14: ("driver: the bunch moving towards -z (Eq. bunch-density, zeta = z - z0 - t)",
+         [P + "test_driver_normalised_charge"]),
+    15: ("WARMC decode: u^a from n lambda u^a divided by n instead of n lambda (Eq. lb-ade-warmc-comps-A)",
+         [P + "test_warmc_decode_identities"]),
 }
 
 
