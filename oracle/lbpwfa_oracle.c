@@ -1186,7 +1186,7 @@ static void adj_decode_warmc(const orc_state* S, long c, const double* A, const 
   /* theta_pair = A_theta n / A_1 */
   for (int j = 0; j < S->ntheta; ++j) {
     int a = S->thpair[j][0], b = S->thpair[j][1];
-    double l = lm->th[a][b] + (a != b ? lm->th[b][a] : 0.0);
+    double l = lm->th[a][b] + (a != b ? PLANTED(16, lm->th[b][a], 0.0) : 0.0);
     double At = A[2 + Ds + j];
     lA[(long)(2 + Ds + j) * nc + c] += l * n / nl;
     lA[c] += l * At / nl;

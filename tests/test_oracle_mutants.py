@@ -49,6 +49,8 @@ MUTANTS = {
          [P + "test_driver_normalised_charge"]),
     15: ("WARMC decode: u^a from n lambda u^a divided by n instead of n lambda (Eq. lb-ade-warmc-comps-A)",
          [P + "test_warmc_decode_identities"]),
+    16: ("adjoint WARMC decode: an off-diagonal theta pair's adjoint without its transposed entry",
+         [J + "test_adjoint_driver_parameters", J + "test_adjoint_starting_state"]),
 }
 
 
