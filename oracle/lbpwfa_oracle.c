@@ -864,7 +864,7 @@ static void forward_stages(orc_state* S)
       if (S->have_prev) {
         dth00_dt = (m->th00 - S->prev[0 * nc + c]) / dt;
         for (int a = 0; a < 3; ++a) {
-          dth0_dt[a] = (m->th0[a] - S->prev[(long)(1 + a) * nc + c]) / dt;
+          dth0_dt[a] = PLANTED(17, (m->th0[a] - S->prev[(long)(1 + a) * nc + c]) / dt, 0.0);
           dw_dt[a] = (m->w[a] - S->prev[(long)(4 + a) * nc + c]) / dt;
         }
       }

@@ -51,6 +51,8 @@ MUTANTS = {
          [P + "test_warmc_decode_identities"]),
     16: ("adjoint WARMC decode: an off-diagonal theta pair's adjoint without its transposed entry",
          [J + "test_adjoint_driver_parameters", J + "test_adjoint_starting_state"]),
+    17: ("WARMC source: the backward time derivative of theta^{0a} dropped from the n lambda u row",
+         [P + "test_warm_dispersion_1d3v"]),
 }
 
 
