@@ -393,8 +393,11 @@ def run_ours(a):
             bad = run.reduce()[2]
         mean_ms = sum(times) / len(times)
         mlups = info.ncell / (mean_ms * 1e-3) / 1e6
-        gbs = info.bytes_per_update * info.ncell / (mean_ms * 1e-3) / 1e9
-        return dict(mlups=mlups, ms=mean_ms, gbs=gbs, frac=gbs / hbm, bytes_per_update=info.bytes_per_update,
+        gbs = info.algorithmic_bytes_per_update * info.ncell / (mean_ms * 1e-3) / 1e9
+        stored = info.bytes_per_update * info.ncell / (mean_ms * 1e-3) / 1e9
+        return dict(mlups=mlups, ms=mean_ms, gbs=gbs, frac=gbs / hbm,
+                    bytes_per_update=info.algorithmic_bytes_per_update,
+                    stored_bytes_per_update=info.bytes_per_update, stored_gbs=stored,
                     ncell=info.ncell, total_ms=sum(times), nonfinite=bad, times=times,
                     kernel=KERNEL_NAMES[info.kernel_variant])
 
@@ -424,12 +427,38 @@ def run_ours(a):
             "frac": round(main["frac"], 4),
             "traffic": _traffic_for(f"{main['kernel']}:{_config_block(cfg, a.precision)['workload']}"),
             "bytes_per_update": main["bytes_per_update"], "peak_source": f"{peak_kind} hbm_gbs",
+            "bytes_note": "algorithmic bytes per node update (2 K Q s populations + 2 x 3 field components "
+                          "x 4 B); achieved = bytes_per_update x nodes / mean CUDA-event step time",
+            "stored_bytes_per_update": main["stored_bytes_per_update"],
+            "stored_frac": round(main["stored_gbs"] / hbm, 4),
         },
         "clocks": clocks,
         "gpu_launches": a.steps,
     }
     if main["nonfinite"]:
         out["warning"] = "non-finite populations at the end of the timed run"
+
+    fp64_peak = None
+    if rank == 0 and not a.no_modes:
+        fp64_peak = lb.measure_fp64_rate()
+        out["fp64_peak"] = {"value_tflops": round(fp64_peak / 1e12, 4), "source":
+                            "lbpwfa_measure_fp64_rate (independent DFMA chains, CUDA events, this GPU)"}
+
+    def mode_entry(r, steps, workload):
+        e = {"mlups": round(r["mlups"], 2), "ms_per_step": round(r["ms"], 5),
+             "achieved_gbs": round(r["gbs"], 1), "frac_of_measured_hbm": round(r["frac"], 4),
+             "bytes_per_update": r["bytes_per_update"], "stored_bytes_per_update": r["stored_bytes_per_update"],
+             "steps": steps, "kernel": r["kernel"]}
+        if fp64_peak and workload.endswith("fp64"):
+            # FP64 storage is bound by FP64 arithmetic on this GPU: FP64 operations per update
+            # (2 DFMA + DADD + DMUL, counted by ncu on the same kernel) over the measured rate
+            fl = _flops64_for(f"{r['kernel']}:{workload}")
+            if fl is not None:
+                e["fp64_alu"] = {"bound": "alu", "flops_per_update": fl,
+                                 "achieved_tflops": round(fl * r["mlups"] * 1e6 / 1e12, 4),
+                                 "peak_tflops": round(fp64_peak / 1e12, 4),
+                                 "frac": round(fl * r["mlups"] * 1e6 / fp64_peak, 4)}
+        return e
 
     if rank == 0 and not a.no_modes and a.workload == "2d_lec":
         modes = {}
@@ -439,22 +468,17 @@ def run_ours(a):
                     steps = 300 if prec == "fp64" else 1000
                     r = measure(prec, steps, 5, mu=mu, variant=variant)
                     key = f"lec_{prec}_mu{mu:g}" + {0: "", 1: "_plain", 2: "_box", 3: "_persistent"}[variant]
-                    modes[key] = {"mlups": round(r["mlups"], 2), "ms_per_step": round(r["ms"], 5),
-                                  "achieved_gbs": round(r["gbs"], 1), "frac_of_measured_hbm": round(r["frac"], 4),
-                                  "bytes_per_update": r["bytes_per_update"], "steps": steps, "kernel": r["kernel"]}
+                    modes[key] = mode_entry(r, steps, f"2d_lec_1024x512_{prec}")
         for prec in ("fp64", "fp32", "fp16s"):
             steps = 200 if prec == "fp64" else 600
             r = measure(prec, steps, 5, mu=1e-2, variant=0, closure="warmc")
-            modes[f"warmc_{prec}_mu0.01"] = {"mlups": round(r["mlups"], 2), "ms_per_step": round(r["ms"], 5),
-                                             "achieved_gbs": round(r["gbs"], 1),
-                                             "frac_of_measured_hbm": round(r["frac"], 4),
-                                             "bytes_per_update": r["bytes_per_update"], "steps": steps,
-                                             "kernel": r["kernel"]}
+            modes[f"warmc_{prec}_mu0.01"] = mode_entry(r, steps, f"2d_warmc_1024x512_{prec}")
         out["modes"] = modes
         out["precision_vs_fp64"] = _precision_table(cfg, stream)
         # the same check on the axisymmetric path (600 x 120 nodes of the 3D3V configuration's spacing 0.05)
         out["precision_vs_fp64_axisymmetric"] = _precision_table(
             dict(CONFIG_AXI, n=(600, 120), dx=0.05, z0=3.0), stream)
+        out["precision_vs_fp64_3d"] = _precision_3d(stream)
 
     if rank == 0 and not a.no_configs and a.workload == "2d_lec":
         out["configs_measured"] = _configs(stream, flush, hbm)
@@ -467,14 +491,97 @@ def run_ours(a):
 
     if rank == 0 and world == 1 and not a.no_cpu:
         mlups, ns, dt = _oracle_sample(cfg)
+        one = _oracle_one_thread(cfg)
         out["cpu_baseline"] = {"value": round(mlups, 4), "unit": "MLUPS", "cores": os.cpu_count(),
-                               "kind": "oracle",
-                               "sample": f"{ns} FP64 oracle steps of the full 1024x512 grid ({dt:.1f} s)"}
+                               "kind": "oracle", "cpu_model": _cpu_model(),
+                               "sample": f"{ns} FP64 oracle steps of the full 1024x512 grid ({dt:.1f} s)",
+                               "one_thread": one}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def _flops64_for(kernel_key):
+    """FP64 operations per node update of a kernel on a workload (2 x DFMA +
+    DADD + DMUL of one launch over its nodes, from a committed ncu summary's
+    `flops64 <kernel:workload> <count> sources_sha256=<digest>` line), valid
+    only while the kernel sources are unchanged."""
+    import glob
+    import re
+    try:
+        from paper_2309_04872_gb300 import build as B
+        digest = B.step_kernel_digest()
+        for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+            for m in re.finditer(r"flops64 (\S+) ([0-9.]+) sources_sha256=([0-9a-f]+)", open(fn).read()):
+                if m.group(1) == kernel_key and m.group(3) == digest:
+                    return float(m.group(2))
+    except OSError:
+        pass
+    return None
+
+
+def _cpu_model():
+    """The host CPU's model name (lscpu), for the CPU baseline."""
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in txt.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def _oracle_one_thread(cfg, budget_s=8.0):
+    """The oracle on one host thread (a child process with OMP_NUM_THREADS=1,
+    so the parent's thread pool is untouched): MLUPS on the same grid."""
+    code = ("import json,sys,time; sys.path.insert(0, %r); import oracle as O; o=O.Oracle(%r); o.step(1); "
+            "t=time.perf_counter(); o.step(1); one=time.perf_counter()-t; n=max(1,min(50,int(%r/max(one,1e-6)))); "
+            "t=time.perf_counter(); o.step(n); dt=time.perf_counter()-t; "
+            "print(json.dumps({'steps': n, 'seconds': dt}))") % (ROOT, dict(cfg), budget_s)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
+    ncell = 1
+    for v in cfg["n"]:
+        ncell *= v
+    return {"value": round(ncell * d["steps"] / d["seconds"] / 1e6, 4), "unit": "MLUPS", "cores": 1,
+            "sample": f"{d['steps']} FP64 oracle steps of the full grid on one thread ({d['seconds']:.1f} s)"}
+
+
+def _precision_3d(stream, nsteps=2000):
+    """The 3D configuration's accuracy statement: WARMC D = 3, mu = 1e-2,
+    alpha = 1, sigma_z = 0.7, sigma_r = 0.3 on a 250 x 70 x 72 grid (ragged
+    against the marching kernel's 32 x 8 columns and 32-plane chunks), FP32
+    and FP16S storage against the FP64 path after nsteps: relative L2 error
+    per field (n - 1, u_z, u_x, gamma - 1, lambda - lambda_0, theta_zz -
+    theta_rest, theta_xx - theta_rest, theta_zx, E_z, E_x)."""
+    from paper_2309_04872_gb300 import lbpwfa as lb
+    cfg = dict(CONFIG_3D, n=(250, 70, 72), z0=1.4)
+    names = ["n-1", "u_z", "u_x", "gamma-1", "lambda-lambda0", "theta_zz", "theta_xx", "theta_zx"]
+    mask = lb.M_N | lb.M_UZ | lb.M_UX | lb.M_GAMMA | lb.M_LAMBDA | lb.M_TH_ZZ | lb.M_TH_XX | lb.M_TH_ZX
+    with lb.Run(dict(cfg, alpha=0.0, init_fields=False), "fp64", stream=stream.cuda_stream) as r0:
+        rest = r0.moments(mask)[:, :1]
+    out = {}
+    for prec in ("fp64", "fp32", "fp16s"):
+        with lb.Run(cfg, prec, stream=stream.cuda_stream) as run:
+            run.step(nsteps)
+            out[prec] = (run.moments(mask) - rest, run.fields(lb.F_EZ | lb.F_EX), run.reduce()[2])
+    m64, f64, _ = out["fp64"]
+    res = {"grid": list(cfg["n"]), "steps": nsteps, "alpha": cfg["alpha"], "mu": cfg["mu"]}
+    for prec in ("fp32", "fp16s"):
+        m, f, bad = out[prec]
+        d = {nm: float(np.linalg.norm(m[j] - m64[j]) / np.linalg.norm(m64[j])) for j, nm in enumerate(names)}
+        d["E_z"] = float(np.linalg.norm(f[1] - f64[1]) / np.linalg.norm(f64[1]))
+        d["E_x"] = float(np.linalg.norm(f[0] - f64[0]) / np.linalg.norm(f64[0]))
+        d["nonfinite"] = int(bad)
+        res[prec] = d
+    return res
 
 
 def _precision_table(cfg, stream, nsteps=2000):
@@ -531,7 +638,7 @@ def _configs(stream, flush, hbm):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / 96
-            gbs = info.bytes_per_step / (ms * 1e-3) / 1e9
+            gbs = info.algorithmic_bytes_per_step / (ms * 1e-3) / 1e9
             nlec = sum(1 for d in draws if d["closure"] == "lec")
             res[f"batch_64x2d_{bprec}"] = {
                 "mlups": round(info.ncell / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
@@ -550,11 +657,12 @@ def _configs(stream, flush, hbm):
                 info = run.info()
                 times = _time_steps(run, stream, 100 if prec == "fp64" else 300, 5, flush)
             mean = sum(times) / len(times)
-            gbs = info.bytes_per_update * info.ncell / (mean * 1e-3) / 1e9
+            gbs = info.algorithmic_bytes_per_update * info.ncell / (mean * 1e-3) / 1e9
             res[f"axi_{closure}_{prec}_3000x600"] = {
                 "mlups": round(info.ncell / (mean * 1e-3) / 1e6, 2), "ms_per_step": round(mean, 4),
                 "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
-                "bytes_per_update": info.bytes_per_update, "steps": len(times),
+                "bytes_per_update": info.algorithmic_bytes_per_update,
+                "stored_bytes_per_update": info.bytes_per_update, "steps": len(times),
                 "kernel": KERNEL_NAMES[info.kernel_variant], "geometry": "axisymmetric (z, r)"}
     for prec in ("fp32", "fp64"):
         try:
@@ -565,11 +673,12 @@ def _configs(stream, flush, hbm):
             res[f"3d_warmc_{prec}_512x256x256"] = {"error": str(err)}
             continue
         mean = sum(times) / len(times)
-        gbs = info.bytes_per_update * info.ncell / (mean * 1e-3) / 1e9
+        gbs = info.algorithmic_bytes_per_update * info.ncell / (mean * 1e-3) / 1e9
         res[f"3d_warmc_{prec}_512x256x256"] = {
             "mlups": round(info.ncell / (mean * 1e-3) / 1e6, 2), "ms_per_step": round(mean, 3),
             "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
-            "bytes_per_update": info.bytes_per_update, "steps": len(times),
+            "bytes_per_update": info.algorithmic_bytes_per_update,
+            "stored_bytes_per_update": info.bytes_per_update, "steps": len(times),
             "kernel": KERNEL_NAMES[info.kernel_variant],
             "device_gb": round(info.device_bytes / 1e9, 2)}
     return res

@@ -140,6 +140,13 @@ typedef struct {
                               at r > 0.  Batches may mix both geometries;
                               the adjoint takes Cartesian runs only
                               (LBPWFA_ERR_INVALID). */
+  size_t device_bytes_cap; /* 0: no cap.  Else the most device memory the
+                              handle may hold (state, diagnostics scratch,
+                              adjoint tape and checkpoints together): a
+                              create or a later allocation that would pass
+                              it returns LBPWFA_ERR_OOM, before any device
+                              memory is touched.  lbpwfa_create checks the
+                              state's size first, before any CUDA call. */
 } lbpwfa_params;
 
 typedef struct {
@@ -150,11 +157,23 @@ typedef struct {
   double dt;               /* time step, omega_p^-1 */
   double time;             /* step * dt */
   size_t device_bytes;     /* device memory held by the handle */
-  double bytes_per_update; /* algorithmic HBM bytes of one node update of the
-                              step kernel (populations + fields [+ WARMC
-                              previous-step values]) */
+  double bytes_per_update; /* stored HBM bytes one node update of the step
+                              kernel reads and writes in this design:
+                              populations (with the FP16S low planes),
+                              fields (FP32 modes: high and low parts) and the
+                              WARMC previous-step values */
   int kernel_variant;      /* step kernel in use: 1 plain, 2 TMA box per CTA,
-                              3 persistent TMA, 4 3D marching columns */
+                              3 persistent TMA, 4 3D marching columns,
+                              5 axisymmetric plain */
+  double algorithmic_bytes_per_update; /* the method's bytes per node update,
+                              independent of this design's extra storage:
+                              2 K Q s (populations read and written, s the
+                              stored population size) + 2 F r (the F field
+                              components, r the real size: 8 in FP64, 4
+                              otherwise) + 2 (2 (1 + dim)) r for WARMC (the
+                              previous step's theta^{0 beta} and w^beta).
+                              2D LEC: 480 / 240 / 132 B in FP64 / FP32 /
+                              FP16S; 2D WARMC FP32 648; 3D WARMC FP32 1784 */
 } lbpwfa_info_t;
 
 /* Create a run: validates *p, allocates all device state on the handle's
@@ -264,10 +283,15 @@ int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info);
  *    contents; each call overwrites every partial it reads, but calls whose
  *    work overlaps on the GPU race on it.
  *  - out: 3 doubles (sum n, sum n_b, non-finite populations) on the device
- *    when out_is_device (asynchronous), else on the host (synchronises; then
- *    returns NONFINITE when out[2] > 0).  Call with the handle's device
- *    current.  The summation order differs from lbpwfa_reduce (more, smaller
- *    blocks), so the two agree to FP64 round-off, not bitwise. */
+ *    when out_is_device (asynchronous), else on the host.  The host form
+ *    synchronises and then, like lbpwfa_reduce, returns TIMEOUT when a
+ *    bounded device wait of an earlier step gave up, else NONFINITE when
+ *    out[2] > 0.  The device form reports neither: read out[2], and call
+ *    lbpwfa_synchronize for the timeout status.
+ *  - Call with the handle's device current; another current device returns
+ *    INVALID with the reason in lbpwfa_last_error.  The summation order
+ *    differs from lbpwfa_reduce (more, smaller blocks), so the two agree to
+ *    FP64 round-off, not bitwise. */
 int lbpwfa_reduce_noalloc(lbpwfa_t h, double* out, int out_is_device);
 
 /* Checkpoint: binary file with a header (parameters, step, precision), the
@@ -280,8 +304,29 @@ int lbpwfa_load(lbpwfa_t h, const char* path);
 /* Queue subsequent work on another stream (NULL = the library stream). */
 int lbpwfa_set_stream(lbpwfa_t h, void* stream);
 /* Wait for the handle's queued work; returns TIMEOUT when a bounded device
- * wait gave up (the step is then incomplete). */
+ * wait gave up (the step is then incomplete).  The timeout status sticks
+ * (lbpwfa_reduce and lbpwfa_synchronize keep returning it) until the state
+ * is replaced by lbpwfa_set_state or lbpwfa_load. */
 int lbpwfa_synchronize(lbpwfa_t h);
+
+/* The FP64 fused multiply-add rate of the current device, in FLOP/s (two
+ * per DFMA), measured by a kernel of independent register-resident DFMA
+ * chains timed with CUDA events on a stream of its own (best of three
+ * launches after a warm-up).  It is the ALU roofline of the FP64 storage
+ * mode: on GB300 the FP64 step is bound by FP64 arithmetic, not by HBM.
+ * Changes no device setting and allocates nothing.  The paper has no
+ * counterpart.  Errors: INVALID (flops NULL), CUDA. */
+int lbpwfa_measure_fp64_rate(double* flops);
+
+/* Failure-detection hook: the number of polls the first wait of each tile
+ * (the TMA-staged step kernels wait on an mbarrier for their population box)
+ * makes before it gives up, flags LBPWFA_ERR_TIMEOUT in the handle's device
+ * error word, lets the copy in flight land, and ends the CTA.  lbpwfa_create
+ * sets LBPWFA_WAIT_POLLS; 0 gives up at once, so a test can reach the
+ * timeout path without a fault.  The step is then incomplete.  The kernels
+ * that pull from global memory do not wait.  Errors: INVALID (h NULL). */
+#define LBPWFA_WAIT_POLLS (1u << 24)
+int lbpwfa_set_wait_limit(lbpwfa_t h, uint32_t polls);
 
 /* ------------------------------------------------------------------------
  * Gradients by the discrete adjoint (1D and 2D; FP64 or FP32 storage).
@@ -351,9 +396,12 @@ typedef struct {
   int graph_steps;         /* steps per captured graph */
   int64_t step;
   size_t device_bytes;
-  double bytes_per_step;   /* algorithmic HBM bytes of one batch step */
+  double bytes_per_step;   /* stored HBM bytes of one batch step (the runs'
+                              bytes_per_update times their nodes) */
   double tuned_ms[2][4];   /* per closure: autotuner step time per candidate
                               tile (-1 unused) */
+  double algorithmic_bytes_per_step; /* the runs' algorithmic_bytes_per_update
+                              times their nodes */
 } lbpwfa_batch_info_t;
 
 /* Create nruns >= 1 runs from p[0..nruns-1], each validated as by

@@ -160,6 +160,7 @@ struct StepParams {
   float inv_scale[11];   // FP16S: 1/s_k
   float scale[11];       // FP16S: s_k
   int* err;              // device error word (bit 0: a bounded wait gave up)
+  unsigned wait_limit;   // polls of a tile's first barrier wait before it gives up
   void* tape;            // adjoint recording (1D/2D), or null: this step's
                          // deviation moments dA [K], E^{n+1/2} [DIM] and
                          // B^n [present B] as [K + DIM + NB][plane] of real

@@ -55,6 +55,8 @@ struct lbpwfa_s {
   bool use_axi = false;    // 2D axisymmetric (z, r) kernel
   bool in_batch = false;  // owned by a batch: stepped only through lbpwfa_batch_step
   int num_sms = 0;
+  int device = -1;  // the CUDA device current at lbpwfa_create (holds every buffer)
+  unsigned wait_limit = LBPWFA_WAIT_POLLS;  // polls of a tile's first barrier wait
   alignas(64) CUtensorMap maps[2];
   int* err_d = nullptr;  // device error word written by bounded waits
   lbprt::AdjRec* adj = nullptr;
@@ -76,6 +78,7 @@ lbp::StepParams step_params(const lbpwfa_s* h);
 double zeta0_of(double z0, long long step, double dt);
 int launch_step(lbpwfa_s* h, void* tape);
 int check_err_word(lbpwfa_s* h);
+int clear_err_word(lbpwfa_s* h);
 
 // adjoint recording hooks (adjoint_rt.cu)
 int adj_before_step(lbpwfa_s* h, void** tape);  // checkpoint / tape slot of the next step

@@ -44,6 +44,18 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Bounded wait on one phase of an mbarrier: at most `polls` polls, false when
+// they ran out.  A tile's first wait polls P.wait_limit times (2^24 unless the
+// host lowered it to exercise the timeout path); the drain after a timeout,
+// which lets the copy in flight land before the CTA leaves, keeps the long
+// limit kDrainPolls.
+constexpr uint32_t kDrainPolls = 1u << 24;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t polls) {
+  for (uint32_t spin = 0; spin < polls; ++spin)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 template <int CL, int PR> struct TmaTile2D;
 // Tile and resident CTAs per SM (the shared-memory box sets the occupancy;
 // the register budget is held to match it).
@@ -125,12 +137,14 @@ lb_step_tma2d_kernel(const StepParams P, const __grid_constant__ CUtensorMap tma
   FieldPF<real> F;
   if (bulk) prefetch_own<2, real, false, T::TZ, T::TX, 1>(P, F, blockIdx.x, blockIdx.y, 0);
   else prefetch_own<2, real, true, T::TZ, T::TX, 1>(P, F, blockIdx.x, blockIdx.y, 0);
-  // bounded wait for the box; on timeout flag the error and leave
-  bool done = false;
-  for (uint32_t spin = 0; spin < (1u << 24) && !(done = mbar_try_wait(bar, 0)); ++spin) {
-  }
+  // bounded wait for the box; on timeout flag the error, let the copy in
+  // flight land in shared memory, and leave
+  const bool done = mbar_wait_bounded(bar, 0, P.wait_limit);
   if (!__syncthreads_and(done)) {
-    if (threadIdx.x == 0 && P.err) atomicOr(P.err, 1);
+    if (threadIdx.x == 0) {
+      if (P.err) atomicOr(P.err, 1);
+      mbar_wait_bounded(bar, 0, kDrainPolls);
+    }
     return;
   }
   SmemPull2D<CL, PR> pull{P, box, oz, ox};
@@ -216,13 +230,6 @@ struct SmemPullBox2D {
   }
 };
 
-// Bounded wait on one phase of an mbarrier; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t spin = 0; spin < (1u << 24); ++spin)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
 // AXI: the axisymmetric (z, r) step (the axis rules and 1/r sources of
 // step_body's AXI mode).
 template <int CL, int PR, bool AXI = false>
@@ -255,11 +262,11 @@ lb_step_persist2d_kernel(const StepParams P, const __grid_constant__ CUtensorMap
     else prefetch_own<2, real, true, T::TZ, T::TX, 1>(P, F, tz, tx, 0);
     // bounded wait for this tile's box (the barrier's phase j); on timeout
     // flag the error, let the copy in flight land, and leave
-    const bool done = mbar_wait_bounded(bar, j & 1u);
+    const bool done = mbar_wait_bounded(bar, j & 1u, P.wait_limit);
     if (!__syncthreads_and(done)) {
       if (threadIdx.x == 0) {
         if (P.err) atomicOr(P.err, 1);
-        mbar_wait_bounded(bar, j & 1u);
+        mbar_wait_bounded(bar, j & 1u, kDrainPolls);
       }
       return;
     }

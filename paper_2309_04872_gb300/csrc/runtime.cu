@@ -42,6 +42,13 @@ int fail_cuda(lbpwfa_s* h, cudaError_t e, const char* what) {
 
 int alloc(lbpwfa_s* h, Buf& b, size_t bytes) {
   if (bytes == 0) return LBPWFA_OK;
+  const size_t cap = h->prm.device_bytes_cap;
+  if (cap != 0 && (bytes > cap || h->device_bytes > cap - bytes)) {
+    h->err = "device memory cap: " + std::to_string(h->device_bytes + bytes) + " bytes would pass the cap of " +
+             std::to_string(cap);
+    b.p = nullptr;
+    return LBPWFA_ERR_OOM;
+  }
   cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -196,6 +203,7 @@ StepParams step_params(const lbpwfa_s* h) {
     P.inv_scale[k] = h->inv_scale[k];
   }
   P.err = h->err_d;
+  P.wait_limit = h->wait_limit;
   fill_consts<float>(h, P.cf);
   fill_consts<double>(h, P.cd);
   return P;
@@ -243,6 +251,12 @@ bool make_pop_map(lbpwfa_s* h, void* base, CUtensorMap* map, const int* boxdim) 
   CUresult r = enc(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+// The state was replaced: a timeout flagged before no longer applies.
+int clear_err_word(lbpwfa_s* h) {
+  CK(h, cudaMemsetAsync(h->err_d, 0, sizeof(int), h->stream));
+  return LBPWFA_OK;
 }
 
 int check_err_word(lbpwfa_s* h) {
@@ -398,6 +412,14 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
   h->store_sz = p->precision == LBPWFA_FP64 ? 8 : (p->precision == LBPWFA_FP32 ? 4 : 2);
   h->real_sz = p->precision == LBPWFA_FP64 ? 8 : 4;
   h->dt = p->courant * p->dx;
+  h->NPL = h->K * h->Q + (p->precision == LBPWFA_FP16S ? h->K : 0);
+  if (p->device_bytes_cap != 0) {
+    // the state's size against the cap, before any CUDA call
+    const double need = 2.0 * h->NPL * (double)h->plane * h->store_sz +
+                        4.0 * 3.0 * (double)h->plane * h->real_sz * (h->real_sz == 4 ? 2.0 : 1.0) +
+                        (double)h->NPREV * h->plane * h->real_sz;
+    if (need > (double)p->device_bytes_cap) { delete h; return LBPWFA_ERR_OOM; }
+  }
 
   // Rest advected values.  WARMC: Eq. (traces3) at rest (theta^{00} = 0,
   // theta^{ij} = mu delta^{ij} over the D kinetic dimensions, n_0 = 1):
@@ -430,8 +452,7 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
   cudaError_t pe = h->ks.prepare();
   if (pe != cudaSuccess) { fail_cuda(h, pe, "cudaFuncSetAttribute"); lbpwfa_destroy(h); return LBPWFA_ERR_CUDA; }
 
-  // FP16S: one more plane per set for the rest population's low part
-  h->NPL = h->K * h->Q + (p->precision == LBPWFA_FP16S ? h->K : 0);
+  // FP16S: one more plane per set for the rest population's low part (NPL)
   const size_t pop_bytes = (size_t)h->NPL * h->plane * h->store_sz;
   const size_t fld_bytes = 3 * (size_t)h->plane * h->real_sz * (h->real_sz == 4 ? 2 : 1);
   int r = LBPWFA_OK;
@@ -452,6 +473,7 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
   {
     int dev = 0;
     cudaGetDevice(&dev);
+    h->device = dev;
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
   }
   // axisymmetric (z, r) grids: the plain kernel with the axis rules
@@ -707,6 +729,10 @@ int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double*
   }
   adj_invalidate(h);
   h->have_prev = 0;
+  {
+    int r = clear_err_word(h);
+    if (r != LBPWFA_OK) return r;
+  }
   if (!src_is_device) CK(h, cudaStreamSynchronize(h->stream));
   return LBPWFA_OK;
 }
@@ -781,6 +807,11 @@ int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info) {
   const double field_words = (ne + nbf) * (h->real_sz == 4 ? 2.0 : 1.0);
   info->bytes_per_update = 2.0 * h->NPL * h->store_sz + 2.0 * (field_words + h->NPREV) * h->real_sz;
   info->kernel_variant = h->use_persist ? 3 : (h->use_axi ? 5 : (h->use_march ? 4 : (h->use_tma ? 2 : 1)));
+  // the method's bytes: populations, one real per field component, and the
+  // WARMC previous-step theta^{0 beta}, w^beta (beta = 0..dim)
+  const int nalg_prev = h->prm.closure == LBPWFA_WARMC ? 2 * (1 + dim) : 0;
+  info->algorithmic_bytes_per_update =
+      2.0 * h->K * h->Q * h->store_sz + 2.0 * (ne + nbf) * h->real_sz + 2.0 * nalg_prev * h->real_sz;
   return LBPWFA_OK;
 }
 
@@ -801,6 +832,12 @@ int lbpwfa_synchronize(lbpwfa_t h) {
   if (!h) return LBPWFA_ERR_INVALID;
   CK(h, cudaStreamSynchronize(h->stream));
   return check_err_word(h);
+}
+
+int lbpwfa_set_wait_limit(lbpwfa_t h, uint32_t polls) {
+  if (!h) return LBPWFA_ERR_INVALID;
+  h->wait_limit = polls;
+  return LBPWFA_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -883,6 +920,10 @@ int lbpwfa_load(lbpwfa_t h, const char* path) {
   CK(h, cudaMemcpyAsync(h->B[h->cur].p, q, H.fld_bytes, cudaMemcpyHostToDevice, h->stream));
   q += H.fld_bytes;
   if (H.prev_bytes) CK(h, cudaMemcpyAsync(h->prev.p, q, H.prev_bytes, cudaMemcpyHostToDevice, h->stream));
+  {
+    int r = clear_err_word(h);
+    if (r != LBPWFA_OK) return r;
+  }
   CK(h, cudaStreamSynchronize(h->stream));
   adj_invalidate(h);
   h->step = H.step;
@@ -924,12 +965,21 @@ namespace {
 std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[256] = {nullptr};
 
-// Device address of the array for the current device; resolved by the first
-// call on each device (host code may not use the symbol itself as an address).
+// Device address of the array on the handle's device; resolved by the first
+// call on each device (host code may not use the symbol itself as an
+// address: in host code it names a host-side stand-in).
 int noalloc_scratch(lbpwfa_s* h, double** out) {
   int dev = -1;
   CK(h, cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 256) return LBPWFA_ERR_INVALID;
+  if (dev != h->device) {
+    h->err = "lbpwfa_reduce_noalloc: device " + std::to_string(dev) + " is current, but the run lives on device " +
+             std::to_string(h->device);
+    return LBPWFA_ERR_INVALID;
+  }
+  if (dev < 0 || dev >= 256) {
+    h->err = "lbpwfa_reduce_noalloc: device index " + std::to_string(dev) + " is outside 0..255";
+    return LBPWFA_ERR_INVALID;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
@@ -963,7 +1013,71 @@ extern "C" int lbpwfa_reduce_noalloc(lbpwfa_t h, double* out, int out_is_device)
                         out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
   if (out_is_device) return LBPWFA_OK;
   CK(h, cudaStreamSynchronize(h->stream));
+  // a bounded device wait that gave up in an earlier step left a
+  // half-updated state: report that before the sums (the error word is the
+  // handle's own, allocated at create)
+  st = check_err_word(h);
+  if (st != LBPWFA_OK) return st;
   return out[2] > 0 ? LBPWFA_ERR_NONFINITE : LBPWFA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 fused multiply-add rate of the current GPU: the ALU roofline of the
+// FP64 storage mode.  Every thread runs kFmaChains independent DFMA chains
+// (enough independent work to keep the FP64 pipe busy at full occupancy);
+// the result reaches memory only if it equals a value it never takes, so
+// the chains are not removed and nothing is written.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kFmaChains = 8;
+static __device__ double g_fp64_sink;
+
+__global__ void __launch_bounds__(256) fp64_fma_kernel(int iters, double m, double c) {
+  double a[kFmaChains];
+#pragma unroll
+  for (int j = 0; j < kFmaChains; ++j) a[j] = 1.0 + 1e-9 * (double)(threadIdx.x + j);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) a[j] = fma(a[j], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < kFmaChains; ++j) s += a[j];
+  if (s == -1.0) g_fp64_sink = s;
+}
+}  // namespace
+
+extern "C" int lbpwfa_measure_fp64_rate(double* flops) {
+  if (!flops) return LBPWFA_ERR_INVALID;
+  *flops = 0.0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LBPWFA_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LBPWFA_ERR_CUDA;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LBPWFA_ERR_CUDA;
+  int r = LBPWFA_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = LBPWFA_ERR_CUDA;
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  double best_ms = 1e30;
+  for (int rep = 0; rep < 4 && r == LBPWFA_OK; ++rep) {  // the first launch is a warm-up
+    cudaEventRecord(e0, st);
+    fp64_fma_kernel<<<blocks, threads, 0, st>>>(iters, 0.9999999, 1e-8);
+    cudaEventRecord(e1, st);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      r = LBPWFA_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best_ms) best_ms = ms;
+  }
+  if (r == LBPWFA_OK)
+    *flops = 2.0 * kFmaChains * (double)iters * blocks * threads / (best_ms * 1e-3);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -1330,11 +1444,13 @@ int lbpwfa_batch_info(lbpwfa_batch_t b, lbpwfa_batch_info_t* info) {
   info->nruns = (int)b->runs.size();
   info->ncell = 0;
   info->bytes_per_step = 0.0;
+  info->algorithmic_bytes_per_step = 0.0;
   for (lbpwfa_s* h : b->runs) {
     lbpwfa_info_t ri{};
     lbpwfa_info(h, &ri);
     info->ncell += ri.ncell;
     info->bytes_per_step += ri.bytes_per_update * (double)ri.ncell;
+    info->algorithmic_bytes_per_step += ri.algorithmic_bytes_per_update * (double)ri.ncell;
   }
   info->nitems = b->nitems[0] + b->nitems[1];
   for (int cl = 0; cl < 2; ++cl) {

@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
         ("profile", ctypes.POINTER(ctypes.c_double)), ("profile_len", ctypes.c_int),
         ("profile_dz", ctypes.c_double), ("precision", ctypes.c_int), ("boundary", ctypes.c_int),
         ("init_fields", ctypes.c_int), ("stream", ctypes.c_void_p), ("kernel_variant", ctypes.c_int),
-        ("geometry", ctypes.c_int),
+        ("geometry", ctypes.c_int), ("device_bytes_cap", ctypes.c_size_t),
     ]
 
 
@@ -64,14 +64,14 @@ class Info(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("Q", ctypes.c_int), ("ncell", ctypes.c_int64),
                 ("step", ctypes.c_int64), ("dt", ctypes.c_double), ("time", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("bytes_per_update", ctypes.c_double),
-                ("kernel_variant", ctypes.c_int)]
+                ("kernel_variant", ctypes.c_int), ("algorithmic_bytes_per_update", ctypes.c_double)]
 
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("nruns", ctypes.c_int), ("ncell", ctypes.c_int64), ("nitems", ctypes.c_int64),
                 ("tile", (ctypes.c_int * 2) * 2), ("grid", ctypes.c_int * 2), ("graph_steps", ctypes.c_int),
                 ("step", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("bytes_per_step", ctypes.c_double),
-                ("tuned_ms", (ctypes.c_double * 4) * 2)]
+                ("tuned_ms", (ctypes.c_double * 4) * 2), ("algorithmic_bytes_per_step", ctypes.c_double)]
 
 
 class RecordParams(ctypes.Structure):
@@ -91,7 +91,7 @@ EXPORTED = ["lbpwfa_create", "lbpwfa_step", "lbpwfa_moments", "lbpwfa_fields", "
             "lbpwfa_status_string", "lbpwfa_last_error", "lbpwfa_reduce_noalloc",
             "lbpwfa_batch_create", "lbpwfa_batch_step", "lbpwfa_batch_member", "lbpwfa_batch_info",
             "lbpwfa_batch_destroy", "lbpwfa_record", "lbpwfa_adjoint_step", "lbpwfa_line_fit",
-            "lbpwfa_gauss_residual"]
+            "lbpwfa_gauss_residual", "lbpwfa_set_wait_limit", "lbpwfa_measure_fp64_rate"]
 
 
 def library_path() -> str:
@@ -126,6 +126,8 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbpwfa_load.argtypes = [vp, ctypes.c_char_p]
     L.lbpwfa_set_stream.argtypes = [vp, vp]
     L.lbpwfa_synchronize.argtypes = [vp]
+    L.lbpwfa_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
+    L.lbpwfa_measure_fp64_rate.argtypes = [_DP]
     L.lbpwfa_destroy.argtypes = [vp]
     L.lbpwfa_destroy.restype = None
     L.lbpwfa_status_string.argtypes = [ctypes.c_int]
@@ -142,6 +144,15 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbpwfa_adjoint_step.argtypes = [vp, ctypes.POINTER(AdjointIO)]
     _lib = L
     return L
+
+
+def measure_fp64_rate() -> float:
+    """FP64 FMA rate of the current GPU in FLOP/s (lbpwfa_measure_fp64_rate)."""
+    out = ctypes.c_double()
+    st = load_library().lbpwfa_measure_fp64_rate(ctypes.byref(out))
+    if st != 0:
+        raise LbpwfaError(st, "lbpwfa_measure_fp64_rate")
+    return out.value
 
 
 def _code(v, table):
@@ -181,6 +192,7 @@ def make_params(cfg: dict, precision="fp64", stream=None, variant=0):
     p.stream = stream
     p.kernel_variant = int(variant)
     p.geometry = _code(cfg.get("geometry", "cartesian"), {"cartesian": CARTESIAN, "axisymmetric": AXISYMMETRIC})
+    p.device_bytes_cap = int(cfg.get("device_bytes_cap", 0))
     return p, keep
 
 
@@ -252,6 +264,11 @@ class Run:
     def synchronize(self):
         self._check(load_library().lbpwfa_synchronize(self._h), "lbpwfa_synchronize")
 
+    def set_wait_limit(self, polls: int):
+        """Polls of each tile's first barrier wait before it gives up
+        (lbpwfa_set_wait_limit; a failure-detection test hook)."""
+        self._check(load_library().lbpwfa_set_wait_limit(self._h, int(polls)), "lbpwfa_set_wait_limit")
+
     def moments(self, mask: int, out=None):
         nb = bin(mask & 0x3FFFF).count("1")
         if out is None:
@@ -316,12 +333,14 @@ class Run:
                                                     ctypes.c_void_p(B.ctypes.data), 0), "lbpwfa_get_state")
         return f, E, B
 
-    def reduce(self):
+    def reduce(self, status: bool = False):
+        """FP64 sums (sum n, sum n_b, non-finite populations); with status
+        also the call's status code (0, or -4 when out[2] > 0)."""
         out = np.zeros(3)
         st = load_library().lbpwfa_reduce(self._h, out.ctypes.data_as(_DP))
         if st not in (0, -4):
             self._check(st, "lbpwfa_reduce")
-        return out
+        return (out, st) if status else out
 
     def save(self, path: str):
         self._check(load_library().lbpwfa_save(self._h, path.encode()), "lbpwfa_save")

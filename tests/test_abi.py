@@ -85,3 +85,19 @@ def test_invalid_parameters_rejected_before_any_device_work(lib_path):
     lo = (ctypes.c_int * 3)(0, 0, 0)
     hi = (ctypes.c_int * 3)(1, 1, 1)
     assert lib.lbpwfa_gauss_residual(None, lo, hi, out) == -1
+
+
+def test_device_memory_cap_refuses_before_any_device_work(lib_path):
+    """A cap below the state's size returns OOM from lbpwfa_create before
+    the first CUDA call (so no GPU is needed); no handle is returned."""
+    from paper_2309_04872_gb300 import lbpwfa
+    lib = lbpwfa.load_library()
+    base = dict(dim=2, n=(64, 32), dx=0.05, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=1e-2,
+                alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=1.0)
+    for prec in ("fp64", "fp32", "fp16s"):
+        for cap in (1, 4096, 64 * 32 * 72 * 2):
+            p, keep = lbpwfa.make_params({**base, "device_bytes_cap": cap}, precision=prec)
+            h = ctypes.c_void_p()
+            assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -2, (prec, cap)
+            assert not h.value
+    assert lib.lbpwfa_set_wait_limit(None, 0) == -1

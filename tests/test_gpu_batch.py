@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from tests import parity as P
 from tests import inputs
 
 pytestmark = pytest.mark.gpu
@@ -75,10 +76,7 @@ def test_batch_fp64_matches_oracle():
             Ao = o.advected()
             rest = o.rest_advected()
             for k in range(o.K):
-                d = np.linalg.norm(A[k] - Ao[k])
-                assert d <= 1e-12 * np.linalg.norm(Ao[k]) + 1e-13 * np.sqrt(Ao[k].size)
-                if rest[k] != 0:
-                    assert d <= 1e-9 * np.linalg.norm(Ao[k] - rest[k]) + 1e-13 * abs(rest[k]) * np.sqrt(Ao[k].size)
+                P.check64(A[k], Ao[k], rest[k], 40, o.Q, f"batch member A{k}", P.rest_scale(o))
 
 
 def test_batch_member_state_reset_matches_single_run():
@@ -196,10 +194,7 @@ def test_batch_axisymmetric_fp64_matches_oracle():
             Ao = o.advected()
             rest = o.rest_advected()
             for k in range(o.K):
-                d = np.linalg.norm(A[k] - Ao[k])
-                assert d <= 1e-12 * np.linalg.norm(Ao[k]) + 1e-13 * np.sqrt(Ao[k].size)
-                if rest[k] != 0:
-                    assert d <= 1e-9 * np.linalg.norm(Ao[k] - rest[k]) + 1e-13 * abs(rest[k]) * np.sqrt(Ao[k].size)
+                P.check64(A[k], Ao[k], rest[k], 40, o.Q, f"batch member A{k}", P.rest_scale(o))
 
 
 def test_batched_temperature_sweep_acoustic_speed():

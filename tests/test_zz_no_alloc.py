@@ -35,10 +35,14 @@ def _noalloc(run, out, on_device):
     return L.lbpwfa_reduce_noalloc(run.handle, ptr, 1 if on_device else 0)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_noalloc_reduce_matches_reduce_on_two_calls(prec):
+# 131 x 37 nodes fit one partial of the fixed array; 512 x 256 (131 072
+# nodes) spread over 16 partials, so the multi-partial part of the array and
+# the final sum over the partials run too
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+@pytest.mark.parametrize("n", [(131, 37), (512, 256)])
+def test_noalloc_reduce_matches_reduce_on_two_calls(prec, n):
     import torch
-    cfg = dict(dim=2, n=(131, 37), dx=0.05, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=1e-2,
+    cfg = dict(dim=2, n=n, dx=0.05, courant=0.1, tau=0.53, closure="warmc", dv=3, mu=1e-2,
                alpha=0.2, sigma_z=0.6, sigma_r=0.3, z0=2.0, boundary="open", init_fields=True)
     orc = O.Oracle(cfg)
     base = orc.rest_advected()
@@ -56,6 +60,32 @@ def test_noalloc_reduce_matches_reduce_on_two_calls(prec):
             for got in (host, dev.cpu().numpy()):
                 assert np.allclose(got[:2], ref[:2], rtol=1e-12, atol=0.0), (call, got, ref)
                 assert got[2] == ref[2] == 0.0
+
+
+def test_noalloc_reduce_reports_nonfinite_and_timeout_like_reduce():
+    """The host form returns NONFINITE for a planted NaN and TIMEOUT after a
+    bounded device wait gave up, as lbpwfa_reduce does."""
+    cfg = dict(dim=2, n=(300, 70), dx=0.05, courant=0.1, tau=0.53, closure="lec", dv=3, mu=1e-2,
+               alpha=0.2, sigma_z=0.6, sigma_r=0.3, z0=2.0, boundary="open", init_fields=True)
+    orc = O.Oracle(cfg)
+    base = orc.rest_advected()
+    f = inputs.random_populations(5, orc.K, orc.Q, orc.ncell, base, np.abs(base) * 0.02 + 1e-3)
+    bad = f.copy()
+    bad[1, 2, 40 + 300 * 30] = np.inf
+    with lb.Run(cfg, "fp32") as run:
+        assert run.info().kernel_variant == 3   # the persistent TMA kernel (bounded waits)
+        run.set_state(bad)
+        out = np.zeros(3)
+        assert _noalloc(run, out, False) == -4 and out[2] == 1
+        run.set_state(f)
+        assert _noalloc(run, out, False) == 0 and out[2] == 0
+        run.set_wait_limit(0)
+        run.step(1)
+        assert _noalloc(run, out, False) == -5
+        run.set_wait_limit(1 << 24)
+        run.set_state(f)
+        run.step(1)
+        assert _noalloc(run, out, False) == 0
 
 
 def test_noalloc_reduce_rejects_runs_beyond_its_scratch():
