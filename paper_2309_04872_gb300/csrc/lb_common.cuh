@@ -303,14 +303,14 @@ __device__ __forceinline__ real lec_pi_minus_1(real dn, real p2, real g, int D) 
   return d * xe + d * (real(2) + d) / (xe * xe + xe + real(1));
 }
 // FP32 form: x^(2/3) enters only multiplied by d or in a denominator near 3,
-// so the hardware log2/exp2 (a few ulp) keeps Pi - 1 to a few ulp; the
-// reciprocals are correctly rounded.
+// so the hardware log2/exp2 (a few ulp) keeps Pi - 1 to a few ulp; so do the
+// hardware reciprocals (about 1 ulp), which replace correctly rounded ones.
 __device__ __forceinline__ float lec_pi_minus_1_f32(float dn, float p2, float ig, float g, int D) {
-  const float d = (dn - p2 * __frcp_rn(g + 1.0f)) * ig;
+  const float d = (dn - p2 * __fdividef(1.0f, g + 1.0f)) * ig;
   if (D == 1) return d * (3.0f + d * (3.0f + d));
   const float x = 1.0f + d;
   const float xe = exp2f((2.0f / 3.0f) * __log2f(x));
-  return d * xe + d * (2.0f + d) * __frcp_rn(fmaf(xe, xe, xe) + 1.0f);
+  return d * xe + d * (2.0f + d) * __fdividef(1.0f, fmaf(xe, xe, xe) + 1.0f);
 }
 
 // LEC transport velocity, Sec. 4.1: p^(0) = A_p / n, then
@@ -357,26 +357,28 @@ __device__ __forceinline__ void decode_lec(real n, const real* Ap, real cH, int 
   if (pim1_out) *pim1_out = lec_pi_minus_1<real>(dn, s - real(1), g, D);
 }
 
-// FP32 form of the same iteration for the reduced-precision modes.  Inside
-// the loop H uses the hardware reciprocal square root and log2/exp2 for
-// (n/gamma)^(2/D); their error is scaled by (1 + D/2) mu in H (below 1e-8
-// for mu <= 5e-2).  The returned u and Pi are evaluated once more with
-// correctly rounded sqrt, reciprocal and cbrt.
+// FP32 form of the same iteration for the reduced-precision modes.  The
+// power is split as (n/gamma)^(2/D) = n^(2/D) s^(-1/D) with s = 1 + |p|^2,
+// so log2 n leaves the loop and one iteration costs a log2, an exp2 and a
+// hardware reciprocal (their error is scaled by (1 + D/2) mu in H: below
+// 1e-8 for mu <= 5e-2).  1/gamma of the result is the hardware reciprocal
+// square root (about 1 ulp); gamma = s / gamma.
 template <int DIM>
 __device__ __forceinline__ void decode_lec_f32(float n, const float* Ap, float cH, int D, float* u, float& Pi,
                                                float dn = 0.0f, float* pim1_out = nullptr) {
-  const float in_ = __frcp_rn(n);
+  const float in_ = __fdividef(1.0f, n);
   float p0[DIM], p[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) { p0[a] = Ap[a] * in_; p[a] = p0[a]; }
   const float e = 2.0f / (float)D;
+  const float ln = e * __log2f(n);  // log2 n^(2/D)
+  const float n2 = n * n;           // D = 1: (n/gamma)^2 = n^2 / s
   for (int it = 0; it < 32; ++it) {
     float s = 1.0f;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) s = fmaf(p[a], p[a], s);
-    const float x = n * rsqrtf(s);
-    const float pw = D == 1 ? x * x : exp2f(e * __log2f(x));
-    const float iH = __frcp_rn(fmaf(cH, pw, 1.0f));
+    const float pw = D == 1 ? n2 * __fdividef(1.0f, s) : exp2f(fmaf(-0.5f * e, __log2f(s), ln));
+    const float iH = __fdividef(1.0f, fmaf(cH, pw, 1.0f));
     float d = 0.0f, pm = 0.0f;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -390,8 +392,8 @@ __device__ __forceinline__ void decode_lec_f32(float n, const float* Ap, float c
   float s = 1.0f;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) s = fmaf(p[a], p[a], s);
-  const float g = sqrtf(s);
-  const float ig = __frcp_rn(g);
+  const float ig = rsqrtf(s);
+  const float g = s * ig;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) u[a] = p[a] * ig;
   if (pim1_out) {
