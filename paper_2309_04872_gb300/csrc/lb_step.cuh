@@ -957,6 +957,26 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   const real itau = S.inv_tau, omt = real(1) - S.inv_tau;
   const real base = real(-1.5) * usq;
   store* fout = reinterpret_cast<store*>(P.fout);
+  // 1D/2D: the equilibrium's set-independent factors of each pair of
+  // opposite velocities, with 1/tau folded in, formed once per node:
+  // Ef = w (base + 9/2 cu^2) / tau, Of = 3 w cu / tau; then per set and pair
+  // f*_i - w A_rest = df_i (1 - 1/tau) + w (dA/tau + dt F) + A Ef +- A Of.
+  // 3D (rolled set loop, registers scarce) forms them per set.
+  constexpr int NP = (Q - 1) / 2;
+  constexpr bool PRE = DIM <= 2;
+  real Ef[PRE ? NP : 1], Of[PRE ? NP : 1];
+  if constexpr (PRE) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const int i = 1 + 2 * q;
+      real cu = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) cu += real(L::c(i, a)) * ul[a];
+      const real wi = real(L::w(i));
+      Ef[q] = (wi * (base + real(4.5) * cu * cu)) * itau;
+      Of[q] = ((real(3) * wi) * cu) * itau;
+    }
+  }
   // one population set: pull (or the kept values), relax, store; the source
   // dt F_k is evaluated after the pull (dtF_of), as in a plain loop body
   auto collide_set = [&](int k, real Arest_k, float sc, float isc, auto dtF_of) {
@@ -979,18 +999,30 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
     if constexpr (AXI) dtF += dt * geo(k, A);
     store* fk = fout + (size_t)k * Q * (size_t)P.plane;
     real moved = 0;
+    if constexpr (PRE) {
+      const real g = dA * itau + dtF;
 #pragma unroll
-    for (int q = 0; q < (Q - 1) / 2; ++q) {
-      const int i = 1 + 2 * q, j = i + 1;
-      real cu = 0;
+      for (int q = 0; q < NP; ++q) {
+        const int i = 1 + 2 * q, j = i + 1;
+        const real evw = A * Ef[q] + real(L::w(i)) * g;
+        const real odd = A * Of[q];
+        moved = add_rn(moved, Codec<PR>::store_q(fk, i * pl + id, df[i] * omt + (evw + odd), sc, isc));
+        moved = add_rn(moved, Codec<PR>::store_q(fk, j * pl + id, df[j] * omt + (evw - odd), sc, isc));
+      }
+    } else {
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) cu += real(L::c(i, a)) * ul[a];
-      const real wi = real(L::w(i));
-      const real even = wi * (dA + A * (base + real(4.5) * cu * cu));
-      const real odd = (real(3) * wi) * A * cu;
-      const real wF = wi * dtF;
-      moved = add_rn(moved, Codec<PR>::store_q(fk, i * pl + id, df[i] * omt + (even + odd) * itau + wF, sc, isc));
-      moved = add_rn(moved, Codec<PR>::store_q(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF, sc, isc));
+      for (int q = 0; q < NP; ++q) {
+        const int i = 1 + 2 * q, j = i + 1;
+        real cu = 0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) cu += real(L::c(i, a)) * ul[a];
+        const real wi = real(L::w(i));
+        const real even = wi * (dA + A * (base + real(4.5) * cu * cu));
+        const real odd = (real(3) * wi) * A * cu;
+        const real wF = wi * dtF;
+        moved = add_rn(moved, Codec<PR>::store_q(fk, i * pl + id, df[i] * omt + (even + odd) * itau + wF, sc, isc));
+        moved = add_rn(moved, Codec<PR>::store_q(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF, sc, isc));
+      }
     }
     Codec<PR>::store0(fk, id, fout + ((size_t)K * Q + k) * (size_t)P.plane, id, sub_rn(add_rn(dA, dtF), moved), sc);
   };
