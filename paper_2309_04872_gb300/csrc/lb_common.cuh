@@ -201,6 +201,15 @@ template <> struct Codec<PR_F64> {
     return __ldg(p + i);
   }
   __device__ static void store0(double* p, long long i, double*, long long, double v, float) { gst(p + i, v); }
+  // storage units (the step's working units; scale 1 here)
+  static constexpr bool kScaled = false;
+  __device__ static double load_u(const double* p, long long i) { return __ldg(p + i); }
+  __device__ static double load0_u(const double* p, long long i, const double*, long long) { return __ldg(p + i); }
+  __device__ static double store_qu(double* p, long long i, double v) {
+    gst(p + i, v);
+    return v;
+  }
+  __device__ static void store0_u(double* p, long long i, double*, long long, double v) { gst(p + i, v); }
 };
 template <> struct Codec<PR_F32> {
   static constexpr int kLoPlanes = 0;
@@ -214,6 +223,14 @@ template <> struct Codec<PR_F32> {
     return __ldg(p + i);
   }
   __device__ static void store0(float* p, long long i, float*, long long, float v, float) { gst(p + i, v); }
+  static constexpr bool kScaled = false;
+  __device__ static float load_u(const float* p, long long i) { return __ldg(p + i); }
+  __device__ static float load0_u(const float* p, long long i, const float*, long long) { return __ldg(p + i); }
+  __device__ static float store_qu(float* p, long long i, float v) {
+    gst(p + i, v);
+    return v;
+  }
+  __device__ static void store0_u(float* p, long long i, float*, long long, float v) { gst(p + i, v); }
 };
 // Binary16 of the scaled deviation.  The rest population takes the remainder
 // of its set's moment in the collision, so its rounding is the one error of
@@ -245,6 +262,27 @@ template <> struct Codec<PR_F16S> {
     gst(p + i, h);
     // x - h is exact in FP32: h is x rounded to 11 significant bits, and the
     // difference holds the rest of x's bits
+    gst(lo + j, __float2half_rn(__fsub_rn(x, __half2float(h)) * kLoScale));
+  }
+  // Storage units: the stored binary16 read as FP32 without the 1/s_k.  The
+  // scale is a power of two, so working in these units and applying 1/s_k
+  // once to a set's moment gives the same bits as scaling every population.
+  static constexpr bool kScaled = true;
+  __device__ static float load_u(const __half* p, long long i) { return __half2float(__ldg(p + i)); }
+  __device__ static float join_u(__half hi, __half lo) {
+    return fmaf(__half2float(lo), kLoInv, __half2float(hi));
+  }
+  __device__ static float load0_u(const __half* p, long long i, const __half* lo, long long j) {
+    return join_u(__ldg(p + i), __ldg(lo + j));
+  }
+  __device__ static float store_qu(__half* p, long long i, float x) {
+    const __half h = __float2half_rn(x);
+    gst(p + i, h);
+    return __half2float(h);
+  }
+  __device__ static void store0_u(__half* p, long long i, __half* lo, long long j, float x) {
+    const __half h = __float2half_rn(x);
+    gst(p + i, h);
     gst(lo + j, __float2half_rn(__fsub_rn(x, __half2float(h)) * kLoScale));
   }
 };

@@ -48,6 +48,16 @@ __device__ __forceinline__ real set_moment(const real* df) {
   return s;
 }
 
+// Deviation moment dA_k of a set pulled in storage units: the sum, times
+// 1/s_k for the scaled binary16 format (a power of two: the same bits as
+// summing the scaled-back populations).
+template <int Q, int PR, typename real>
+__device__ __forceinline__ real set_dA(const real* df, float inv_s) {
+  const real m = set_moment<Q>(df);
+  if constexpr (Codec<PR>::kScaled) return m * inv_s;
+  return m;
+}
+
 // 3D models keep the loops over population sets rolled: one 19-velocity body
 // per loop instead of K (up to 11), so the step fits the instruction cache.
 // 2D models unroll them (2D WARMC, 8 x 9 populations, runs faster unrolled at
@@ -107,7 +117,8 @@ __host__ __device__ constexpr bool odd_in_r(int k) {
 }
 
 // Deviations of the pulled populations f^n_ki - w_i A_rest,k at node
-// (z, x, y) (already inside the domain), straight from global memory.
+// (z, x, y) (already inside the domain), straight from global memory, in
+// storage units (FP16S: times s_k; set_dA applies 1/s_k to the set's sum).
 // AXI: (z, r) grid whose x = 0 row is the r = 0 boundary node; it takes the
 // pulled populations of its bulk node as they are (Eq. open-bc) for the
 // sets even under r -> -r and with the mirrored velocity (Eq. reflective-bc)
@@ -125,7 +136,6 @@ __device__ __forceinline__ void pulled_dev(const StepParams& P, int z, int x, in
     if (DIM >= 3) y = min(max(y, 1), P.n[2] - 2);
   }
   const store* f = (const store*)P.fin + (size_t)k * L::Q * (size_t)P.plane;
-  const float is = P.inv_scale[k];
   const int pl = (int)P.plane;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
@@ -139,9 +149,9 @@ __device__ __forceinline__ void pulled_dev(const StepParams& P, int z, int x, in
       // rest population (with its low part in the reduced-precision format)
       const store* lo = (const store*)P.fin + ((size_t)Model<DIM, CL>::K * L::Q + k) * (size_t)P.plane;
       const int c0 = cell_index32(P, sz, sx, sy);
-      df[0] = Codec<PR>::load0(f, c0, lo, c0, is);
+      df[0] = Codec<PR>::load0_u(f, c0, lo, c0);
     } else {
-      df[i] = Codec<PR>::load(f, i * pl + cell_index32(P, sz, sx, sy), is);
+      df[i] = Codec<PR>::load_u(f, i * pl + cell_index32(P, sz, sx, sy));
     }
   }
   if constexpr (AXI) {
@@ -463,7 +473,7 @@ __device__ __forceinline__ void decode_node(const StepParams& P, const StepConst
     for (int k = 0; k < K; ++k) {
       real df[Q];
       pull.template get<EDGE>(z, x, y, k, df);
-      scr[k * NT] = set_moment<Q>(df);
+      scr[k * NT] = set_dA<Q, PR>(df, P.inv_scale[k]);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) dA[k] = scr[k * NT];
@@ -472,7 +482,7 @@ __device__ __forceinline__ void decode_node(const StepParams& P, const StepConst
     for (int k = 0; k < K; ++k) {
       real df[Q];
       pull.template get<EDGE>(z, x, y, k, df);
-      dA[k] = set_moment<Q>(df);
+      dA[k] = set_dA<Q, PR>(df, P.inv_scale[k]);
     }
   }
   real rec[M::NM];
@@ -600,7 +610,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       for (int k = 0; k < K; ++k) {
         real df[Q];
         pull.template get<EDGE>(ez, ex, ey, k, df);
-        scr[k * NT] = set_moment<Q>(df);
+        scr[k * NT] = set_dA<Q, PR>(df, P.inv_scale[k]);
       }
 #pragma unroll
       for (int k = 0; k < K; ++k) dA_own[k] = scr[k * NT];
@@ -616,7 +626,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
 #pragma unroll
           for (int i = 0; i < Q; ++i) skeep[(k * Q + i) * NT] = df[i];
         }
-        dA_own[k] = set_moment<Q>(df);
+        dA_own[k] = set_dA<Q, PR>(df, P.inv_scale[k]);
       }
     }
     real rec[M::NM];
@@ -992,22 +1002,26 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
       dA = dA_own[k];
     } else {
       pull.template get<EDGE>(gz, gx, gy, k, df);
-      dA = set_moment<Q>(df);
+      dA = set_dA<Q, PR>(df, isc);
     }
     const real A = Arest_k + dA;
     real dtF = dtF_of();
     if constexpr (AXI) dtF += dt * geo(k, A);
     store* fk = fout + (size_t)k * Q * (size_t)P.plane;
+    // df and the stored values are in storage units; us = s_k (FP16S) scales
+    // the equilibrium and source parts into them (exactly: a power of two)
+    const real us = Codec<PR>::kScaled ? real(sc) : real(1);
     real moved = 0;
     if constexpr (PRE) {
-      const real g = dA * itau + dtF;
+      const real As = A * us;
+      const real gs = (dA * itau + dtF) * us;
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
         const int i = 1 + 2 * q, j = i + 1;
-        const real evw = A * Ef[q] + real(L::w(i)) * g;
-        const real odd = A * Of[q];
-        moved = add_rn(moved, Codec<PR>::store_q(fk, i * pl + id, df[i] * omt + (evw + odd), sc, isc));
-        moved = add_rn(moved, Codec<PR>::store_q(fk, j * pl + id, df[j] * omt + (evw - odd), sc, isc));
+        const real evw = As * Ef[q] + real(L::w(i)) * gs;
+        const real odd = As * Of[q];
+        moved = add_rn(moved, Codec<PR>::store_qu(fk, i * pl + id, df[i] * omt + (evw + odd)));
+        moved = add_rn(moved, Codec<PR>::store_qu(fk, j * pl + id, df[j] * omt + (evw - odd)));
       }
     } else {
 #pragma unroll
@@ -1017,14 +1031,15 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
 #pragma unroll
         for (int a = 0; a < DIM; ++a) cu += real(L::c(i, a)) * ul[a];
         const real wi = real(L::w(i));
-        const real even = wi * (dA + A * (base + real(4.5) * cu * cu));
-        const real odd = (real(3) * wi) * A * cu;
-        const real wF = wi * dtF;
-        moved = add_rn(moved, Codec<PR>::store_q(fk, i * pl + id, df[i] * omt + (even + odd) * itau + wF, sc, isc));
-        moved = add_rn(moved, Codec<PR>::store_q(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF, sc, isc));
+        const real even = (wi * (dA + A * (base + real(4.5) * cu * cu))) * us;
+        const real odd = ((real(3) * wi) * A * cu) * us;
+        const real wF = (wi * dtF) * us;
+        moved = add_rn(moved, Codec<PR>::store_qu(fk, i * pl + id, df[i] * omt + (even + odd) * itau + wF));
+        moved = add_rn(moved, Codec<PR>::store_qu(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF));
       }
     }
-    Codec<PR>::store0(fk, id, fout + ((size_t)K * Q + k) * (size_t)P.plane, id, sub_rn(add_rn(dA, dtF), moved), sc);
+    Codec<PR>::store0_u(fk, id, fout + ((size_t)K * Q + k) * (size_t)P.plane, id,
+                        sub_rn(add_rn(dA, dtF) * us, moved));
   };
   if constexpr (RollSets<DIM, K>::value) {
     // the sources first, into this thread's shared-memory column; the

@@ -82,7 +82,7 @@ struct TmaCfg2D {
 };
 
 // Pull from the staged box (open boundaries: a boundary node reads as its
-// nearest bulk node, Eq. open-bc).
+// nearest bulk node, Eq. open-bc), in storage units as pulled_dev.
 template <int CL, int PR>
 struct SmemPull2D {
   using T = TmaCfg2D<CL, PR>;
@@ -96,18 +96,17 @@ struct SmemPull2D {
     using L = Lattice<2>;
     const int bz = (EDGE ? min(max(z, 1), P.n[0] - 2) : z) - oz;
     const int bx = (EDGE ? min(max(x, 1), P.n[1] - 2) : x) - ox;
-    const float is = P.inv_scale[k];
     const store* bk = box + (size_t)k * L::Q * T::BX * T::BZ;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const store v = bk[(i * T::BX + (bx - L::c(i, 1))) * T::BZ + (bz - L::c(i, 0))];
-      if constexpr (PR == PR_F16S) df[i] = __half2float(v) * is;
+      if constexpr (PR == PR_F16S) df[i] = __half2float(v);  // storage units
       else df[i] = v;
     }
     if constexpr (Codec<PR>::kLoPlanes > 0) {
       // the rest population with its low part (staged after the K*Q planes)
       const store* lo = box + ((size_t)T::KQ + k) * T::BX * T::BZ;
-      df[0] = Codec<PR>::join(bk[bx * T::BZ + bz], lo[bx * T::BZ + bz], is);
+      df[0] = Codec<PR>::join_u(bk[bx * T::BZ + bz], lo[bx * T::BZ + bz]);
     }
   }
 };
@@ -205,18 +204,17 @@ struct SmemPullBox2D {
     const bool mirror = AXI && EDGE && x == 0 && odd_in_r<CL>(k);
     const int bz = (EDGE ? min(max(z, 1), P.n[0] - 2) : z) - oz;
     const int bx = (EDGE ? min(max(x, 1), P.n[1] - 2) : x) - ox;
-    const float is = P.inv_scale[k];
     const store* bk = box + (size_t)k * L::Q * T::BX * T::BZ;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const store v = bk[(i * T::BX + (bx - L::c(i, 1))) * T::BZ + (bz - L::c(i, 0))];
-      if constexpr (PR == PR_F16S) df[i] = __half2float(v) * is;
+      if constexpr (PR == PR_F16S) df[i] = __half2float(v);  // storage units
       else df[i] = v;
     }
     if constexpr (Codec<PR>::kLoPlanes > 0) {
       // the rest population with its low part (staged after the K*Q planes)
       const store* lo = box + ((size_t)T::KQ + k) * T::BX * T::BZ;
-      df[0] = Codec<PR>::join(bk[bx * T::BZ + bz], lo[bx * T::BZ + bz], is);
+      df[0] = Codec<PR>::join_u(bk[bx * T::BZ + bz], lo[bx * T::BZ + bz]);
     }
     if constexpr (AXI) {
       if (mirror) {
