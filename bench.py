@@ -73,11 +73,12 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
     ap.add_argument("--workload", default="2d_lec",
-                    choices=["2d_lec", "2d_warmc", "3d_warmc", "3d_warmc_128", "adjoint_2d_warmc", "batch_2d",
-                             "axi_warmc", "axi_lec"],
+                    choices=["2d_lec", "2d_warmc", "3d_warmc", "3d_warmc_128", "3d_warmc_64", "adjoint_2d_warmc",
+                             "batch_2d", "axi_warmc", "axi_lec"],
                     help="2d_lec: 1024 x 512 LEC (default); 2d_warmc: the same grid with the warm-plasma "
                          "closure; 3d_warmc: 512 x 256 x 256 WARMC; "
-                         "3d_warmc_128: 128^3 WARMC (small case for profiling); adjoint_2d_warmc: "
+                         "3d_warmc_128, 3d_warmc_64: 128^3 and 64^3 WARMC (small cases for profiling); "
+                         "adjoint_2d_warmc: "
                          "forward + reverse sweep of the 512 x 256 WARMC adjoint case over --steps steps "
                          "(whole tape kept), for profiling; batch_2d: the first --batch-runs runs of the batched "
                          "sweep over --steps steps, for profiling; axi_warmc, axi_lec: the 3000 x 600 "
@@ -370,7 +371,8 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     lb.load_library()
     cfg = {"2d_lec": WORKLOAD_2D, "2d_warmc": dict(WORKLOAD_2D, closure="warmc"), "3d_warmc": CONFIG_3D,
-           "3d_warmc_128": dict(CONFIG_3D, n=(128, 128, 128), z0=2.0), "axi_warmc": CONFIG_AXI,
+           "3d_warmc_128": dict(CONFIG_3D, n=(128, 128, 128), z0=2.0),
+           "3d_warmc_64": dict(CONFIG_3D, n=(64, 64, 64), z0=1.2), "axi_warmc": CONFIG_AXI,
            "axi_lec": dict(CONFIG_AXI, closure="lec")}[a.workload]
     cfg = dict(cfg)
     stream = torch.cuda.Stream(device=dev)
@@ -439,7 +441,7 @@ def run_ours(a):
         out["warning"] = "non-finite populations at the end of the timed run"
 
     fp64_peak = None
-    if rank == 0 and not a.no_modes:
+    if rank == 0 and (not a.no_modes or not a.no_configs):
         fp64_peak = lb.measure_fp64_rate()
         out["fp64_peak"] = {"value_tflops": round(fp64_peak / 1e12, 4), "source":
                             "lbpwfa_measure_fp64_rate (independent DFMA chains, CUDA events, this GPU)"}
@@ -449,15 +451,12 @@ def run_ours(a):
              "achieved_gbs": round(r["gbs"], 1), "frac_of_measured_hbm": round(r["frac"], 4),
              "bytes_per_update": r["bytes_per_update"], "stored_bytes_per_update": r["stored_bytes_per_update"],
              "steps": steps, "kernel": r["kernel"]}
-        if fp64_peak and workload.endswith("fp64"):
+        if workload.endswith("fp64"):
             # FP64 storage is bound by FP64 arithmetic on this GPU: FP64 operations per update
             # (2 DFMA + DADD + DMUL, counted by ncu on the same kernel) over the measured rate
-            fl = _flops64_for(f"{r['kernel']}:{workload}")
-            if fl is not None:
-                e["fp64_alu"] = {"bound": "alu", "flops_per_update": fl,
-                                 "achieved_tflops": round(fl * r["mlups"] * 1e6 / 1e12, 4),
-                                 "peak_tflops": round(fp64_peak / 1e12, 4),
-                                 "frac": round(fl * r["mlups"] * 1e6 / fp64_peak, 4)}
+            alu = _fp64_alu(r["kernel"], workload, r["mlups"], fp64_peak)
+            if alu:
+                e["fp64_alu"] = alu
         return e
 
     if rank == 0 and not a.no_modes and a.workload == "2d_lec":
@@ -481,7 +480,7 @@ def run_ours(a):
         out["precision_vs_fp64_3d"] = _precision_3d(stream)
 
     if rank == 0 and not a.no_configs and a.workload == "2d_lec":
-        out["configs_measured"] = _configs(stream, flush, hbm)
+        out["configs_measured"] = _configs(stream, flush, hbm, fp64_peak)
 
     if rank == 0 and not a.no_adjoint and a.workload == "2d_lec":
         out["adjoint"] = _adjoint(stream)
@@ -606,9 +605,20 @@ def _precision_table(cfg, stream, nsteps=2000):
     return res
 
 
-def _configs(stream, flush, hbm):
-    """The 1D configuration as a whole run (4000 steps, FP64) and the 3D
-    configuration (FP32 storage) over a few timed steps."""
+def _fp64_alu(kernel, workload, mlups, fp64_peak):
+    """FP64 ALU roofline entry of an FP64-storage measurement, or None."""
+    fl = _flops64_for(f"{kernel}:{workload}") if fp64_peak else None
+    if fl is None:
+        return None
+    rate = fl * mlups * 1e6
+    return {"bound": "alu", "flops_per_update": fl, "achieved_tflops": round(rate / 1e12, 4),
+            "peak_tflops": round(fp64_peak / 1e12, 4), "frac": round(rate / fp64_peak, 4)}
+
+
+def _configs(stream, flush, hbm, fp64_peak=None):
+    """The 1D configuration as a whole run (4000 steps, FP64), the batched
+    sweep, the axisymmetric grid and the 3D configuration over a few timed
+    steps."""
     import torch
 
     from paper_2309_04872_gb300 import lbpwfa as lb
@@ -664,6 +674,11 @@ def _configs(stream, flush, hbm):
                 "bytes_per_update": info.algorithmic_bytes_per_update,
                 "stored_bytes_per_update": info.bytes_per_update, "steps": len(times),
                 "kernel": KERNEL_NAMES[info.kernel_variant], "geometry": "axisymmetric (z, r)"}
+            if prec == "fp64":
+                alu = _fp64_alu(KERNEL_NAMES[info.kernel_variant], f"axi_{closure}_3000x600_fp64",
+                                info.ncell / (mean * 1e-3) / 1e6, fp64_peak)
+                if alu:
+                    res[f"axi_{closure}_{prec}_3000x600"]["fp64_alu"] = alu
     for prec in ("fp32", "fp64"):
         try:
             with lb.Run(CONFIG_3D, prec, stream=stream.cuda_stream) as run:
@@ -681,6 +696,11 @@ def _configs(stream, flush, hbm):
             "stored_bytes_per_update": info.bytes_per_update, "steps": len(times),
             "kernel": KERNEL_NAMES[info.kernel_variant],
             "device_gb": round(info.device_bytes / 1e9, 2)}
+        if prec == "fp64":
+            alu = _fp64_alu(KERNEL_NAMES[info.kernel_variant], "3d_warmc_512x256x256_fp64",
+                            info.ncell / (mean * 1e-3) / 1e6, fp64_peak)
+            if alu:
+                res[f"3d_warmc_{prec}_512x256x256"]["fp64_alu"] = alu
     return res
 
 
