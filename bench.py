@@ -71,7 +71,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32c", "fp16s"])
     ap.add_argument("--workload", default="2d_lec",
                     choices=["2d_lec", "2d_warmc", "3d_warmc", "3d_warmc_128", "3d_warmc_64", "adjoint_2d_warmc",
                              "batch_2d", "axi_warmc", "axi_lec"],
@@ -428,7 +428,7 @@ def run_ours(a):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if a.precision != "fp64" else "f64",
+        "dtype": "f64" if a.precision == "fp64" else "f32",
         "data": "synthetic",
         "config": _config_block(cfg, a.precision, {"kernel": main["kernel"]}),
         "roofline": {
@@ -475,12 +475,18 @@ def run_ours(a):
                     r = measure(prec, steps, 5, mu=mu, variant=variant)
                     key = f"lec_{prec}_mu{mu:g}" + {0: "", 1: "_plain", 2: "_box", 3: "_persistent"}[variant]
                     modes[key] = mode_entry(r, steps, f"2d_lec_1024x512_{prec}")
-        for prec in ("fp64", "fp32", "fp16s"):
+        # FP32 storage with exact set sums (the automatic kernel)
+        for mu in (1e-3, 1e-2):
+            r = measure("fp32c", 1000, 5, mu=mu, variant=0)
+            modes[f"lec_fp32c_mu{mu:g}"] = mode_entry(r, 1000, "2d_lec_1024x512_fp32c")
+        for prec in ("fp64", "fp32", "fp32c", "fp16s"):
             steps = 200 if prec == "fp64" else 600
             r = measure(prec, steps, 5, mu=1e-2, variant=0, closure="warmc")
             modes[f"warmc_{prec}_mu0.01"] = mode_entry(r, steps, f"2d_warmc_1024x512_{prec}")
         out["modes"] = modes
         out["precision_vs_fp64"] = _precision_table(cfg, stream)
+        # the 2D configuration's second temperature (k_B T / m c^2 = 1e-3)
+        out["precision_vs_fp64_mu1e-3"] = _precision_table(dict(cfg, mu=1e-3), stream)
         # the same check on the axisymmetric path (600 x 120 nodes of the 3D3V configuration's spacing 0.05)
         out["precision_vs_fp64_axisymmetric"] = _precision_table(
             dict(CONFIG_AXI, n=(600, 120), dx=0.05, z0=3.0), stream)
@@ -598,12 +604,12 @@ def _precision_table(cfg, stream, nsteps=2000):
     for closure in ("lec", "warmc"):
         c = dict(cfg, closure=closure)
         out = {}
-        for prec in ("fp64", "fp32", "fp16s"):
+        for prec in ("fp64", "fp32", "fp32c", "fp16s"):
             with lb.Run(c, prec, stream=stream.cuda_stream) as run:
                 run.step(nsteps)
                 out[prec] = (run.moments(lb.M_N)[0] - 1.0, run.fields(lb.F_EZ)[0])
         ref_n, ref_e = out["fp64"]
-        for prec in ("fp32", "fp16s"):
+        for prec in ("fp32", "fp32c", "fp16s"):
             n1, ez = out[prec]
             res[f"{closure}_{prec}"] = {
                 "rel_err_n_minus_1": float(np.linalg.norm(n1 - ref_n) / np.linalg.norm(ref_n)),

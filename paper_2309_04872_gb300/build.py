@@ -19,7 +19,7 @@ LIB = os.path.join(OUT, "liblbpwfa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo", "-Xcompiler", "-fPIC",
               "-diag-suppress", "177", "-I", INCLUDE]
-UNITS = ["lb_inst_f64.cu", "lb_inst_f32.cu", "lb_inst_f16s.cu", "lb_batch.cu", "lb_batch_f32.cu", "lb_batch_f64.cu",
+UNITS = ["lb_inst_f64.cu", "lb_inst_f32.cu", "lb_inst_f16s.cu", "lb_inst_f32c.cu", "lb_batch.cu", "lb_batch_f32.cu", "lb_batch_f64.cu",
          "lb_batch_f16s.cu", "lb_adjoint.cu", "runtime.cu", "adjoint_rt.cu"]
 
 

@@ -121,7 +121,9 @@ extern "C" int lbpwfa_record(lbpwfa_t h, const lbpwfa_record_params* rp) {
   adj_free(h);
   AdjRec* r = new AdjRec();
   h->adj = r;
-  if (!adjoint_kernels(h->prm.dim, h->prm.closure, h->prm.precision, &r->ak)) {
+  // exact-sum FP32 storage reverses with the FP32 kernels (the same real type)
+  const int adj_prec = h->prm.precision == LBPWFA_FP32C ? LBPWFA_FP32 : h->prm.precision;
+  if (!adjoint_kernels(h->prm.dim, h->prm.closure, adj_prec, &r->ak)) {
     adj_free(h);
     return LBPWFA_ERR_INVALID;
   }

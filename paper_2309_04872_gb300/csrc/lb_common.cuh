@@ -9,7 +9,10 @@
 namespace lbp {
 
 enum { CL_LEC = 0, CL_WARMC = 1 };
-enum { PR_F64 = 0, PR_F32 = 1, PR_F16S = 2 };
+// PR_F32C: FP32 storage whose set moments and post-collision remainders are
+// carried exactly (every rounding error of their sums kept, one rounding at
+// the end), at a higher cost per step than PR_F32.
+enum { PR_F64 = 0, PR_F32 = 1, PR_F16S = 2, PR_F32C = 3 };
 
 // ---------------------------------------------------------------------------
 // Lattices.  D3Q19 is the set of Fig. 1 (weights 1/3, 1/18, 1/36); D1Q3 and
@@ -105,6 +108,9 @@ template <int PR> struct Prec;
 template <> struct Prec<PR_F64> { using real = double; using store = double; };
 template <> struct Prec<PR_F32> { using real = float; using store = float; };
 template <> struct Prec<PR_F16S> { using real = float; using store = __half; };
+template <> struct Prec<PR_F32C> { using real = float; using store = float; };
+// whether a storage precision carries its set sums exactly
+template <int PR> __host__ __device__ constexpr bool exact_sums() { return PR == PR_F32C; }
 
 // Present field components on the dual Yee grid (component index z, x, y).
 template <int DIM> __host__ __device__ constexpr bool e_present(int a) {
@@ -232,6 +238,7 @@ template <> struct Codec<PR_F32> {
   }
   __device__ static void store0_u(float* p, long long i, float*, long long, float v) { gst(p + i, v); }
 };
+template <> struct Codec<PR_F32C> : Codec<PR_F32> {};
 // Binary16 of the scaled deviation.  The rest population takes the remainder
 // of its set's moment in the collision, so its rounding is the one error of
 // the node's moment that does not cancel; it carries a second binary16 with
@@ -307,6 +314,14 @@ __device__ __forceinline__ void two_float_add(float& hi, float& lo, float d) {
   const float l = __fadd_rn(lo, err);
   hi = __fadd_rn(s, l);
   lo = __fsub_rn(l, __fsub_rn(hi, s));
+}
+
+// Knuth's TwoSum: s = fl(a + b) and e with s + e == a + b exactly (FP32
+// operations only, uncontracted).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 // Uncontracted sums: the same rounding in every kernel that inlines them.

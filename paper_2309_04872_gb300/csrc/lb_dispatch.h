@@ -63,5 +63,6 @@ struct KernelSet {
 bool kernels_f64(int dim, int closure, KernelSet* ks);
 bool kernels_f32(int dim, int closure, KernelSet* ks);
 bool kernels_f16s(int dim, int closure, KernelSet* ks);
+bool kernels_f32c(int dim, int closure, KernelSet* ks);
 
 }  // namespace lbp

@@ -51,12 +51,57 @@ __device__ __forceinline__ real set_moment(const real* df) {
 // Deviation moment dA_k of a set pulled in storage units: the sum, times
 // 1/s_k for the scaled binary16 format (a power of two: the same bits as
 // summing the scaled-back populations).
+// The set sum with every rounding error kept (TwoSum) and one final
+// rounding (exact_sums precisions).
+template <int Q>
+__device__ __forceinline__ float set_moment_exact(const float* df) {
+  float s = df[0], c = 0.0f;
+#pragma unroll
+  for (int i = 1; i + 1 < Q; i += 2) {
+    float p, e1, e2;
+    two_sum(df[i], df[i + 1], p, e1);
+    two_sum(s, p, s, e2);
+    c = __fadd_rn(c, __fadd_rn(e1, e2));
+  }
+  return __fadd_rn(s, c);
+}
+
 template <int Q, int PR, typename real>
 __device__ __forceinline__ real set_dA(const real* df, float inv_s) {
+  if constexpr (exact_sums<PR>()) return set_moment_exact<Q>(df);
   const real m = set_moment<Q>(df);
   if constexpr (Codec<PR>::kScaled) return m * inv_s;
   return m;
 }
+
+// Running sum of the stored moving populations of a set, and the rest
+// population as the remainder (dA + dt F) - that sum: plainly, or with the
+// rounding errors carried (exact_sums) so the remainder is rounded once.
+template <int PR, typename real>
+struct Remainder {
+  static_assert(!exact_sums<PR>() || !Codec<PR>::kScaled, "the exact sums run in unscaled FP32");
+  real s = 0, c = 0;
+  __device__ __forceinline__ void add(real v) {
+    if constexpr (exact_sums<PR>()) {
+      float e;
+      two_sum(s, v, s, e);
+      c = __fadd_rn(c, e);
+    } else {
+      s = add_rn(s, v);
+    }
+  }
+  // (dA + dtF) us - sum
+  __device__ __forceinline__ real rest(real dA, real dtF, real us) const {
+    if constexpr (exact_sums<PR>()) {
+      float th, tl, dh, dl;
+      two_sum(dA, dtF, th, tl);
+      two_sum(th, -s, dh, dl);
+      return __fadd_rn(dh, __fsub_rn(__fadd_rn(dl, tl), c));
+    } else {
+      return sub_rn(add_rn(dA, dtF) * us, s);
+    }
+  }
+};
 
 // 3D models keep the loops over population sets rolled: one 19-velocity body
 // per loop instead of K (up to 11), so the step fits the instruction cache.
@@ -1011,7 +1056,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
     // df and the stored values are in storage units; us = s_k (FP16S) scales
     // the equilibrium and source parts into them (exactly: a power of two)
     const real us = Codec<PR>::kScaled ? real(sc) : real(1);
-    real moved = 0;
+    Remainder<PR, real> moved;
     if constexpr (PRE) {
       const real As = A * us;
       const real gs = (dA * itau + dtF) * us;
@@ -1020,8 +1065,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
         const int i = 1 + 2 * q, j = i + 1;
         const real evw = As * Ef[q] + real(L::w(i)) * gs;
         const real odd = As * Of[q];
-        moved = add_rn(moved, Codec<PR>::store_qu(fk, i * pl + id, df[i] * omt + (evw + odd)));
-        moved = add_rn(moved, Codec<PR>::store_qu(fk, j * pl + id, df[j] * omt + (evw - odd)));
+        moved.add(Codec<PR>::store_qu(fk, i * pl + id, df[i] * omt + (evw + odd)));
+        moved.add(Codec<PR>::store_qu(fk, j * pl + id, df[j] * omt + (evw - odd)));
       }
     } else {
 #pragma unroll
@@ -1034,12 +1079,11 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
         const real even = (wi * (dA + A * (base + real(4.5) * cu * cu))) * us;
         const real odd = ((real(3) * wi) * A * cu) * us;
         const real wF = (wi * dtF) * us;
-        moved = add_rn(moved, Codec<PR>::store_qu(fk, i * pl + id, df[i] * omt + (even + odd) * itau + wF));
-        moved = add_rn(moved, Codec<PR>::store_qu(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF));
+        moved.add(Codec<PR>::store_qu(fk, i * pl + id, df[i] * omt + (even + odd) * itau + wF));
+        moved.add(Codec<PR>::store_qu(fk, j * pl + id, df[j] * omt + (even - odd) * itau + wF));
       }
     }
-    Codec<PR>::store0_u(fk, id, fout + ((size_t)K * Q + k) * (size_t)P.plane, id,
-                        sub_rn(add_rn(dA, dtF) * us, moved));
+    Codec<PR>::store0_u(fk, id, fout + ((size_t)K * Q + k) * (size_t)P.plane, id, moved.rest(dA, dtF, us));
   };
   if constexpr (RollSets<DIM, K>::value) {
     // the sources first, into this thread's shared-memory column; the

@@ -65,6 +65,7 @@ template <> struct TmaTile2D<CL_LEC, PR_F64> { static constexpr int TZ = 32, TX 
 template <> struct TmaTile2D<CL_WARMC, PR_F32> { static constexpr int TZ = 32, TX = 4, MINB = 2; };
 template <> struct TmaTile2D<CL_WARMC, PR_F16S> { static constexpr int TZ = 32, TX = 8, MINB = 2; };
 template <> struct TmaTile2D<CL_WARMC, PR_F64> { static constexpr int TZ = 0, TX = 0, MINB = 1; };  // not staged
+template <int CL> struct TmaTile2D<CL, PR_F32C> : TmaTile2D<CL, PR_F32> {};
 
 template <int CL, int PR>
 struct TmaCfg2D {
@@ -169,6 +170,7 @@ template <> struct PersistTile2D<CL_LEC, PR_F64> { static constexpr int TZ = 32,
 template <> struct PersistTile2D<CL_WARMC, PR_F32> { static constexpr int TZ = 0, TX = 0, MINB = 1, AUTO = 0; };
 template <> struct PersistTile2D<CL_WARMC, PR_F16S> { static constexpr int TZ = 0, TX = 0, MINB = 1, AUTO = 0; };
 template <> struct PersistTile2D<CL_WARMC, PR_F64> { static constexpr int TZ = 0, TX = 0, MINB = 1, AUTO = 0; };
+template <int CL> struct PersistTile2D<CL, PR_F32C> : PersistTile2D<CL, PR_F32> {};
 
 template <int CL, int PR>
 struct PersistCfg2D {

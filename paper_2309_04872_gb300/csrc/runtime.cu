@@ -95,7 +95,7 @@ int validate(const lbpwfa_params* p) {
     return LBPWFA_ERR_INVALID;
   }
   if (p->dim >= 2 && !(p->sigma_r > 0.0)) return LBPWFA_ERR_INVALID;
-  if (p->precision < LBPWFA_FP64 || p->precision > LBPWFA_FP16S) return LBPWFA_ERR_INVALID;
+  if (p->precision < LBPWFA_FP64 || p->precision > LBPWFA_FP32C) return LBPWFA_ERR_INVALID;
   if (p->boundary != LBPWFA_OPEN && p->boundary != LBPWFA_PERIODIC) return LBPWFA_ERR_INVALID;
   if (p->kernel_variant < 0 || p->kernel_variant > 4) return LBPWFA_ERR_INVALID;
   if (p->geometry != LBPWFA_CARTESIAN && p->geometry != LBPWFA_AXISYMMETRIC) return LBPWFA_ERR_INVALID;
@@ -397,6 +397,7 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
   bool ok = false;
   if (p->precision == LBPWFA_FP64) ok = kernels_f64(dim, p->closure, &h->ks);
   else if (p->precision == LBPWFA_FP32) ok = kernels_f32(dim, p->closure, &h->ks);
+  else if (p->precision == LBPWFA_FP32C) ok = kernels_f32c(dim, p->closure, &h->ks);
   else ok = kernels_f16s(dim, p->closure, &h->ks);
   if (!ok) { delete h; return LBPWFA_ERR_INVALID; }
 
@@ -409,7 +410,7 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
   h->plane = (long long)h->nzp * h->n[1] * h->n[2];
   h->ncell = (long long)h->n[0] * h->n[1] * h->n[2];
   if ((long long)h->Q * h->plane >= (1LL << 31)) { delete h; return LBPWFA_ERR_INVALID; }  // 32-bit plane offsets
-  h->store_sz = p->precision == LBPWFA_FP64 ? 8 : (p->precision == LBPWFA_FP32 ? 4 : 2);
+  h->store_sz = p->precision == LBPWFA_FP64 ? 8 : (p->precision == LBPWFA_FP16S ? 2 : 4);
   h->real_sz = p->precision == LBPWFA_FP64 ? 8 : 4;
   h->dt = p->courant * p->dx;
   h->NPL = h->K * h->Q + (p->precision == LBPWFA_FP16S ? h->K : 0);
@@ -1346,6 +1347,7 @@ int lbpwfa_batch_create(const lbpwfa_params* p, int nruns, int flags, lbpwfa_bat
     int st = validate(&p[i]);
     if (st != LBPWFA_OK) return st;
     if (p[i].dim != 2 || p[i].precision != p[0].precision) return LBPWFA_ERR_INVALID;
+    if (p[i].precision == LBPWFA_FP32C) return LBPWFA_ERR_INVALID;  // single runs only
   }
   lbpwfa_batch_s* b = new lbpwfa_batch_s();
   b->precision = p[0].precision;

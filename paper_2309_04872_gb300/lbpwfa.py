@@ -16,10 +16,10 @@ import numpy as np
 from . import build as _build
 
 LEC, WARMC = 0, 1
-FP64, FP32, FP16S = 0, 1, 2
+FP64, FP32, FP16S, FP32C = 0, 1, 2, 3
 OPEN, PERIODIC = 0, 1
 CARTESIAN, AXISYMMETRIC = 0, 1
-_PREC = {"fp64": FP64, "fp32": FP32, "fp16s": FP16S}
+_PREC = {"fp64": FP64, "fp32": FP32, "fp16s": FP16S, "fp32c": FP32C}
 
 M_N, M_UZ, M_UX, M_UY, M_GAMMA, M_PZ, M_PX, M_PY = (1 << b for b in range(8))
 M_P0, M_LAMBDA = 1 << 8, 1 << 9

@@ -150,18 +150,19 @@ def test_fp64_adjoint_matches_finite_differences(closure):
         assert abs(g[k] - fd) <= 1e-6 * max(abs(fd), 1e-12), (name, g[k], fd)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp32c"])
 @pytest.mark.parametrize("closure", ["lec", "warmc"])
-def test_fp32_adjoint_within_1e4_of_fp64_finite_differences(closure):
+def test_fp32_adjoint_within_1e4_of_fp64_finite_differences(closure, prec):
     c = _cfg(2, closure, n=(128, 64), dx=0.05, mu=5e-3, alpha=0.1, sigma_z=1.0, sigma_r=0.5, z0=4.0)
     N = 300
-    _, g, _ = _gpu_adjoint(c, N, "fp32", C=50)
+    _, g, _ = _gpu_adjoint(c, N, prec, C=50)
     for k, name in enumerate(["alpha", "sigma_z", "sigma_r"]):
         h = 1e-4 * c[name]
         fd = (_J_gpu(dict(c, **{name: c[name] + h}), N) - _J_gpu(dict(c, **{name: c[name] - h}), N)) / (2 * h)
         assert abs(g[k] - fd) <= 1e-4 * abs(fd), (name, g[k], fd)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32c"])
 @pytest.mark.parametrize("closure", ["lec", "warmc"])
 def test_checkpointed_equals_kept_tape(precision, closure):
     prof = 0.2 * np.exp(-0.5 * (np.arange(-24, 25) * 0.05 / 0.6) ** 2)

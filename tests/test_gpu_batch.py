@@ -132,6 +132,13 @@ def test_batch_autotune_cache(tmp_path, monkeypatch):
     assert choice // 4 in (0, 1, 2) and choice % 4 in (0, 1, 2)
 
 
+def test_batch_rejects_exact_sum_storage():
+    """FP32C (exact set sums) is a single-run storage mode."""
+    with pytest.raises(lb.LbpwfaError) as ei:
+        lb.Batch(_runs()[:2], "fp32c", tune=False)
+    assert ei.value.status == -1
+
+
 def test_batch_rejects_mixed_inputs():
     runs = _runs()
     with pytest.raises(lb.LbpwfaError):

@@ -217,7 +217,7 @@ def test_fp64_3d_config3_reduced_grid_200_steps():
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("dim", [1, 2, 3])
 @pytest.mark.parametrize("closure", ["lec", "warmc"])
-@pytest.mark.parametrize("prec,tol,floor", [("fp32", 1e-4, 1e-7), ("fp16s", 2e-2, 1e-4)])
+@pytest.mark.parametrize("prec,tol,floor", [("fp32", 1e-4, 1e-7), ("fp32c", 1e-4, 1e-7), ("fp16s", 2e-2, 1e-4)])
 def test_reduced_precision_driver_parity(dim, closure, prec, tol, floor):
     """Bounds: the unit round-off of the stored deviations (2^-24, 2^-11)
     times the amplification of the field source, where curl B and the driver
@@ -234,7 +234,7 @@ def test_reduced_precision_driver_parity(dim, closure, prec, tol, floor):
 # ---------------------------------------------------------------------------
 # Invariants that hold at any size
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", ["fp32", "fp16s"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32c", "fp16s"])
 @pytest.mark.parametrize("dim,closure", [(1, "lec"), (2, "warmc"), (3, "lec")])
 def test_rest_state_is_exact_in_shifted_storage(prec, dim, closure):
     cfg = _cfg(dim, closure, "periodic", alpha=0.0, init_fields=False)
@@ -248,7 +248,7 @@ def test_rest_state_is_exact_in_shifted_storage(prec, dim, closure):
 
 
 @pytest.mark.parametrize("closure", ["lec", "warmc"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32c", "fp16s"])
 def test_mass_conservation_periodic(prec, closure):
     """Total mass after 50 steps.  The rest population takes the remainder
     of each set's moment, so only its own rounding changes the mass: FP32
@@ -265,7 +265,7 @@ def test_mass_conservation_periodic(prec, closure):
         assert bad == 0
         # measured 5e-10 (FP32) and 6e-11 (FP16S); without the low part of
         # the rest population the FP16S drift is of order 1e-6
-        tol = {"fp64": 1e-12, "fp32": 1e-8, "fp16s": 1e-8}[prec]
+        tol = {"fp64": 1e-12, "fp32": 1e-8, "fp32c": 1e-8, "fp16s": 1e-8}[prec]
         print(f"mass drift {prec} {closure}: {abs(m1 - m0) / abs(m0):.3e}")
         assert abs(m1 - m0) <= tol * abs(m0)
 
@@ -292,6 +292,28 @@ def test_reduced_precision_wake_after_2000_steps(closure):
         en = np.linalg.norm(n1 - n_ref) / np.linalg.norm(n_ref)
         ee = np.linalg.norm(ez - e_ref) / np.linalg.norm(e_ref)
         assert en <= tol and ee <= tol, (prec, en, ee)
+
+
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+@pytest.mark.parametrize("mu", [1e-3, 1e-2])
+def test_exact_sum_fp32_meets_1e6_after_2000_steps(closure, mu):
+    """FP32 storage with exact set sums (FP32C) against the FP64 path after
+    2000 steps, at the two temperatures of the 2D configuration: n - 1 and
+    E_z within 1e-6.  Plain FP32 storage reaches 1.1-1.2e-6 on n - 1 at
+    mu = 1e-3: the rounding of the set sums and remainders, which FP32C
+    carries, is the larger part of its error."""
+    cfg = dict(_WAKE_2D, closure=closure, mu=mu)
+    out = {}
+    for prec in ("fp64", "fp32c"):
+        with lb.Run(cfg, prec) as run:
+            run.step(2000)
+            out[prec] = (run.moments(lb.M_N)[0] - 1.0, run.fields(lb.F_EZ)[0])
+    n_ref, e_ref = out["fp64"]
+    n1, ez = out["fp32c"]
+    en = np.linalg.norm(n1 - n_ref) / np.linalg.norm(n_ref)
+    ee = np.linalg.norm(ez - e_ref) / np.linalg.norm(e_ref)
+    print(f"fp32c {closure} mu {mu}: n-1 {en:.3e}, E_z {ee:.3e}")
+    assert en <= 1e-6 and ee <= 1e-6, (en, ee)
 
 
 def test_reduce_matches_oracle():
