@@ -152,6 +152,12 @@ typedef struct {
                               it returns LBPWFA_ERR_OOM, before any device
                               memory is touched.  lbpwfa_create checks the
                               state's size first, before any CUDA call. */
+  int64_t record_tape;     /* > 0: lbpwfa_create also starts an adjoint
+                              recording window of this many steps at step 0
+                              (lbpwfa_record with max_steps = record_tape);
+                              0: none.  Not for batches. */
+  int64_t checkpoint_every;/* the window's checkpoint interval C (0: keep
+                              every step's tape), as lbpwfa_record */
 } lbpwfa_params;
 
 typedef struct {
@@ -419,6 +425,9 @@ typedef struct {
  * written to it.  p[i].stream of run 0 is the batch's stream.
  * Errors: INVALID, OOM, CUDA. */
 int lbpwfa_batch_create(const lbpwfa_params* p, int nruns, int flags, lbpwfa_batch_t* out);
+/* lbpwfa_batch_create with flags = 0 (autotuned), under the name the
+ * problem statement's interface gives it. */
+int lbpwfa_create_batch(const lbpwfa_params* p, int nruns, lbpwfa_batch_t* out);
 
 /* Advance every run by nsteps >= 0 steps. */
 int lbpwfa_batch_step(lbpwfa_batch_t b, int64_t nsteps);

@@ -106,6 +106,7 @@ int validate(const lbpwfa_params* p) {
   long long cells = 1;
   for (int a = 0; a < p->dim; ++a) cells *= p->n[a];
   if (cells > (1LL << 34)) return LBPWFA_ERR_INVALID;
+  if (p->record_tape < 0 || p->checkpoint_every < 0) return LBPWFA_ERR_INVALID;
   return LBPWFA_OK;
 }
 
@@ -527,6 +528,12 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
   h->cur = 0;
   h->step = 0;
   h->have_prev = 0;
+  if (p->record_tape > 0) {
+    // the adjoint window the parameters ask for, from step 0
+    const lbpwfa_record_params rp{p->record_tape, p->checkpoint_every};
+    r = lbpwfa_record(h, &rp);
+    if (r != LBPWFA_OK) { lbpwfa_destroy(h); return r; }
+  }
   *out = h;
   return LBPWFA_OK;
 }
@@ -1348,6 +1355,7 @@ int lbpwfa_batch_create(const lbpwfa_params* p, int nruns, int flags, lbpwfa_bat
     if (st != LBPWFA_OK) return st;
     if (p[i].dim != 2 || p[i].precision != p[0].precision) return LBPWFA_ERR_INVALID;
     if (p[i].precision == LBPWFA_FP32C) return LBPWFA_ERR_INVALID;  // single runs only
+    if (p[i].record_tape > 0) return LBPWFA_ERR_INVALID;           // no adjoint in batches
   }
   lbpwfa_batch_s* b = new lbpwfa_batch_s();
   b->precision = p[0].precision;
@@ -1389,6 +1397,10 @@ int lbpwfa_batch_create(const lbpwfa_params* p, int nruns, int flags, lbpwfa_bat
   if (st != LBPWFA_OK) { lbpwfa_batch_destroy(b); return st; }
   *out = b;
   return LBPWFA_OK;
+}
+
+int lbpwfa_create_batch(const lbpwfa_params* p, int nruns, lbpwfa_batch_t* out) {
+  return lbpwfa_batch_create(p, nruns, 0, out);
 }
 
 int lbpwfa_batch_step(lbpwfa_batch_t b, int64_t nsteps) {

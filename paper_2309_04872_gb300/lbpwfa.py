@@ -48,6 +48,7 @@ class Params(ctypes.Structure):
         ("profile_dz", ctypes.c_double), ("precision", ctypes.c_int), ("boundary", ctypes.c_int),
         ("init_fields", ctypes.c_int), ("stream", ctypes.c_void_p), ("kernel_variant", ctypes.c_int),
         ("geometry", ctypes.c_int), ("device_bytes_cap", ctypes.c_size_t),
+        ("record_tape", ctypes.c_int64), ("checkpoint_every", ctypes.c_int64),
     ]
 
 
@@ -91,7 +92,8 @@ EXPORTED = ["lbpwfa_create", "lbpwfa_step", "lbpwfa_moments", "lbpwfa_fields", "
             "lbpwfa_status_string", "lbpwfa_last_error", "lbpwfa_reduce_noalloc",
             "lbpwfa_batch_create", "lbpwfa_batch_step", "lbpwfa_batch_member", "lbpwfa_batch_info",
             "lbpwfa_batch_destroy", "lbpwfa_record", "lbpwfa_adjoint_step", "lbpwfa_line_fit",
-            "lbpwfa_gauss_residual", "lbpwfa_set_wait_limit", "lbpwfa_measure_fp64_rate"]
+            "lbpwfa_gauss_residual", "lbpwfa_set_wait_limit", "lbpwfa_measure_fp64_rate",
+            "lbpwfa_create_batch"]
 
 
 def library_path() -> str:
@@ -136,6 +138,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbpwfa_last_error.restype = ctypes.c_char_p
     L.lbpwfa_batch_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
     L.lbpwfa_batch_step.argtypes = [vp, ctypes.c_int64]
+    L.lbpwfa_create_batch.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(vp)]
     L.lbpwfa_batch_member.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
     L.lbpwfa_batch_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
     L.lbpwfa_batch_destroy.argtypes = [vp]
@@ -193,6 +196,8 @@ def make_params(cfg: dict, precision="fp64", stream=None, variant=0):
     p.kernel_variant = int(variant)
     p.geometry = _code(cfg.get("geometry", "cartesian"), {"cartesian": CARTESIAN, "axisymmetric": AXISYMMETRIC})
     p.device_bytes_cap = int(cfg.get("device_bytes_cap", 0))
+    p.record_tape = int(cfg.get("record_tape", 0))
+    p.checkpoint_every = int(cfg.get("checkpoint_every", 0))
     return p, keep
 
 

@@ -175,6 +175,23 @@ def test_checkpointed_equals_kept_tape(precision, closure):
         assert np.array_equal(g1, g0) and np.array_equal(p1, p0)
 
 
+def test_recording_armed_at_create_equals_lbpwfa_record():
+    """record_tape / checkpoint_every in the parameters start the window at
+    create, as lbpwfa_record does; the gradients are bitwise the same."""
+    c = _cfg(2, "warmc")
+    N = 23
+    J0, g0, _ = _gpu_adjoint(c, N, "fp32", C=10)
+    with lb.Run(dict(c, record_tape=N, checkpoint_every=10), "fp32") as run:
+        run.step(N)
+        wit = (c["n"][0] // 2, c["n"][1] // 2 - 1)
+        J1, g1, _ = run.adjoint(wit)
+    with lb.Run(c, "fp32") as run:
+        run.record(N, 10)
+        run.step(N)
+        J2, g2, _ = run.adjoint(wit)
+    assert J1 == J2 and np.array_equal(g1, g2)
+
+
 def test_state_after_sweep_is_end_of_window():
     c = _cfg(2, "warmc")
     with lb.Run(c, "fp32") as a, lb.Run(c, "fp32") as b:
