@@ -595,7 +595,7 @@ static void init_fields(orc_state* S)
       double tE = -0.5 * S->dt;
       /* E_x slot at (x, y + dx/2, z + dx/2) */
       {
-        double z = pos[0] + 0.5 * dx, x = pos[1], y = pos[2] + 0.5 * dx;
+        double z = pos[0] + PLANTED(18, 0.5 * dx, 0.0), x = pos[1], y = pos[2] + 0.5 * dx;
         double s = (x * x + y * y) / (2.0 * sr * sr);
         double fr = s > 0 ? -expm1(-s) / (2.0 * s) : 0.5;
         S->E[1 * nc + c] = -driver_long(p, z - p->z0 - tE) * x * fr;

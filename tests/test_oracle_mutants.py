@@ -53,6 +53,8 @@ MUTANTS = {
          [J + "test_adjoint_driver_parameters", J + "test_adjoint_starting_state"]),
     17: ("WARMC source: the backward time derivative of theta^{0a} dropped from the n lambda u row",
          [P + "test_warm_dispersion_1d3v"]),
+    18: ("3D initial field: an E_x slot taken half a cell low in z (Sec. 6, the v -> c field on the Yee grid)",
+         [P + "test_gauss_law_of_the_3d_initial_field"]),
 }
 
 
