@@ -26,22 +26,35 @@ struct AdjRec {
   size_t state_bytes = 0;   // one checkpoint: f, E, B, prev
   Buf tape, ckpt, prev0, finalst;
   std::vector<int> ckpt_have_prev;
-  Buf lf[2], lE[2], lB[2], lp[2], rA, rG, rEn, rBn;
+  Buf lf[2], lE[2], lB[2], lp[2], rA, rG, rEn, rBn, cA, cF, cU, lAf;
   Buf rows, setp, gpart, g3, gp, Tx, Kx, jv;
   int ntx = 1;
   size_t bytes = 0;
+  // checkpoints: the next segment is recomputed on a second stream while
+  // this one is reversed; each has its own half of the tape
+  cudaStream_t rs = nullptr;
+  cudaEvent_t ev_rec[2] = {nullptr, nullptr};  // tape half filled
+  cudaEvent_t ev_rev[2] = {nullptr, nullptr};  // tape half consumed
 };
 
 namespace {
 
 void free_rec(lbpwfa_s* h, AdjRec* r) {
   Buf* all[] = {&r->tape, &r->ckpt, &r->prev0, &r->finalst, &r->lf[0], &r->lf[1], &r->lE[0], &r->lE[1],
-                &r->lB[0], &r->lB[1], &r->lp[0], &r->lp[1], &r->rA, &r->rG, &r->rEn, &r->rBn, &r->rows,
+                &r->lB[0], &r->lB[1], &r->lp[0], &r->lp[1], &r->rA, &r->rG, &r->rEn, &r->rBn, &r->cA,
+                &r->cF, &r->cU, &r->lAf, &r->rows,
                 &r->setp, &r->gpart, &r->g3, &r->gp, &r->Tx, &r->Kx, &r->jv};
   for (Buf* b : all) {
     h->device_bytes -= b->bytes;
     release(*b);
   }
+  for (int j = 0; j < 2; ++j) {
+    if (r->ev_rec[j]) cudaEventDestroy(r->ev_rec[j]);
+    if (r->ev_rev[j]) cudaEventDestroy(r->ev_rev[j]);
+    r->ev_rec[j] = r->ev_rev[j] = nullptr;
+  }
+  if (r->rs) cudaStreamDestroy(r->rs);
+  r->rs = nullptr;
 }
 
 int ab(lbpwfa_s* h, AdjRec* r, Buf& b, size_t bytes) {
@@ -139,10 +152,16 @@ extern "C" int lbpwfa_record(lbpwfa_t h, const lbpwfa_record_params* rp) {
     if (st == LBPWFA_OK && h->prev.bytes) st = ab(h, r, r->prev0, h->prev.bytes);
   } else {
     const long long nck = (r->cap + r->C - 1) / r->C;
-    st = ab(h, r, r->tape, (size_t)r->C * r->entry_bytes);
+    st = ab(h, r, r->tape, 2 * (size_t)r->C * r->entry_bytes);
     if (st == LBPWFA_OK) st = ab(h, r, r->ckpt, (size_t)nck * r->state_bytes);
     if (st == LBPWFA_OK) st = ab(h, r, r->finalst, r->state_bytes);
     r->ckpt_have_prev.assign((size_t)nck, 0);
+    cudaError_t e = cudaStreamCreateWithFlags(&r->rs, cudaStreamNonBlocking);
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+      e = cudaEventCreateWithFlags(&r->ev_rec[j], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_rev[j], cudaEventDisableTiming);
+    }
+    if (st == LBPWFA_OK && e != cudaSuccess) st = fail_cuda(h, e, "lbpwfa_record: recompute stream");
   }
   const size_t popb = (size_t)h->K * h->Q * pl * rs, fldb = 3 * pl * rs;
   for (int j = 0; j < 2 && st == LBPWFA_OK; ++j) {
@@ -153,6 +172,10 @@ extern "C" int lbpwfa_record(lbpwfa_t h, const lbpwfa_record_params* rp) {
   }
   if (st == LBPWFA_OK) st = ab(h, r, r->rA, (size_t)r->ak.K * pl * rs);
   if (st == LBPWFA_OK) st = ab(h, r, r->rG, (size_t)r->ak.NG * pl * rs);
+  if (st == LBPWFA_OK) st = ab(h, r, r->cA, (size_t)r->ak.K * pl * rs);
+  if (st == LBPWFA_OK) st = ab(h, r, r->cF, (size_t)r->ak.K * pl * rs);
+  if (st == LBPWFA_OK) st = ab(h, r, r->cU, (size_t)r->ak.K * h->prm.dim * pl * rs);
+  if (st == LBPWFA_OK) st = ab(h, r, r->lAf, (size_t)r->ak.K * pl * rs);
   if (st == LBPWFA_OK) st = ab(h, r, r->rEn, fldb);
   if (st == LBPWFA_OK) st = ab(h, r, r->rBn, fldb);
   if (st == LBPWFA_OK) st = ab(h, r, r->rows, (size_t)kRowSets * 2 * r->ntx * h->n[0] * sizeof(double));
@@ -271,13 +294,22 @@ struct Sweep {
     A.rG = r->rG.p;
     A.rEn = r->rEn.p;
     A.rBn = r->rBn.p;
+    A.cA = r->cA.p;
+    A.cF = r->cF.p;
+    A.cU = r->cU.p;
+    A.lAf = r->lAf.p;
     A.rows = rows_of_set(nsets);
     A.Tx = (const double*)r->Tx.p;
     const dim3 g((unsigned)((h->n[0] + r->ak.tz - 1) / r->ak.tz), (unsigned)r->ntx, 1);
+    const dim3 gk(g.x, g.y, (unsigned)r->ak.K);
+    r->ak.coll(A, gk, h->stream);
+    CK_LAUNCH(h, "adj_coll_kernel launch");
     r->ak.local(A, g, h->stream);
     CK_LAUNCH(h, "adj_local_kernel launch");
     r->ak.field(A, g, h->stream);
     CK_LAUNCH(h, "adj_field_kernel launch");
+    r->ak.pop(A, gk, h->stream);
+    CK_LAUNCH(h, "adj_pop_kernel launch");
     setp.push_back(make_double2(zeta0_of(h->prm.z0, r->start_step + j, h->dt), 0.0));
     nsets += 1;
     cl = 1 - cl;
@@ -334,24 +366,43 @@ extern "C" int lbpwfa_adjoint_step(lbpwfa_t h, lbpwfa_adjoint_io* io) {
     int st = save_state(h, (char*)r->finalst.p);
     if (st != LBPWFA_OK) return st;
     const long long nseg = (r->len + r->C - 1) / r->C;
-    for (long long s = nseg - 1; s >= 0; --s) {
+    // segment s is recomputed into tape half s % 2 on the second stream, as
+    // soon as the reverse of segment s + 2 has consumed that half, so the
+    // recompute of segment s - 1 runs while segment s is reversed
+    cudaStream_t ms = h->stream;
+    auto half = [&](long long s) { return (char*)r->tape.p + (size_t)(s & 1) * r->C * r->entry_bytes; };
+    for (int j = 0; j < 2; ++j) CK(h, cudaEventRecord(r->ev_rev[j], ms));  // after the state was saved
+    auto recompute = [&](long long s) -> int {
       const long long b = s * r->C, e = std::min(r->len, b + r->C);
-      const char* ck = (const char*)r->ckpt.p + (size_t)s * r->state_bytes;
-      st = restore_state(h, ck);
-      if (st != LBPWFA_OK) return st;
+      CK(h, cudaStreamWaitEvent(r->rs, r->ev_rev[s & 1], 0));
+      h->stream = r->rs;
+      int rc = restore_state(h, (const char*)r->ckpt.p + (size_t)s * r->state_bytes);
       h->step = r->start_step + b;
       h->have_prev = r->ckpt_have_prev[s];
-      for (long long j = b; j < e; ++j) {
-        st = launch_step(h, (char*)r->tape.p + (size_t)(j - b) * r->entry_bytes);
+      for (long long j = b; j < e && rc == LBPWFA_OK; ++j) rc = launch_step(h, half(s) + (size_t)(j - b) * r->entry_bytes);
+      h->stream = ms;
+      if (rc != LBPWFA_OK) return rc;
+      CK(h, cudaEventRecord(r->ev_rec[s & 1], r->rs));
+      return LBPWFA_OK;
+    };
+    st = recompute(nseg - 1);
+    if (st != LBPWFA_OK) return st;
+    for (long long s = nseg - 1; s >= 0; --s) {
+      const long long b = s * r->C, e = std::min(r->len, b + r->C);
+      CK(h, cudaStreamWaitEvent(ms, r->ev_rec[s & 1], 0));
+      if (s > 0) {
+        st = recompute(s - 1);
         if (st != LBPWFA_OK) return st;
       }
+      const char* ck = (const char*)r->ckpt.p + (size_t)s * r->state_bytes;
       const char* prev_ck = h->prev.bytes ? ck + h->f[0].bytes + 2 * h->E[0].bytes : nullptr;
       for (long long j = e - 1; j >= b; --j) {
-        const char* en = (const char*)r->tape.p + (size_t)(j - b) * r->entry_bytes;
+        const char* en = half(s) + (size_t)(j - b) * r->entry_bytes;
         st = S.reverse(j, en, j > b ? en - r->entry_bytes : nullptr, j > b ? nullptr : prev_ck, first);
         if (st != LBPWFA_OK) return st;
         first = false;
       }
+      CK(h, cudaEventRecord(r->ev_rev[s & 1], ms));
     }
   }
   int st = S.flush();

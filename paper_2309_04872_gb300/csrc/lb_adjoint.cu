@@ -10,16 +10,24 @@ template <int DIM> struct AdjTile;
 template <> struct AdjTile<1> { static constexpr int TZ = 128, TX = 1; };
 template <> struct AdjTile<2> { static constexpr int TZ = 32, TX = 8; };
 
-// Resident CTAs per SM the register budget is held to (latency-bound
-// gathers want warps; FP32 WARMC 2D, 1000-step sweep: 1/1 CTAs 117 ms,
-// 2/2 103 ms, 3/3 107 ms, 3/4 101 ms); FP64 unconstrained.
+// Resident CTAs per SM the per-node kernels' register budget is held to
+// (latency-bound chains want warps).  FP32 WARMC 2D, 1000-step reverse sweep
+// with the population gathers inside them: 1/1 CTAs 117 ms, 2/2 103, 3/3
+// 107, 3/4 101; with the gathers in the per-set kernels: 3/4 74 ms, 4/4 70,
+// 4/5 76 (adj_local at 5 spills).  FP64 unconstrained.
 template <typename real> struct AdjMinBlocks { static constexpr int LOCAL = 1, FIELD = 1; };
-template <> struct AdjMinBlocks<float> { static constexpr int LOCAL = 3, FIELD = 4; };
+template <> struct AdjMinBlocks<float> { static constexpr int LOCAL = 4, FIELD = 4; };
 
 template <int DIM, int CL, int PR>
 struct AdjImpl {
   using real = typename Prec<PR>::real;
   using T = AdjTile<DIM>;
+  static void coll(const AdjParams& A, dim3 g, cudaStream_t s) {
+    adj_coll_kernel<DIM, CL, real, T::TZ, T::TX><<<g, T::TZ * T::TX, 0, s>>>(A);
+  }
+  static void pop(const AdjParams& A, dim3 g, cudaStream_t s) {
+    adj_pop_kernel<DIM, CL, real, T::TZ, T::TX><<<g, T::TZ * T::TX, 0, s>>>(A);
+  }
   static void local(const AdjParams& A, dim3 g, cudaStream_t s) {
     adj_local_kernel<DIM, CL, real, T::TZ, T::TX, AdjMinBlocks<real>::LOCAL><<<g, T::TZ * T::TX, 0, s>>>(A);
   }
@@ -46,8 +54,10 @@ struct AdjImpl {
     k->NTAPE = AM::NTAPE;
     k->tz = T::TZ;
     k->tx = T::TX;
+    k->coll = &coll;
     k->local = &local;
     k->field = &field;
+    k->pop = &pop;
     k->init_rows = &init_rows;
     k->seed = &seed;
     k->read_slot = &read_slot;

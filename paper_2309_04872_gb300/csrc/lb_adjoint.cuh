@@ -11,19 +11,23 @@
 // reverse step applies the transpose of each stage in the opposite order.
 // Every transposed stencil is written in gather ("pull") form, so each node
 // computes its own adjoint without atomics:
-//   adj_local_kernel  - per node: adjoint of streaming (gather of the next
-//     state's population adjoints, folding the boundary copies), of the
-//     collision and of the sources' local terms; publishes small records
-//     for the neighbours: the decode adjoint of its local part, the
+//   adj_coll_kernel   - per node and set: the gather of the next state's
+//     population adjoints (folding the boundary copies) and the adjoint of
+//     streaming and collision for that set.  One thread per (node, set),
+//     so the gathers run in parallel instead of on each node's chain.
+//   adj_local_kernel  - per node: the collision adjoints summed over the
+//     sets, and the adjoint of the sources' local terms; publishes small
+//     records for the neighbours: the decode adjoint of its local part, the
 //     coefficients of its gradient stencils, and the adjoints of its
 //     node-averaged E^{n+1/2} and B^n.
 //   adj_field_kernel  - per node: adjoint of E^{n+1/2} at the slots around
 //     the node (next-state E, B update, node averages), of B^n (E update,
 //     node average), of the decoded values (neighbours' gradient records,
-//     the current n u), the decode adjoint, and the population adjoint
-//     lambda_f^n = (1 - 1/tau) lambda_fs + lambda_A; plus per-row partial
-//     sums of dt lambda(E_z) times the driver's transverse factor, from
-//     which the driver-parameter gradients are formed.
+//     the current n u) and the decode adjoint, giving lambda_A; plus per-row
+//     partial sums of dt lambda(E_z) times the driver's transverse factor,
+//     from which the driver-parameter gradients are formed.
+//   adj_pop_kernel    - per node and set: the population adjoint
+//     lambda_f^n = (1 - 1/tau) lambda_fs + lambda_A.
 // The step's forward values come from the tape the step kernel wrote while
 // recording: its deviation moments dA^n (decoded here exactly as the step
 // decoded them), E^{n+1/2} and B^n; the previous step's values of the WARMC
@@ -299,10 +303,10 @@ __device__ __forceinline__ void decode_adjoint(const StepParams& P, const StepCo
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 1: streaming, collision and local source adjoints.
+// Kernel 2: collision adjoints summed over the sets, local source adjoints.
 // ---------------------------------------------------------------------------
-template <int DIM, int CL, typename real, class LSrc>
-__device__ __forceinline__ void adj_local_node(const AdjParams& A, const LSrc& src, int z, int x) {
+template <int DIM, int CL, typename real>
+__device__ __forceinline__ void adj_local_node(const AdjParams& A, int z, int x) {
   using M = Model<DIM, CL>;
   using AM = AdjModel<DIM, CL>;
   using L = Lattice<DIM>;
@@ -392,47 +396,19 @@ __device__ __forceinline__ void adj_local_node(const AdjParams& A, const LSrc& s
     }
   }
 
-  // ---- streaming + collision adjoint --------------------------------------
-  // fs = f (1 - 1/tau) + f^eq(A, C u)/tau + w dt F with
-  // f^eq = w A (1 + 3 cu + 9/2 cu^2 - 3/2 u^2):
-  //   lambda_A += sum_i w_i (1 + P_i) lambda_fs / tau
-  //   lambda_u += sum_i w_i A C (3 xi + 9 cu xi - 3 u) lambda_fs / tau
-  //   lambda_F  = dt sum_i w_i lambda_fs
-  real ul[3] = {0, 0, 0}, usq = 0;
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) { ul[a] = S.courant * u[a]; usq += ul[a] * ul[a]; }
-  // opposite velocities (i, i + 1) share w_i and |cu|: with s = l_i + l_j and
-  // d = l_i - l_j the even part carries 1 + 9/2 cu^2 - 3/2 u^2, the odd 3 cu
-  static_assert(opposite_pairs<DIM>(), "lattice order must pair opposite velocities");
+  // ---- streaming + collision adjoint (per set, adj_coll_kernel) -----------
   real lA[K], lF[K], lu_c[3] = {0, 0, 0};
-  const real even0 = real(1) - real(1.5) * usq;
+  {
+    const real* cA = reinterpret_cast<const real*>(A.cA);
+    const real* cF = reinterpret_cast<const real*>(A.cF);
+    const real* cU = reinterpret_cast<const real*>(A.cU);
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    real lk[Q];
-    src.load(k, z, x, lk);
-    const real w0l = real(L::w(0)) * lk[0];
-    real m0 = w0l, mA = w0l * even0, mu_[3] = {0, 0, 0};
+    for (int k = 0; k < K; ++k) {
+      lA[k] = gld(cA + k * pl + id);
+      lF[k] = gld(cF + k * pl + id);
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) mu_[a] = -real(3) * ul[a] * w0l;
-#pragma unroll
-    for (int q = 0; q < (Q - 1) / 2; ++q) {
-      const int i = 1 + 2 * q;
-      const real wi = real(L::w(i));
-      const real sp = wi * (lk[i] + lk[i + 1]), dm = wi * (lk[i] - lk[i + 1]);
-      real cu = 0;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) cu += real(L::c(i, a)) * ul[a];
-      m0 += sp;
-      mA += sp * (even0 + real(4.5) * cu * cu) + real(3) * cu * dm;
-      const real t = real(3) * dm + real(9) * cu * sp;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) mu_[a] += real(L::c(i, a)) * t - real(3) * ul[a] * sp;
+      for (int a = 0; a < DIM; ++a) lu_c[a] += gld(cU + (k * DIM + a) * pl + id);
     }
-    const real Ak = S.Arest[k] + N.dA[k];
-    lA[k] = mA * S.inv_tau;
-    lF[k] = S.dt * m0;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) lu_c[a] += Ak * mu_[a];
   }
 #pragma unroll
   for (int a = 0; a < DIM; ++a) lm.u[a] += lu_c[a] * S.courant * S.inv_tau;
@@ -555,17 +531,89 @@ __global__ void __launch_bounds__(TZ* TX, MINB) adj_local_kernel(const AdjParams
   const StepParams& P = A.P;
   const int z = blockIdx.x * TZ + threadIdx.x % TZ;
   const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
+  if (z >= P.n[0] || (DIM >= 2 && x >= P.n[1])) return;
+  adj_local_node<DIM, CL, real>(A, z, x);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 1 (launched first): streaming and collision adjoints per set.
+// ---------------------------------------------------------------------------
+
+// Streaming + collision adjoint of one set k at one node, the gather of the
+// next state's population adjoints kept off the per-node kernels' chains:
+// fs = f (1 - 1/tau) + f^eq(A, C u)/tau + w dt F with
+// f^eq = w A (1 + 3 cu + 9/2 cu^2 - 3/2 u^2) gives
+//   lambda_A += sum_i w_i (1 + P_i) lambda_fs / tau
+//   lambda_u += sum_i w_i A C (3 xi + 9 cu xi - 3 u) lambda_fs / tau
+//   lambda_F  = dt sum_i w_i lambda_fs.
+// Written: cA = the first, cF = the third, cU = A_k times the sum of the
+// second (adj_local adds C/tau times its sum over the sets, in set order).
+template <int DIM, int CL, typename real, class LSrc>
+__device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& src, int z, int x, int k) {
+  using L = Lattice<DIM>;
+  constexpr int Q = L::Q;
+  const StepParams& P = A.P;
+  const StepConst<real>& S = consts<real>(P);
+  const int pl = (int)P.plane;
+  const int id = aidx(P, z, x);
+  Node<DIM, CL, real> N;
+  load_node<DIM, CL, real>(P, reinterpret_cast<const real*>(A.tape), id, N);
+  real ul[3] = {0, 0, 0}, usq = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    ul[a] = S.courant * N.rec[Model<DIM, CL>::R_U + a];
+    usq += ul[a] * ul[a];
+  }
+  // opposite velocities (i, i + 1) share w_i and |cu|: with s = l_i + l_j and
+  // d = l_i - l_j the even part carries 1 + 9/2 cu^2 - 3/2 u^2, the odd 3 cu
+  static_assert(opposite_pairs<DIM>(), "lattice order must pair opposite velocities");
+  const real even0 = real(1) - real(1.5) * usq;
+  real lk[Q];
+  src.load(k, z, x, lk);
+  const real w0l = real(L::w(0)) * lk[0];
+  real m0 = w0l, mA = w0l * even0, mu_[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) mu_[a] = -real(3) * ul[a] * w0l;
+#pragma unroll
+  for (int q = 0; q < (Q - 1) / 2; ++q) {
+    const int i = 1 + 2 * q;
+    const real wi = real(L::w(i));
+    const real sp = wi * (lk[i] + lk[i + 1]), dm = wi * (lk[i] - lk[i + 1]);
+    real cu = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) cu += real(L::c(i, a)) * ul[a];
+    m0 += sp;
+    mA += sp * (even0 + real(4.5) * cu * cu) + real(3) * cu * dm;
+    const real t = real(3) * dm + real(9) * cu * sp;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) mu_[a] += real(L::c(i, a)) * t - real(3) * ul[a] * sp;
+  }
+  const real Ak = S.Arest[k] + N.dA[k];
+  reinterpret_cast<real*>(A.cA)[k * pl + id] = mA * S.inv_tau;
+  reinterpret_cast<real*>(A.cF)[k * pl + id] = S.dt * m0;
+  real* cU = reinterpret_cast<real*>(A.cU);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) cU[(k * DIM + a) * pl + id] = Ak * mu_[a];
+}
+
+// grid: (z tiles, x tiles, K)
+template <int DIM, int CL, typename real, int TZ, int TX>
+__global__ void __launch_bounds__(TZ* TX) adj_coll_kernel(const AdjParams A) {
+  const StepParams& P = A.P;
+  const int z = blockIdx.x * TZ + threadIdx.x % TZ;
+  const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
+  const int k = blockIdx.z;
   const real* lf = reinterpret_cast<const real*>(A.lf_in);
   if (block_interior<DIM, TZ, TX>(P)) {
-    adj_local_node<DIM, CL, real>(A, GlobalLSrc<DIM, false, real>{P, lf}, z, x);
+    adj_coll_node<DIM, CL, real>(A, GlobalLSrc<DIM, false, real>{P, lf}, z, x, k);
   } else {
     if (z >= P.n[0] || (DIM >= 2 && x >= P.n[1])) return;
-    adj_local_node<DIM, CL, real>(A, GlobalLSrc<DIM, true, real>{P, lf}, z, x);
+    adj_coll_node<DIM, CL, real>(A, GlobalLSrc<DIM, true, real>{P, lf}, z, x, k);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2: field adjoints, gradient-stencil gathers, decode adjoint and the
+// Kernel 3: field adjoints, gradient-stencil gathers, decode adjoint and the
 // population adjoint of the previous state.
 // ---------------------------------------------------------------------------
 
@@ -626,9 +674,8 @@ __device__ __forceinline__ void row_partials(const AdjParams& A, double (&red)[2
   }
 }
 
-template <int DIM, int CL, typename real, class LSrc>
-__device__ __forceinline__ void adj_field_node(const AdjParams& A, const LSrc& src, int z, int x, double& r0,
-                                               double& r2) {
+template <int DIM, int CL, typename real>
+__device__ __forceinline__ void adj_field_node(const AdjParams& A, int z, int x, double& r0, double& r2) {
   using M = Model<DIM, CL>;
   using L = Lattice<DIM>;
   constexpr int K = M::K, Q = L::Q;
@@ -738,18 +785,41 @@ __device__ __forceinline__ void adj_field_node(const AdjParams& A, const LSrc& s
     for (int k = 0; k < K; ++k) lA[k] = gld(rA + k * pl + id);
     decode_adjoint<DIM, CL, real>(P, S, N, lm, lA);
 
-    // ---- population adjoint of the previous state ----------------------------
-    real* lfo = reinterpret_cast<real*>(A.lf_out);
-    const real omt = real(1) - S.inv_tau;
+    // the population adjoint of the previous state adds lA (adj_pop_kernel)
+    real* lAf = reinterpret_cast<real*>(A.lAf);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      real lk[Q];
-      src.load(k, z, x, lk);
-      real* lok = lfo + (size_t)k * Q * pl + id;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) lok[i * pl] = omt * lk[i] + lA[k];
-    }
+    for (int k = 0; k < K; ++k) lAf[k * pl + id] = lA[k];
   }
+}
+
+// Population adjoint of the previous state, one set k at one node:
+// lambda_f^n = (1 - 1/tau) lambda_fs + lambda_A, with lambda_fs gathered as
+// in adj_coll_node and lambda_A from adj_field_kernel.  grid: (z tiles,
+// x tiles, K)
+template <int DIM, int CL, typename real, int TZ, int TX>
+__global__ void __launch_bounds__(TZ* TX) adj_pop_kernel(const AdjParams A) {
+  using L = Lattice<DIM>;
+  constexpr int Q = L::Q;
+  const StepParams& P = A.P;
+  const StepConst<real>& S = consts<real>(P);
+  const int z = blockIdx.x * TZ + threadIdx.x % TZ;
+  const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
+  const int k = blockIdx.z;
+  const real* lf = reinterpret_cast<const real*>(A.lf_in);
+  real lk[Q];
+  if (block_interior<DIM, TZ, TX>(P)) {
+    GlobalLSrc<DIM, false, real>{P, lf}.load(k, z, x, lk);
+  } else {
+    if (z >= P.n[0] || (DIM >= 2 && x >= P.n[1])) return;
+    GlobalLSrc<DIM, true, real>{P, lf}.load(k, z, x, lk);
+  }
+  const int pl = (int)P.plane;
+  const int id = aidx(P, z, x);
+  const real lAk = gld(reinterpret_cast<const real*>(A.lAf) + k * pl + id);
+  const real omt = real(1) - S.inv_tau;
+  real* lok = reinterpret_cast<real*>(A.lf_out) + (size_t)k * Q * pl + id;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) lok[i * pl] = omt * lk[i] + lAk;
 }
 
 template <int DIM, int CL, typename real, int TZ, int TX, int MINB>
@@ -760,12 +830,7 @@ __global__ void __launch_bounds__(TZ* TX, MINB) adj_field_kernel(const AdjParams
   const int z = blockIdx.x * TZ + tzi;
   const int x = DIM >= 2 ? blockIdx.y * TX + txi : 0;
   double r0 = 0.0, r2 = 0.0;
-  const real* lf = reinterpret_cast<const real*>(A.lf_in);
-  if (block_interior<DIM, TZ, TX>(P)) {
-    adj_field_node<DIM, CL, real>(A, GlobalLSrc<DIM, false, real>{P, lf}, z, x, r0, r2);
-  } else if (z < P.n[0] && (DIM < 2 || x < P.n[1])) {
-    adj_field_node<DIM, CL, real>(A, GlobalLSrc<DIM, true, real>{P, lf}, z, x, r0, r2);
-  }
+  if (z < P.n[0] && (DIM < 2 || x < P.n[1])) adj_field_node<DIM, CL, real>(A, z, x, r0, r2);
   row_partials<TZ, TX>(A, red, tzi, txi, z, r0, r2);
 }
 

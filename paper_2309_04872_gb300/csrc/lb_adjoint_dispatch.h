@@ -13,9 +13,13 @@ struct StepParams;
 
 struct AdjKernelSet {
   int K, NG, NPREV, NTAPE;
-  int tz, tx;  // tile of the two per-node kernels
+  int tz, tx;  // tile of the per-node kernels
+  // per (node, set), grid.z = K: the gathers of the next state's population
+  // adjoints, before adj_local (coll) and after adj_field (pop)
+  void (*coll)(const AdjParams&, dim3 grid, cudaStream_t);
   void (*local)(const AdjParams&, dim3 grid, cudaStream_t);
   void (*field)(const AdjParams&, dim3 grid, cudaStream_t);
+  void (*pop)(const AdjParams&, dim3 grid, cudaStream_t);
   void (*init_rows)(const StepParams&, const void* lE, const void* lB, const double* Kx, double* rows, dim3 grid,
                     cudaStream_t);
   void (*seed)(void* lE, long long idx, double v, cudaStream_t);

@@ -23,6 +23,13 @@ struct AdjParams {
   void* rG;                 // [NG][plane] gradient-stencil coefficients
   void* rEn;                // [3][plane]  adjoint of the node-averaged E^{n+1/2}
   void* rBn;                // [3][plane]  adjoint of the node-averaged B^n
+  // per node and set, from the gather of the next state's population
+  // adjoints (adj_coll_kernel): the collision's adjoint of A_k, of dt F_k,
+  // and A_k times its part of the adjoint of u
+  void* cA;                 // [K][plane]
+  void* cF;                 // [K][plane]
+  void* cU;                 // [K][DIM][plane]
+  void* lAf;                // [K][plane]  the node's adjoint of A_k after the field terms (adj_field_kernel)
   double* rows;             // [2][gridDim.y][n0] partial row sums of this step
   const double* Tx;         // [2][n1]: T(x) and T(x) x^2 / sigma_r^3 at the E_z slots
 };
