@@ -18,21 +18,38 @@ template <> struct AdjTile<2> { static constexpr int TZ = 32, TX = 8; };
 template <typename real> struct AdjMinBlocks { static constexpr int LOCAL = 1, FIELD = 1; };
 template <> struct AdjMinBlocks<float> { static constexpr int LOCAL = 4, FIELD = 4; };
 
+// Launch with programmatic stream serialization (the kernels wait for
+// their predecessor themselves, pdl_enter).
+template <typename... Args>
+void launch_pdl(void (*kernel)(Args...), dim3 g, unsigned threads, cudaStream_t s, const AdjParams& A) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = g;
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, A);
+}
+
 template <int DIM, int CL, int PR>
 struct AdjImpl {
   using real = typename Prec<PR>::real;
   using T = AdjTile<DIM>;
   static void coll(const AdjParams& A, dim3 g, cudaStream_t s) {
-    adj_coll_kernel<DIM, CL, real, T::TZ, T::TX><<<g, T::TZ * T::TX, 0, s>>>(A);
+    launch_pdl(adj_coll_kernel<DIM, CL, real, T::TZ, T::TX>, g, T::TZ * T::TX, s, A);
   }
   static void pop(const AdjParams& A, dim3 g, cudaStream_t s) {
-    adj_pop_kernel<DIM, CL, real, T::TZ, T::TX><<<g, T::TZ * T::TX, 0, s>>>(A);
+    launch_pdl(adj_pop_kernel<DIM, CL, real, T::TZ, T::TX>, g, T::TZ * T::TX, s, A);
   }
   static void local(const AdjParams& A, dim3 g, cudaStream_t s) {
-    adj_local_kernel<DIM, CL, real, T::TZ, T::TX, AdjMinBlocks<real>::LOCAL><<<g, T::TZ * T::TX, 0, s>>>(A);
+    launch_pdl(adj_local_kernel<DIM, CL, real, T::TZ, T::TX, AdjMinBlocks<real>::LOCAL>, g, T::TZ * T::TX, s, A);
   }
   static void field(const AdjParams& A, dim3 g, cudaStream_t s) {
-    adj_field_kernel<DIM, CL, real, T::TZ, T::TX, AdjMinBlocks<real>::FIELD><<<g, T::TZ * T::TX, 0, s>>>(A);
+    launch_pdl(adj_field_kernel<DIM, CL, real, T::TZ, T::TX, AdjMinBlocks<real>::FIELD>, g, T::TZ * T::TX, s, A);
   }
   static void init_rows(const StepParams& P, const void* lE, const void* lB, const double* Kx, double* rows,
                         dim3 g, cudaStream_t s) {

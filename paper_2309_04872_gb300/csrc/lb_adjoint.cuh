@@ -151,6 +151,27 @@ struct GlobalLSrc {
   }
 };
 
+// Programmatic dependent launch: the reverse step's kernels are launched
+// so that the next one's CTAs may be scheduled while this one's last CTAs
+// run; each kernel lets its dependents launch on entry and waits for its
+// predecessor's completion (and memory) before it reads anything.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Whether every node of the calling warp lies three or more nodes inside
+// the grid (a warp is 32 consecutive z of one x row of the tile).
+template <int DIM, int TZ, int TX>
+__device__ __forceinline__ bool warp_interior(const StepParams& P) {
+  static_assert(TZ % 32 == 0, "a warp spans 32 consecutive z");
+  const int w = (int)threadIdx.x / 32;
+  const int z0 = blockIdx.x * TZ + (w % (TZ / 32)) * 32, x = DIM >= 2 ? blockIdx.y * TX + w / (TZ / 32) : 0;
+  bool in = z0 >= 3 && z0 + 31 <= P.n[0] - 4;
+  if (DIM >= 2) in = in && x >= 3 && x <= P.n[1] - 4;
+  return in;
+}
+
 // Whether every node of the block's tile lies three or more nodes inside
 // the grid (no boundary rule in the population gather).
 template <int DIM, int TZ, int TX>
@@ -528,6 +549,7 @@ __device__ __forceinline__ void adj_local_node(const AdjParams& A, int z, int x)
 
 template <int DIM, int CL, typename real, int TZ, int TX, int MINB>
 __global__ void __launch_bounds__(TZ* TX, MINB) adj_local_kernel(const AdjParams A) {
+  pdl_enter();
   const StepParams& P = A.P;
   const int z = blockIdx.x * TZ + threadIdx.x % TZ;
   const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
@@ -556,12 +578,23 @@ __device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& sr
   const StepConst<real>& S = consts<real>(P);
   const int pl = (int)P.plane;
   const int id = aidx(P, z, x);
-  Node<DIM, CL, real> N;
-  load_node<DIM, CL, real>(P, reinterpret_cast<const real*>(A.tape), id, N);
+  const real* tp = reinterpret_cast<const real*>(A.tape);
+  // the node's u as the step decoded it (WARMC: only the moments it needs)
+  real u[3] = {0, 0, 0};
+  if constexpr (CL == CL_WARMC) {
+    const real inl = real(1) / (S.Arest[1] + gld(tp + pl + id));
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) u[a] = gld(tp + (2 + a) * pl + id) * inl;
+  } else {
+    Node<DIM, CL, real> N;
+    load_node<DIM, CL, real>(P, tp, id, N);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) u[a] = N.rec[Model<DIM, CL>::R_U + a];
+  }
   real ul[3] = {0, 0, 0}, usq = 0;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    ul[a] = S.courant * N.rec[Model<DIM, CL>::R_U + a];
+    ul[a] = S.courant * u[a];
     usq += ul[a] * ul[a];
   }
   // opposite velocities (i, i + 1) share w_i and |cu|: with s = l_i + l_j and
@@ -588,7 +621,7 @@ __device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& sr
 #pragma unroll
     for (int a = 0; a < DIM; ++a) mu_[a] += real(L::c(i, a)) * t - real(3) * ul[a] * sp;
   }
-  const real Ak = S.Arest[k] + N.dA[k];
+  const real Ak = S.Arest[k] + gld(tp + k * pl + id);
   reinterpret_cast<real*>(A.cA)[k * pl + id] = mA * S.inv_tau;
   reinterpret_cast<real*>(A.cF)[k * pl + id] = S.dt * m0;
   real* cU = reinterpret_cast<real*>(A.cU);
@@ -599,12 +632,13 @@ __device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& sr
 // grid: (z tiles, x tiles, K)
 template <int DIM, int CL, typename real, int TZ, int TX>
 __global__ void __launch_bounds__(TZ* TX) adj_coll_kernel(const AdjParams A) {
+  pdl_enter();
   const StepParams& P = A.P;
   const int z = blockIdx.x * TZ + threadIdx.x % TZ;
   const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
   const int k = blockIdx.z;
   const real* lf = reinterpret_cast<const real*>(A.lf_in);
-  if (block_interior<DIM, TZ, TX>(P)) {
+  if (warp_interior<DIM, TZ, TX>(P)) {
     adj_coll_node<DIM, CL, real>(A, GlobalLSrc<DIM, false, real>{P, lf}, z, x, k);
   } else {
     if (z >= P.n[0] || (DIM >= 2 && x >= P.n[1])) return;
@@ -798,6 +832,7 @@ __device__ __forceinline__ void adj_field_node(const AdjParams& A, int z, int x,
 // x tiles, K)
 template <int DIM, int CL, typename real, int TZ, int TX>
 __global__ void __launch_bounds__(TZ* TX) adj_pop_kernel(const AdjParams A) {
+  pdl_enter();
   using L = Lattice<DIM>;
   constexpr int Q = L::Q;
   const StepParams& P = A.P;
@@ -807,7 +842,7 @@ __global__ void __launch_bounds__(TZ* TX) adj_pop_kernel(const AdjParams A) {
   const int k = blockIdx.z;
   const real* lf = reinterpret_cast<const real*>(A.lf_in);
   real lk[Q];
-  if (block_interior<DIM, TZ, TX>(P)) {
+  if (warp_interior<DIM, TZ, TX>(P)) {
     GlobalLSrc<DIM, false, real>{P, lf}.load(k, z, x, lk);
   } else {
     if (z >= P.n[0] || (DIM >= 2 && x >= P.n[1])) return;
@@ -824,6 +859,7 @@ __global__ void __launch_bounds__(TZ* TX) adj_pop_kernel(const AdjParams A) {
 
 template <int DIM, int CL, typename real, int TZ, int TX, int MINB>
 __global__ void __launch_bounds__(TZ* TX, MINB) adj_field_kernel(const AdjParams A) {
+  pdl_enter();
   const StepParams& P = A.P;
   __shared__ double red[2][TX][TZ];
   const int tzi = threadIdx.x % TZ, txi = threadIdx.x / TZ;
