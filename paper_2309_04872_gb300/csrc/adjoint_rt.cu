@@ -301,7 +301,7 @@ struct Sweep {
     A.rows = rows_of_set(nsets);
     A.Tx = (const double*)r->Tx.p;
     const dim3 g((unsigned)((h->n[0] + r->ak.tz - 1) / r->ak.tz), (unsigned)r->ntx, 1);
-    const dim3 gk(g.x, g.y, (unsigned)r->ak.K);
+    const dim3 gk(g.x, g.y, (unsigned)((r->ak.K + r->ak.spt - 1) / r->ak.spt));
     r->ak.coll(A, gk, h->stream);
     CK_LAUNCH(h, "adj_coll_kernel launch");
     r->ak.local(A, g, h->stream);

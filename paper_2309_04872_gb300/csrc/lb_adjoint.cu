@@ -71,6 +71,7 @@ struct AdjImpl {
     k->NTAPE = AM::NTAPE;
     k->tz = T::TZ;
     k->tx = T::TX;
+    k->spt = kAdjSetsPerThread;
     k->coll = &coll;
     k->local = &local;
     k->field = &field;

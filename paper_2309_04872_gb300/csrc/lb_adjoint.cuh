@@ -570,8 +570,13 @@ __global__ void __launch_bounds__(TZ* TX, MINB) adj_local_kernel(const AdjParams
 //   lambda_F  = dt sum_i w_i lambda_fs.
 // Written: cA = the first, cF = the third, cU = A_k times the sum of the
 // second (adj_local adds C/tau times its sum over the sets, in set order).
+// Sets per thread of the per-(node, set) kernels (2D WARMC FP32, cost ratio
+// of the 1000-step sweep with the whole tape: one set 3.13-3.14, two 3.36-3.37,
+// four 3.81-3.82: the gathers want threads, not longer threads).
+constexpr int kAdjSetsPerThread = 1;
+
 template <int DIM, int CL, typename real, class LSrc>
-__device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& src, int z, int x, int k) {
+__device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& src, int z, int x, int k0) {
   using L = Lattice<DIM>;
   constexpr int Q = L::Q;
   const StepParams& P = A.P;
@@ -601,6 +606,10 @@ __device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& sr
   // d = l_i - l_j the even part carries 1 + 9/2 cu^2 - 3/2 u^2, the odd 3 cu
   static_assert(opposite_pairs<DIM>(), "lattice order must pair opposite velocities");
   const real even0 = real(1) - real(1.5) * usq;
+#pragma unroll
+  for (int ks = 0; ks < kAdjSetsPerThread; ++ks) {
+  const int k = k0 + ks;
+  if (k >= Model<DIM, CL>::K) break;
   real lk[Q];
   src.load(k, z, x, lk);
   const real w0l = real(L::w(0)) * lk[0];
@@ -627,6 +636,7 @@ __device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& sr
   real* cU = reinterpret_cast<real*>(A.cU);
 #pragma unroll
   for (int a = 0; a < DIM; ++a) cU[(k * DIM + a) * pl + id] = Ak * mu_[a];
+  }
 }
 
 // grid: (z tiles, x tiles, K)
@@ -636,7 +646,7 @@ __global__ void __launch_bounds__(TZ* TX) adj_coll_kernel(const AdjParams A) {
   const StepParams& P = A.P;
   const int z = blockIdx.x * TZ + threadIdx.x % TZ;
   const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
-  const int k = blockIdx.z;
+  const int k = blockIdx.z * kAdjSetsPerThread;
   const real* lf = reinterpret_cast<const real*>(A.lf_in);
   if (warp_interior<DIM, TZ, TX>(P)) {
     adj_coll_node<DIM, CL, real>(A, GlobalLSrc<DIM, false, real>{P, lf}, z, x, k);
@@ -839,22 +849,24 @@ __global__ void __launch_bounds__(TZ* TX) adj_pop_kernel(const AdjParams A) {
   const StepConst<real>& S = consts<real>(P);
   const int z = blockIdx.x * TZ + threadIdx.x % TZ;
   const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
-  const int k = blockIdx.z;
   const real* lf = reinterpret_cast<const real*>(A.lf_in);
-  real lk[Q];
-  if (warp_interior<DIM, TZ, TX>(P)) {
-    GlobalLSrc<DIM, false, real>{P, lf}.load(k, z, x, lk);
-  } else {
-    if (z >= P.n[0] || (DIM >= 2 && x >= P.n[1])) return;
-    GlobalLSrc<DIM, true, real>{P, lf}.load(k, z, x, lk);
-  }
+  const bool interior = warp_interior<DIM, TZ, TX>(P);
+  if (!interior && (z >= P.n[0] || (DIM >= 2 && x >= P.n[1]))) return;
   const int pl = (int)P.plane;
   const int id = aidx(P, z, x);
-  const real lAk = gld(reinterpret_cast<const real*>(A.lAf) + k * pl + id);
   const real omt = real(1) - S.inv_tau;
-  real* lok = reinterpret_cast<real*>(A.lf_out) + (size_t)k * Q * pl + id;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) lok[i * pl] = omt * lk[i] + lAk;
+  for (int ks = 0; ks < kAdjSetsPerThread; ++ks) {
+    const int k = blockIdx.z * kAdjSetsPerThread + ks;
+    if (k >= Model<DIM, CL>::K) break;
+    real lk[Q];
+    if (interior) GlobalLSrc<DIM, false, real>{P, lf}.load(k, z, x, lk);
+    else GlobalLSrc<DIM, true, real>{P, lf}.load(k, z, x, lk);
+    const real lAk = gld(reinterpret_cast<const real*>(A.lAf) + k * pl + id);
+    real* lok = reinterpret_cast<real*>(A.lf_out) + (size_t)k * Q * pl + id;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) lok[i * pl] = omt * lk[i] + lAk;
+  }
 }
 
 template <int DIM, int CL, typename real, int TZ, int TX, int MINB>

@@ -14,6 +14,7 @@ struct StepParams;
 struct AdjKernelSet {
   int K, NG, NPREV, NTAPE;
   int tz, tx;  // tile of the per-node kernels
+  int spt;     // sets per thread of the per-(node, set) kernels: grid.z = ceil(K / spt)
   // per (node, set), grid.z = K: the gathers of the next state's population
   // adjoints, before adj_local (coll) and after adj_field (pop)
   void (*coll)(const AdjParams&, dim3 grid, cudaStream_t);
