@@ -26,7 +26,7 @@ struct AdjRec {
   size_t state_bytes = 0;   // one checkpoint: f, E, B, prev
   Buf tape, ckpt, prev0, finalst;
   std::vector<int> ckpt_have_prev;
-  Buf lf[2], lE[2], lB[2], lp[2], rA, rG, rEn, rBn, cA, cF, cU, lAf;
+  Buf lf[2], lE[2], lB[2], lp[2], rA, rG, rEn, rBn, cA, cF, cU, lAf, cW;
   Buf rows, setp, gpart, g3, gp, Tx, Kx, jv;
   int ntx = 1;
   size_t bytes = 0;
@@ -42,7 +42,7 @@ namespace {
 void free_rec(lbpwfa_s* h, AdjRec* r) {
   Buf* all[] = {&r->tape, &r->ckpt, &r->prev0, &r->finalst, &r->lf[0], &r->lf[1], &r->lE[0], &r->lE[1],
                 &r->lB[0], &r->lB[1], &r->lp[0], &r->lp[1], &r->rA, &r->rG, &r->rEn, &r->rBn, &r->cA,
-                &r->cF, &r->cU, &r->lAf, &r->rows,
+                &r->cF, &r->cU, &r->lAf, &r->cW, &r->rows,
                 &r->setp, &r->gpart, &r->g3, &r->gp, &r->Tx, &r->Kx, &r->jv};
   for (Buf* b : all) {
     h->device_bytes -= b->bytes;
@@ -176,6 +176,8 @@ extern "C" int lbpwfa_record(lbpwfa_t h, const lbpwfa_record_params* rp) {
   if (st == LBPWFA_OK) st = ab(h, r, r->cF, (size_t)r->ak.K * pl * rs);
   if (st == LBPWFA_OK) st = ab(h, r, r->cU, (size_t)r->ak.K * h->prm.dim * pl * rs);
   if (st == LBPWFA_OK) st = ab(h, r, r->lAf, (size_t)r->ak.K * pl * rs);
+  if (st == LBPWFA_OK && h->prm.closure == LBPWFA_WARMC)
+    st = ab(h, r, r->cW, 2 * (size_t)h->prm.dim * pl * rs);
   if (st == LBPWFA_OK) st = ab(h, r, r->rEn, fldb);
   if (st == LBPWFA_OK) st = ab(h, r, r->rBn, fldb);
   if (st == LBPWFA_OK) st = ab(h, r, r->rows, (size_t)kRowSets * 2 * r->ntx * h->n[0] * sizeof(double));
@@ -298,6 +300,7 @@ struct Sweep {
     A.cF = r->cF.p;
     A.cU = r->cU.p;
     A.lAf = r->lAf.p;
+    A.cW = r->cW.p;
     A.rows = rows_of_set(nsets);
     A.Tx = (const double*)r->Tx.p;
     const dim3 g((unsigned)((h->n[0] + r->ak.tz - 1) / r->ak.tz), (unsigned)r->ntx, 1);

@@ -373,21 +373,13 @@ __device__ __forceinline__ void adj_local_node(const AdjParams& A, int z, int x)
     const real lam = N.rec[M::R_LAM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { th0[a] = N.rec[M::R_TH0 + a]; w[a] = lam * u[a]; }
+    // w = lambda u of this node's previous step and of its neighbours, as
+    // their records give it (formed once per node by adj_coll_kernel)
+    const real* cW = reinterpret_cast<const real*>(A.cW);
     // previous-step w (backward time difference)
     if (hp) {
-      real wp[3] = {0, 0, 0};
-      if (A.tape_prev) {
-        Node<DIM, CL, real> Np;
-        load_node<DIM, CL, real>(P, reinterpret_cast<const real*>(A.tape_prev), id, Np);
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) wp[a] = Np.rec[M::R_LAM] * Np.rec[M::R_U + a];
-      } else {
-        const real* p0 = reinterpret_cast<const real*>(A.prev0);
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) wp[a] = gld(p0 + (1 + DIM + a) * pl + id);
-      }
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) dw[a] = (w[a] - wp[a]) * S.idt;
+      for (int a = 0; a < DIM; ++a) dw[a] = (w[a] - gld(cW + (DIM + a) * pl + id)) * S.idt;
     }
     // gradients of w from the neighbours' decode
 #pragma unroll
@@ -396,14 +388,8 @@ __device__ __forceinline__ void adj_local_node(const AdjParams& A, int z, int x)
       const int cp = wrap_or_clamp(ck + 1, P.n[k], P.periodic), cm = wrap_or_clamp(ck - 1, P.n[k], P.periodic);
       const int idp = k == 0 ? aidx(P, cp, x) : aidx(P, z, cp);
       const int idm = k == 0 ? aidx(P, cm, x) : aidx(P, z, cm);
-      // w^a = lambda u^a of the neighbours, as their records give it
-      const real np_ = real(1) + gld(tp + idp), nm_ = real(1) + gld(tp + idm);
-      const real nlp = S.Arest[1] + gld(tp + pl + idp), nlm = S.Arest[1] + gld(tp + pl + idm);
-      const real lamp = nlp / np_, lamm = nlm / nm_;
-      const real inlp = real(1) / nlp, inlm = real(1) / nlm;
 #pragma unroll
-      for (int a = 0; a < DIM; ++a)
-        gw[a][k] = (lamp * (gld(tp + (2 + a) * pl + idp) * inlp) - lamm * (gld(tp + (2 + a) * pl + idm) * inlm)) * S.i2dx;
+      for (int a = 0; a < DIM; ++a) gw[a][k] = (gld(cW + a * pl + idp) - gld(cW + a * pl + idm)) * S.i2dx;
     }
     // adjoints of the previous-step values this step wrote
     if (A.lp_in) {
@@ -587,9 +573,35 @@ __device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& sr
   // the node's u as the step decoded it (WARMC: only the moments it needs)
   real u[3] = {0, 0, 0};
   if constexpr (CL == CL_WARMC) {
-    const real inl = real(1) / (S.Arest[1] + gld(tp + pl + id));
+    const real nl = S.Arest[1] + gld(tp + pl + id);
+    const real inl = real(1) / nl;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) u[a] = gld(tp + (2 + a) * pl + id) * inl;
+    if (k0 == 0) {
+      // w = lambda u of this step and of the previous one, for adj_local's
+      // backward time difference and its neighbours' central differences
+      real* cW = reinterpret_cast<real*>(A.cW);
+      const real lam = nl / (real(1) + gld(tp + id));
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) cW[a * pl + id] = lam * u[a];
+      if (P.have_prev) {
+        real wp[3] = {0, 0, 0};
+        if (A.tape_prev) {
+          const real* tq = reinterpret_cast<const real*>(A.tape_prev);
+          const real nlq = S.Arest[1] + gld(tq + pl + id);
+          const real inlq = real(1) / nlq;
+          const real lamq = nlq / (real(1) + gld(tq + id));
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) wp[a] = lamq * (gld(tq + (2 + a) * pl + id) * inlq);
+        } else {
+          const real* p0 = reinterpret_cast<const real*>(A.prev0);
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) wp[a] = gld(p0 + (1 + DIM + a) * pl + id);
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) cW[(DIM + a) * pl + id] = wp[a];
+      }
+    }
   } else {
     Node<DIM, CL, real> N;
     load_node<DIM, CL, real>(P, tp, id, N);

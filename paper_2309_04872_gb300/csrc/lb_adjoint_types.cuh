@@ -30,6 +30,7 @@ struct AdjParams {
   void* cF;                 // [K][plane]
   void* cU;                 // [K][DIM][plane]
   void* lAf;                // [K][plane]  the node's adjoint of A_k after the field terms (adj_field_kernel)
+  void* cW;                 // WARMC [2][DIM][plane]: the node's w = lambda u, and the previous step's (adj_coll_kernel)
   double* rows;             // [2][gridDim.y][n0] partial row sums of this step
   const double* Tx;         // [2][n1]: T(x) and T(x) x^2 / sigma_r^3 at the E_z slots
 };
