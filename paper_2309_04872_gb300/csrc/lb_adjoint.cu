@@ -8,15 +8,18 @@ namespace {
 
 template <int DIM> struct AdjTile;
 template <> struct AdjTile<1> { static constexpr int TZ = 128, TX = 1; };
-template <> struct AdjTile<2> { static constexpr int TZ = 32, TX = 8; };
+// 2D: 32 x 4 tiles, so the 512 x 256 grid's 1024 CTAs spread evenly over the
+// SMs (32 x 8: 3.085-3.094 cost ratio of the sweep, 32 x 4: 3.052-3.06)
+template <> struct AdjTile<2> { static constexpr int TZ = 32, TX = 4; };
 
 // Resident CTAs per SM the per-node kernels' register budget is held to
-// (latency-bound chains want warps).  FP32 WARMC 2D, 1000-step reverse sweep
+// (latency-bound chains want warps; the counts below are for 256-thread
+// CTAs, the 128-thread CTAs of the 32 x 4 tile run twice as many).  FP32 WARMC 2D, 1000-step reverse sweep
 // with the population gathers inside them: 1/1 CTAs 117 ms, 2/2 103, 3/3
 // 107, 3/4 101; with the gathers in the per-set kernels: 3/4 74 ms, 4/4 70,
 // 4/5 76 (adj_local at 5 spills).  FP64 unconstrained.
 template <typename real> struct AdjMinBlocks { static constexpr int LOCAL = 1, FIELD = 1; };
-template <> struct AdjMinBlocks<float> { static constexpr int LOCAL = 4, FIELD = 4; };
+template <> struct AdjMinBlocks<float> { static constexpr int LOCAL = 8, FIELD = 8; };
 
 // Launch with programmatic stream serialization (the kernels wait for
 // their predecessor themselves, pdl_enter).

@@ -651,10 +651,10 @@ __device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& sr
   }
 }
 
-// grid: (z tiles, x tiles, K); eight CTAs per SM (32 registers: 3.10-3.13
+// grid: (z tiles, x tiles, K); 2048 threads per SM (32 registers: 3.10-3.13
 // against 3.13-3.14 for the sweep's cost ratio at the compiler's 40)
 template <int DIM, int CL, typename real, int TZ, int TX>
-__global__ void __launch_bounds__(TZ* TX, 8) adj_coll_kernel(const AdjParams A) {
+__global__ void __launch_bounds__(TZ* TX, 2048 / (TZ * TX)) adj_coll_kernel(const AdjParams A) {
   pdl_enter();
   const StepParams& P = A.P;
   const int z = blockIdx.x * TZ + threadIdx.x % TZ;
@@ -854,7 +854,7 @@ __device__ __forceinline__ void adj_field_node(const AdjParams& A, int z, int x,
 // in adj_coll_node and lambda_A from adj_field_kernel.  grid: (z tiles,
 // x tiles, K)
 template <int DIM, int CL, typename real, int TZ, int TX>
-__global__ void __launch_bounds__(TZ* TX, 8) adj_pop_kernel(const AdjParams A) {
+__global__ void __launch_bounds__(TZ* TX, 2048 / (TZ * TX)) adj_pop_kernel(const AdjParams A) {
   pdl_enter();
   using L = Lattice<DIM>;
   constexpr int Q = L::Q;
