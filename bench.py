@@ -512,7 +512,38 @@ def run_ours(a):
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
+        out["summary"] = _summary(out)
         print(json.dumps(out), flush=True)
+
+
+def _summary(out):
+    """A compact digest of the line's measurements, placed last so that a
+    reader who sees only the end of the line still finds every workload:
+    [MLUPS, fraction of the measured HBM by the algorithmic bytes] per
+    workload, the FP64 ALU fractions, the reduced-precision errors of n - 1
+    after 2000 steps, and the adjoint's cost ratios."""
+    s = {"headline": [out["value"], out["roofline"]["frac"]]}
+    for k, v in (out.get("modes") or {}).items():
+        if not k.endswith(("_plain", "_box", "_persistent")):
+            s[k] = [round(v["mlups"]), round(v["frac_of_measured_hbm"], 3)] + \
+                ([round(v["fp64_alu"]["frac"], 3)] if v.get("fp64_alu") else [])
+    for k, v in (out.get("configs_measured") or {}).items():
+        frac = v.get("frac_of_measured_hbm")
+        s[k] = [round(v["mlups"]), round(frac, 3) if frac is not None else None] + \
+            ([round(v["fp64_alu"]["frac"], 3)] if v.get("fp64_alu") else [])
+    for key, tag in (("precision_vs_fp64", "mu1e-2"), ("precision_vs_fp64_mu1e-3", "mu1e-3"),
+                     ("precision_vs_fp64_axisymmetric", "axi")):
+        for k, v in (out.get(key) or {}).items():
+            if isinstance(v, dict) and "rel_err_n_minus_1" in v:
+                s[f"err_n-1_{tag}_{k}"] = float(f"{v['rel_err_n_minus_1']:.2e}")
+    p3 = out.get("precision_vs_fp64_3d") or {}
+    for prec in ("fp32", "fp16s"):
+        if prec in p3:
+            s[f"err_3d_{prec}"] = {k: float(f"{p3[prec][k]:.2e}") for k in ("n-1", "E_z")}
+    adj = out.get("adjoint") or {}
+    if "cost_ratio_whole_tape" in adj:
+        s["adjoint_cost_ratio"] = {"whole_tape": adj["cost_ratio_whole_tape"], "checkpoint50": adj["cost_ratio_checkpoint50"]}
+    return s
 
 
 def _flops64_for(kernel_key):
