@@ -134,7 +134,12 @@ struct StepCfg {
   // (E_z, E_x, B_y and B_y one node up along x and z; FP32 also low parts)
   static constexpr int NHALO_E = DIM == 2 ? (TZ + 1) * (TX + 1) - TZ * TX : 0;
   static constexpr int NSTAGE = NHALO_E * (CF ? 10 : 5);
-  static constexpr size_t smem_bytes = ((size_t)(M::NM + NE_SLOTS) * NR + NDRV + NSCR + NSTAGE) * sizeof(real);
+  // 3D marching: the set moments of the top plane's nodes beyond the first
+  // NT, pulled one (node, set) per thread across the CTA
+  static constexpr int NXTRA = (DIM == 3 && TY == 1 && RZ * RX > NT) ? RZ * RX - NT : 0;
+  static constexpr int NSPLIT = NXTRA * M::K;
+  static constexpr size_t smem_bytes =
+      ((size_t)(M::NM + NE_SLOTS) * NR + NDRV + NSCR + NSTAGE + NSPLIT) * sizeof(real);
   // Sets too wide for registers (2D WARMC, K*Q = 72) could keep the own
   // node's populations in a shared-memory column [K*Q][NT] for the
   // collision instead of pulling them again (launch reserving
@@ -706,8 +711,19 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
         decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, 0, smac, NR, r, scr, NT);
       }
     } else if (march_on) {
-      // marching: move the planes down, decode the new top plane
+      // marching: move the planes down, decode the new top plane.  Its first
+      // NT nodes are pulled and decoded by one thread each; the set moments
+      // of the rest are pulled one (node, set) per thread across the CTA and
+      // decoded after a barrier, so no thread pulls two nodes' sets
       constexpr int PLN = RZ * RX;
+      auto top = [&](int j, int& z, int& x, int& y) {
+        z = oz + j % RZ, x = ox + j / RZ, y = oy + 2;
+        if (EDGE) {
+          z = wrap_or_clamp(z, P.n[0], P.periodic);
+          x = wrap_or_clamp(x, P.n[1], P.periodic);
+          y = wrap_or_clamp(y, P.n[2], P.periodic);
+        }
+      };
       for (int j = tid; j < PLN; j += NT) {
 #pragma unroll 1
         for (int m = 0; m < M::NM; ++m) {
@@ -716,13 +732,34 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
         }
 #pragma unroll
         for (int a = 0; a < C::NE_SLOTS; ++a) sE[a * NR + j] = sE[a * NR + PLN + j];
-        int z = oz + j % RZ, x = ox + j / RZ, y = oy + 2;
-        if (EDGE) {
-          z = wrap_or_clamp(z, P.n[0], P.periodic);
-          x = wrap_or_clamp(x, P.n[1], P.periodic);
-          y = wrap_or_clamp(y, P.n[2], P.periodic);
+        if (C::NXTRA == 0 || j < NT) {
+          int z, x, y;
+          top(j, z, x, y);
+          decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, y, smac, NR, 2 * PLN + j, scr, NT);
         }
-        decode_node<DIM, CL, PR, EDGE>(P, S, pull, z, x, y, smac, NR, 2 * PLN + j, scr, NT);
+      }
+      if constexpr (C::NXTRA > 0) {
+        real* ssplit = sH + C::NSTAGE;  // [NXTRA][K]
+#pragma unroll 1
+        for (int u = tid; u < C::NSPLIT; u += NT) {
+          // consecutive threads take consecutive nodes of one set (coalesced)
+          const int jj = u % C::NXTRA, k = u / C::NXTRA, j = NT + jj;
+          int z, x, y;
+          top(j, z, x, y);
+          real df[Q];
+          pull.template get<EDGE>(z, x, y, k, df);
+          ssplit[jj * K + k] = set_dA<Q, PR>(df, P.inv_scale[k]);
+        }
+        __syncthreads();
+        for (int j = NT + tid; j < PLN; j += NT) {
+          real dA[K];
+#pragma unroll
+          for (int k = 0; k < K; ++k) dA[k] = ssplit[(j - NT) * K + k];
+          real rec[M::NM];
+          decode_record<DIM, CL, real>(P, S, dA, rec);
+#pragma unroll
+          for (int m = 0; m < M::NM; ++m) smac[m * NR + 2 * PLN + j] = rec[m];
+        }
       }
     } else {
       // 3D: stride over the region and skip the interior
