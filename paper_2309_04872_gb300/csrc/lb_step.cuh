@@ -136,7 +136,9 @@ struct StepCfg {
   static constexpr int NSTAGE = NHALO_E * (CF ? 10 : 5);
   // 3D marching: the set moments of the top plane's nodes beyond the first
   // NT, pulled one (node, set) per thread across the CTA
-  static constexpr int NXTRA = (DIM == 3 && TY == 1 && RZ * RX > NT) ? RZ * RX - NT : 0;
+  // (2D WARMC: the decode ring's set moments, pulled the same way)
+  static constexpr int NXTRA = (DIM == 3 && TY == 1 && RZ * RX > NT) ? RZ * RX - NT
+                               : ((DIM == 2 && CL == CL_WARMC && NR > NT) ? NR - NT : 0);
   static constexpr int NSPLIT = NXTRA * M::K;
   static constexpr size_t smem_bytes =
       ((size_t)(M::NM + NE_SLOTS) * NR + NDRV + NSCR + NSTAGE + NSPLIT) * sizeof(real);
@@ -696,7 +698,46 @@ __device__ __forceinline__ void step_body(const StepParams& P, unsigned char* sm
   }
   {
     // halo ring
-    if constexpr (DIM <= 2) {
+    if constexpr (DIM == 2 && C::NXTRA > 0) {
+      // 2D WARMC: the ring's set moments are pulled one (node, set) per
+      // thread, consecutive threads on consecutive ring nodes of one set, so
+      // the 72 pulls of a ring node do not all fall on one thread; the
+      // records are decoded after a barrier
+      constexpr int NRING = NR - NT;
+      static_assert(C::NXTRA == NRING, "one ring split");
+      real* ssplit = sH + C::NSTAGE;  // [NRING][K]
+      auto ring = [&](int h, int& r, int& z, int& x) {
+        int rz, rx;
+        ring_node_2d<RZ, RX>(h, rz, rx);
+        r = rz + RZ * rx;
+        z = oz + rz;
+        x = ox + rx;
+        if (EDGE) {
+          z = wrap_or_clamp(z, P.n[0], P.periodic);
+          x = wrap_or_clamp(x, P.n[1], P.periodic);
+        }
+      };
+      for (int u = tid; u < C::NSPLIT; u += NT) {
+        const int h = u % NRING, k = u / NRING;
+        int r, z, x;
+        ring(h, r, z, x);
+        real df[Q];
+        pull.template get<EDGE>(z, x, 0, k, df);
+        ssplit[h * K + k] = set_dA<Q, PR>(df, P.inv_scale[k]);
+      }
+      __syncthreads();
+      for (int h = tid; h < NRING; h += NT) {
+        int r, z, x;
+        ring(h, r, z, x);
+        real dA[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) dA[k] = ssplit[h * K + k];
+        real rec[M::NM];
+        decode_record<DIM, CL, real>(P, S, dA, rec);
+#pragma unroll
+        for (int m = 0; m < M::NM; ++m) smac[m * NR + r] = rec[m];
+      }
+    } else if constexpr (DIM <= 2) {
       constexpr int NRING = NR - NT;
       for (int h = tid; h < NRING; h += NT) {
         int rz, rx = 0;
