@@ -311,8 +311,6 @@ struct Sweep {
     CK_LAUNCH(h, "adj_local_kernel launch");
     r->ak.field(A, g, h->stream);
     CK_LAUNCH(h, "adj_field_kernel launch");
-    r->ak.pop(A, gk, h->stream);
-    CK_LAUNCH(h, "adj_pop_kernel launch");
     setp.push_back(make_double2(zeta0_of(h->prm.z0, r->start_step + j, h->dt), 0.0));
     nsets += 1;
     cl = 1 - cl;
@@ -348,6 +346,9 @@ extern "C" int lbpwfa_adjoint_step(lbpwfa_t h, lbpwfa_adjoint_io* io) {
     if (r->lp[j].p) CK(h, cudaMemsetAsync(r->lp[j].p, 0, r->lp[j].bytes, h->stream));
   }
   CK(h, cudaMemsetAsync(r->rBn.p, 0, r->rBn.bytes, h->stream));
+  // the first reverse step forms the next state's population adjoints from
+  // zero gathered values and zero lambda_A
+  CK(h, cudaMemsetAsync(r->lAf.p, 0, r->lAf.bytes, h->stream));
   CK(h, cudaMemsetAsync(r->g3.p, 0, r->g3.bytes, h->stream));
   CK(h, cudaMemsetAsync(r->gp.p, 0, r->gp.bytes, h->stream));
   r->ak.seed(r->lE[0].p, wid, io->seed, h->stream);

@@ -45,9 +45,6 @@ struct AdjImpl {
   static void coll(const AdjParams& A, dim3 g, cudaStream_t s) {
     launch_pdl(adj_coll_kernel<DIM, CL, real, T::TZ, T::TX>, g, T::TZ * T::TX, s, A);
   }
-  static void pop(const AdjParams& A, dim3 g, cudaStream_t s) {
-    launch_pdl(adj_pop_kernel<DIM, CL, real, T::TZ, T::TX>, g, T::TZ * T::TX, s, A);
-  }
   static void local(const AdjParams& A, dim3 g, cudaStream_t s) {
     launch_pdl(adj_local_kernel<DIM, CL, real, T::TZ, T::TX, AdjMinBlocks<real>::LOCAL>, g, T::TZ * T::TX, s, A);
   }
@@ -78,7 +75,6 @@ struct AdjImpl {
     k->coll = &coll;
     k->local = &local;
     k->field = &field;
-    k->pop = &pop;
     k->init_rows = &init_rows;
     k->seed = &seed;
     k->read_slot = &read_slot;

@@ -12,9 +12,13 @@
 // Every transposed stencil is written in gather ("pull") form, so each node
 // computes its own adjoint without atomics:
 //   adj_coll_kernel   - per node and set: the gather of the next state's
-//     population adjoints (folding the boundary copies) and the adjoint of
-//     streaming and collision for that set.  One thread per (node, set),
-//     so the gathers run in parallel instead of on each node's chain.
+//     population adjoints (folding the boundary copies), formed as they are
+//     read from the values the previous reverse step's gather left and its
+//     adjoint of A_k: lambda_f^{n+1} = (1 - 1/tau) lambda_fs^{n+1} +
+//     lambda_A^{n+1}; then the adjoint of streaming and collision for that
+//     set.  One thread per (node, set), so the gathers run in parallel
+//     instead of on each node's chain; the gathered values are kept for the
+//     next reverse step, and no kernel writes lambda_f itself.
 //   adj_local_kernel  - per node: the collision adjoints summed over the
 //     sets, and the adjoint of the sources' local terms; publishes small
 //     records for the neighbours: the decode adjoint of its local part, the
@@ -26,8 +30,6 @@
 //     the current n u) and the decode adjoint, giving lambda_A; plus per-row
 //     partial sums of dt lambda(E_z) times the driver's transverse factor,
 //     from which the driver-parameter gradients are formed.
-//   adj_pop_kernel    - per node and set: the population adjoint
-//     lambda_f^n = (1 - 1/tau) lambda_fs + lambda_A.
 // The step's forward values come from the tape the step kernel wrote while
 // recording: its deviation moments dA^n (decoded here exactly as the step
 // decoded them), E^{n+1/2} and B^n; the previous step's values of the WARMC
@@ -81,73 +83,61 @@ __device__ __forceinline__ Pre preimage(int c, int n, int delta, int periodic) {
 // collects their adjoints.  EDGE = false promises that (z, x) lies at least
 // three nodes inside the grid, so no boundary rule applies and the Q loads
 // are issued back to back.
-template <int DIM, typename real>
-__device__ __forceinline__ void edge_lfs(const StepParams& P, const real* lfk, int z, int x,
-                                         real (&l)[Lattice<DIM>::Q]);
-
+// The next state's population adjoints formed where they are gathered:
+// lambda_f^{n+1}_i(m) = (1 - 1/tau) lambda_fs_i(m) + lambda_A_k(m), from the
+// values the previous reverse step's gather left at node m (lam, [K][Q]
+// planes) and its adjoint of A_k (lA, [K] planes), so that no kernel writes
+// lambda_f itself.
 template <int DIM, bool EDGE, typename real>
-__device__ __forceinline__ void load_lfs(const StepParams& P, const real* lfk, int z, int x,
-                                         real (&l)[Lattice<DIM>::Q]) {
-  using L = Lattice<DIM>;
-  constexpr int Q = L::Q;
-  const int pl = (int)P.plane;
-  if constexpr (!EDGE) {
-    const real* b = lfk + aidx(P, z, x);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) l[i] = __ldg(b + i * pl + L::c(i, 0) + (DIM >= 2 ? L::c(i, 1) * P.nzp : 0));
-  } else {
-    edge_lfs<DIM, real>(P, lfk, z, x, l);
-  }
-}
-
-// The boundary-aware form of load_lfs.
-template <int DIM, typename real>
-__device__ __forceinline__ void edge_lfs(const StepParams& P, const real* lfk, int z, int x,
-                                         real (&l)[Lattice<DIM>::Q]) {
-  using L = Lattice<DIM>;
-  constexpr int Q = L::Q;
-  const int pl = (int)P.plane;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const real* b = lfk + (size_t)i * pl;
-    int yz = z + L::c(i, 0), yx = DIM >= 2 ? x + L::c(i, 1) : 0;
-    if (P.periodic) {
-      yz = wrap_or_clamp(yz, P.n[0], 1);
-      if (DIM >= 2) yx = wrap_or_clamp(yx, P.n[1], 1);
-      l[i] = gld(b + aidx(P, yz, yx));
-      continue;
-    }
-    real s = 0;
-    const bool in = yz >= 1 && yz <= P.n[0] - 2 && (DIM < 2 || (yx >= 1 && yx <= P.n[1] - 2));
-    if (in) {
-      int cz[3] = {yz, -1, -1}, cx[3] = {yx, -1, -1};
-      if (yz == 1) cz[1] = 0;
-      if (yz == P.n[0] - 2) cz[2] = P.n[0] - 1;
-      if (DIM >= 2) {
-        if (yx == 1) cx[1] = 0;
-        if (yx == P.n[1] - 2) cx[2] = P.n[1] - 1;
-      }
-#pragma unroll
-      for (int qz = 0; qz < 3; ++qz) {
-        if (cz[qz] < 0) continue;
-#pragma unroll
-        for (int qx = 0; qx < (DIM >= 2 ? 3 : 1); ++qx) {
-          if (cx[qx] < 0) continue;
-          s += gld(b + aidx(P, cz[qz], cx[qx]));
-        }
-      }
-    }
-    l[i] = s;
-  }
-}
-
-// Source of the next state's population adjoints for the gather.
-template <int DIM, bool EDGE, typename real>
-struct GlobalLSrc {
+struct NextLSrc {
   const StepParams& P;
-  const real* lf;
+  const real* lam;
+  const real* lA;
+  real omt;
   __device__ __forceinline__ void load(int k, int z, int x, real (&l)[Lattice<DIM>::Q]) const {
-    load_lfs<DIM, EDGE, real>(P, lf + (size_t)k * Lattice<DIM>::Q * P.plane, z, x, l);
+    using L = Lattice<DIM>;
+    constexpr int Q = L::Q;
+    const int pl = (int)P.plane;
+    const real* lk = lam + (size_t)k * Q * pl;
+    const real* ak = lA + (size_t)k * pl;
+    auto v = [&](int i, int m) { return omt * gld(lk + i * pl + m) + gld(ak + m); };
+    if constexpr (!EDGE) {
+      const int b = aidx(P, z, x);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) l[i] = v(i, b + L::c(i, 0) + (DIM >= 2 ? L::c(i, 1) * P.nzp : 0));
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        int yz = z + L::c(i, 0), yx = DIM >= 2 ? x + L::c(i, 1) : 0;
+        if (P.periodic) {
+          yz = wrap_or_clamp(yz, P.n[0], 1);
+          if (DIM >= 2) yx = wrap_or_clamp(yx, P.n[1], 1);
+          l[i] = v(i, aidx(P, yz, yx));
+          continue;
+        }
+        real s = 0;
+        const bool in = yz >= 1 && yz <= P.n[0] - 2 && (DIM < 2 || (yx >= 1 && yx <= P.n[1] - 2));
+        if (in) {
+          int cz[3] = {yz, -1, -1}, cx[3] = {yx, -1, -1};
+          if (yz == 1) cz[1] = 0;
+          if (yz == P.n[0] - 2) cz[2] = P.n[0] - 1;
+          if (DIM >= 2) {
+            if (yx == 1) cx[1] = 0;
+            if (yx == P.n[1] - 2) cx[2] = P.n[1] - 1;
+          }
+#pragma unroll
+          for (int qz = 0; qz < 3; ++qz) {
+            if (cz[qz] < 0) continue;
+#pragma unroll
+            for (int qx = 0; qx < (DIM >= 2 ? 3 : 1); ++qx) {
+              if (cx[qx] < 0) continue;
+              s += v(i, aidx(P, cz[qz], cx[qx]));
+            }
+          }
+        }
+        l[i] = s;
+      }
+    }
   }
 };
 
@@ -624,6 +614,13 @@ __device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& sr
   if (k >= Model<DIM, CL>::K) break;
   real lk[Q];
   src.load(k, z, x, lk);
+  // the gathered values, from which the next reverse step forms this step's
+  // population adjoints (NextLSrc)
+  {
+    real* lo = reinterpret_cast<real*>(A.lf_out) + (size_t)k * Q * pl + id;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) lo[i * pl] = lk[i];
+  }
   const real w0l = real(L::w(0)) * lk[0];
   real m0 = w0l, mA = w0l * even0, mu_[3] = {0, 0, 0};
 #pragma unroll
@@ -651,21 +648,29 @@ __device__ __forceinline__ void adj_coll_node(const AdjParams& A, const LSrc& sr
   }
 }
 
-// grid: (z tiles, x tiles, K); 2048 threads per SM (32 registers: 3.10-3.13
-// against 3.13-3.14 for the sweep's cost ratio at the compiler's 40)
+// Resident threads per SM the gather kernel's register budget is held to
+// in FP32: 2048 (32 registers, 32 bytes of spills; the sweep's cost ratio
+// 3.03 against 3.05-3.06 at 1536 threads and 40 registers); the FP64 kernels
+// are left to the compiler (held to 32 registers they spill 330 bytes).
+template <typename real, int NT> struct AdjGatherBlocks { static constexpr int value = 1; };
+template <int NT> struct AdjGatherBlocks<float, NT> { static constexpr int value = 2048 / NT; };
+
+// grid: (z tiles, x tiles, K)
 template <int DIM, int CL, typename real, int TZ, int TX>
-__global__ void __launch_bounds__(TZ* TX, 2048 / (TZ * TX)) adj_coll_kernel(const AdjParams A) {
+__global__ void __launch_bounds__(TZ* TX, (AdjGatherBlocks<real, TZ * TX>::value)) adj_coll_kernel(const AdjParams A) {
   pdl_enter();
   const StepParams& P = A.P;
   const int z = blockIdx.x * TZ + threadIdx.x % TZ;
   const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
   const int k = blockIdx.z * kAdjSetsPerThread;
-  const real* lf = reinterpret_cast<const real*>(A.lf_in);
+  const real* lam = reinterpret_cast<const real*>(A.lf_in);
+  const real* lA = reinterpret_cast<const real*>(A.lAf);
+  const real omt = real(1) - consts<real>(P).inv_tau;
   if (warp_interior<DIM, TZ, TX>(P)) {
-    adj_coll_node<DIM, CL, real>(A, GlobalLSrc<DIM, false, real>{P, lf}, z, x, k);
+    adj_coll_node<DIM, CL, real>(A, NextLSrc<DIM, false, real>{P, lam, lA, omt}, z, x, k);
   } else {
     if (z >= P.n[0] || (DIM >= 2 && x >= P.n[1])) return;
-    adj_coll_node<DIM, CL, real>(A, GlobalLSrc<DIM, true, real>{P, lf}, z, x, k);
+    adj_coll_node<DIM, CL, real>(A, NextLSrc<DIM, true, real>{P, lam, lA, omt}, z, x, k);
   }
 }
 
@@ -842,43 +847,11 @@ __device__ __forceinline__ void adj_field_node(const AdjParams& A, int z, int x,
     for (int k = 0; k < K; ++k) lA[k] = gld(rA + k * pl + id);
     decode_adjoint<DIM, CL, real>(P, S, N, lm, lA);
 
-    // the population adjoint of the previous state adds lA (adj_pop_kernel)
+    // the population adjoint of the previous state adds lA (formed by the
+    // next reverse step's gather, NextLSrc)
     real* lAf = reinterpret_cast<real*>(A.lAf);
 #pragma unroll
     for (int k = 0; k < K; ++k) lAf[k * pl + id] = lA[k];
-  }
-}
-
-// Population adjoint of the previous state, one set k at one node:
-// lambda_f^n = (1 - 1/tau) lambda_fs + lambda_A, with lambda_fs gathered as
-// in adj_coll_node and lambda_A from adj_field_kernel.  grid: (z tiles,
-// x tiles, K)
-template <int DIM, int CL, typename real, int TZ, int TX>
-__global__ void __launch_bounds__(TZ* TX, 2048 / (TZ * TX)) adj_pop_kernel(const AdjParams A) {
-  pdl_enter();
-  using L = Lattice<DIM>;
-  constexpr int Q = L::Q;
-  const StepParams& P = A.P;
-  const StepConst<real>& S = consts<real>(P);
-  const int z = blockIdx.x * TZ + threadIdx.x % TZ;
-  const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
-  const real* lf = reinterpret_cast<const real*>(A.lf_in);
-  const bool interior = warp_interior<DIM, TZ, TX>(P);
-  if (!interior && (z >= P.n[0] || (DIM >= 2 && x >= P.n[1]))) return;
-  const int pl = (int)P.plane;
-  const int id = aidx(P, z, x);
-  const real omt = real(1) - S.inv_tau;
-#pragma unroll
-  for (int ks = 0; ks < kAdjSetsPerThread; ++ks) {
-    const int k = blockIdx.z * kAdjSetsPerThread + ks;
-    if (k >= Model<DIM, CL>::K) break;
-    real lk[Q];
-    if (interior) GlobalLSrc<DIM, false, real>{P, lf}.load(k, z, x, lk);
-    else GlobalLSrc<DIM, true, real>{P, lf}.load(k, z, x, lk);
-    const real lAk = gld(reinterpret_cast<const real*>(A.lAf) + k * pl + id);
-    real* lok = reinterpret_cast<real*>(A.lf_out) + (size_t)k * Q * pl + id;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) lok[i * pl] = omt * lk[i] + lAk;
   }
 }
 

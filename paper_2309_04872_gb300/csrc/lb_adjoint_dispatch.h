@@ -15,12 +15,11 @@ struct AdjKernelSet {
   int K, NG, NPREV, NTAPE;
   int tz, tx;  // tile of the per-node kernels
   int spt;     // sets per thread of the per-(node, set) kernels: grid.z = ceil(K / spt)
-  // per (node, set), grid.z = K: the gathers of the next state's population
-  // adjoints, before adj_local (coll) and after adj_field (pop)
+  // per (node, set), grid.z = K: the gather of the next state's population
+  // adjoints, before adj_local
   void (*coll)(const AdjParams&, dim3 grid, cudaStream_t);
   void (*local)(const AdjParams&, dim3 grid, cudaStream_t);
   void (*field)(const AdjParams&, dim3 grid, cudaStream_t);
-  void (*pop)(const AdjParams&, dim3 grid, cudaStream_t);
   void (*init_rows)(const StepParams&, const void* lE, const void* lB, const double* Kx, double* rows, dim3 grid,
                     cudaStream_t);
   void (*seed)(void* lE, long long idx, double v, cudaStream_t);
