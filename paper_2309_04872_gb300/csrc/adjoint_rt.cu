@@ -304,7 +304,14 @@ struct Sweep {
     A.rows = rows_of_set(nsets);
     A.Tx = (const double*)r->Tx.p;
     const dim3 g((unsigned)((h->n[0] + r->ak.tz - 1) / r->ak.tz), (unsigned)r->ntx, 1);
-    const dim3 gk(g.x, g.y, (unsigned)((r->ak.K + r->ak.spt - 1) / r->ak.spt));
+    // 2D: extra block rows for the edge band (see adj_coll_kernel)
+    A.band_rows = 0;
+    if (h->prm.dim == 2 && h->n[0] >= 7 && h->n[1] >= 7) {
+      const long long band = 6LL * h->n[0] + 6LL * (h->n[1] - 6);
+      const long long per_row = (long long)g.x * r->ak.tz * r->ak.tx;
+      A.band_rows = (int)((band + per_row - 1) / per_row);
+    }
+    const dim3 gk(g.x, g.y + (unsigned)A.band_rows, (unsigned)((r->ak.K + r->ak.spt - 1) / r->ak.spt));
     r->ak.coll(A, gk, h->stream);
     CK_LAUNCH(h, "adj_coll_kernel launch");
     r->ak.local(A, g, h->stream);

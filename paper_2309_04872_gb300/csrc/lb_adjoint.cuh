@@ -660,12 +660,34 @@ template <int DIM, int CL, typename real, int TZ, int TX>
 __global__ void __launch_bounds__(TZ* TX, (AdjGatherBlocks<real, TZ * TX>::value)) adj_coll_kernel(const AdjParams A) {
   pdl_enter();
   const StepParams& P = A.P;
-  const int z = blockIdx.x * TZ + threadIdx.x % TZ;
-  const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
   const int k = blockIdx.z * kAdjSetsPerThread;
   const real* lam = reinterpret_cast<const real*>(A.lf_in);
   const real* lA = reinterpret_cast<const real*>(A.lAf);
   const real omt = real(1) - consts<real>(P).inv_tau;
+  if (DIM == 2 && A.band_rows > 0) {
+    // 2D: the nodes within 3 of an edge (the band, whose gathers fold the
+    // boundary copies) are taken by the last band_rows rows of blocks, one
+    // band node per thread; the tiles' threads skip them, so no warp mixes
+    // the two gathers
+    const int n0 = P.n[0], n1 = P.n[1];
+    const int ntiles_x = (int)gridDim.y - A.band_rows;
+    if ((int)blockIdx.y < ntiles_x) {
+      const int z = blockIdx.x * TZ + threadIdx.x % TZ, x = blockIdx.y * TX + threadIdx.x / TZ;
+      if (z < 3 || z >= n0 - 3 || x < 3 || x >= n1 - 3) return;
+      adj_coll_node<DIM, CL, real>(A, NextLSrc<DIM, false, real>{P, lam, lA, omt}, z, x, k);
+    } else {
+      const int t = ((blockIdx.y - ntiles_x) * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+      int z, x;
+      if (t < 3 * n0) { x = t / n0; z = t - x * n0; }
+      else if (t < 6 * n0) { const int u = t - 3 * n0; x = n1 - 3 + u / n0; z = u % n0; }
+      else if (t < 6 * n0 + 6 * (n1 - 6)) { const int u = t - 6 * n0, j = u % 6; x = 3 + u / 6; z = j < 3 ? j : n0 - 6 + j; }
+      else return;
+      adj_coll_node<DIM, CL, real>(A, NextLSrc<DIM, true, real>{P, lam, lA, omt}, z, x, k);
+    }
+    return;
+  }
+  const int z = blockIdx.x * TZ + threadIdx.x % TZ;
+  const int x = DIM >= 2 ? blockIdx.y * TX + threadIdx.x / TZ : 0;
   if (warp_interior<DIM, TZ, TX>(P)) {
     adj_coll_node<DIM, CL, real>(A, NextLSrc<DIM, false, real>{P, lam, lA, omt}, z, x, k);
   } else {

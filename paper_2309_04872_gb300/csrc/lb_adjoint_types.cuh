@@ -31,6 +31,8 @@ struct AdjParams {
   void* cU;                 // [K][DIM][plane]
   void* lAf;                // [K][plane]  the node's adjoint of A_k after the field terms (adj_field_kernel)
   void* cW;                 // WARMC [2][DIM][plane]: the node's w = lambda u, and the previous step's (adj_coll_kernel)
+  int band_rows;            // 2D, 7 or more nodes per axis: rows of adj_coll_kernel blocks (after the tiles' rows)
+                            // that take the nodes within 3 of an edge, one per thread; 0: the tiles take every node
   double* rows;             // [2][gridDim.y][n0] partial row sums of this step
   const double* Tx;         // [2][n1]: T(x) and T(x) x^2 / sigma_r^3 at the E_z slots
 };
