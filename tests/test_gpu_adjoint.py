@@ -116,6 +116,30 @@ def test_fp64_adjoint_from_random_state(dim, closure):
     assert _rel(gg[:names], go[:names], scale) < 1e-9, (gg, go)
 
 
+# 2D grids at and around the size where the reverse step's gather gives the
+# nodes within 3 of an edge their own blocks (both sides at least 7 nodes):
+# a band that covers all but one row or column, one whose side columns are a
+# single node wide, one just too narrow for it, and a one-tile grid.
+SMALL_GRIDS = [(7, 7), (24, 7), (9, 8), (24, 6), (6, 13), (30, 4)]
+
+
+@pytest.mark.parametrize("n", SMALL_GRIDS)
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+def test_fp64_adjoint_on_small_grids_matches_oracle(n, closure):
+    c = _cfg(2, closure, n=n, z0=0.6 + 0.1 * (n[0] // 2), sigma_z=0.3, sigma_r=0.3)
+    st = _random_state(c, 70 + n[0] + n[1])
+    N = 12
+    Jo, go, _ = _oracle_adjoint(c, N, st)
+    Jg, gg, _ = _gpu_adjoint(c, N, state=st)
+    assert abs(Jg - Jo) <= 1e-12 * max(abs(Jo), 1e-3)
+    scale = np.max(np.abs(go[:3]))
+    assert scale > 1e-8
+    assert _rel(gg[:3], go[:3], scale) < 1e-9, (gg, go)
+    # FP32 storage: the same gather in single precision, against FP64
+    _, g32, _ = _gpu_adjoint(c, N, "fp32", state=st)
+    assert _rel(g32[:3], gg[:3], scale) < 1e-4, (g32, gg)
+
+
 @pytest.mark.parametrize("closure", ["lec", "warmc"])
 def test_fp64_profile_gradient_matches_oracle(closure):
     prof = 0.2 * np.exp(-0.5 * (np.arange(-24, 25) * 0.05 / 0.6) ** 2)
