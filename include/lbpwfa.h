@@ -73,7 +73,8 @@ enum { LBPWFA_CARTESIAN = 0, LBPWFA_AXISYMMETRIC = 1 };
 /* Problem statement (Sec. 6, Eq. bunch-density and Qtilde). */
 typedef struct {
   int dim;                 /* 1, 2 or 3 */
-  int n[3];                /* nodes along z, x, y; absent axes ignored; >= 3 */
+  int n[3];                /* nodes along z, x, y; absent axes ignored; >= 3;
+                              x and y at most 262 140 (4 x 65 535 tiles) */
   double dx;               /* lattice spacing, k_p^-1 */
   double courant;          /* C = c dt / dx; dt = C dx. 0 < C <= 1/sqrt(dim) */
   double tau;              /* BGK relaxation time in units of dt, > 1/2
@@ -365,7 +366,8 @@ typedef struct {
  * lbpwfa_step form the window.  Replaces an earlier recording.  Stepping past
  * max_steps returns STATE; lbpwfa_set_state and lbpwfa_load end the
  * recording.  Errors: INVALID (3D, FP16S storage, a batch member, bad
- * arguments), OOM, CUDA. */
+ * arguments, a grid whose tape entry, the K set moments and the E and B
+ * components of each node, passes 2^31 values), OOM, CUDA. */
 int lbpwfa_record(lbpwfa_t h, const lbpwfa_record_params* rp);
 
 typedef struct {

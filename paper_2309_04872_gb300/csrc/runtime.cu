@@ -103,6 +103,10 @@ int validate(const lbpwfa_params* p) {
   if (p->geometry == LBPWFA_AXISYMMETRIC &&
       (p->dim != 2 || p->boundary != LBPWFA_OPEN || p->kernel_variant == 2 || p->kernel_variant == 4))
     return LBPWFA_ERR_INVALID;
+  // the tiled kernels launch (z tiles, x tiles, y tiles) with tiles at least
+  // 4 nodes wide in x and y, and a grid's y and z extents are at most 65535
+  if (p->dim >= 2 && p->n[1] > 4 * 65535) return LBPWFA_ERR_INVALID;
+  if (p->dim >= 3 && p->n[2] > 4 * 65535) return LBPWFA_ERR_INVALID;
   long long cells = 1;
   for (int a = 0; a < p->dim; ++a) cells *= p->n[a];
   if (cells > (1LL << 34)) return LBPWFA_ERR_INVALID;

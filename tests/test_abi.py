@@ -62,7 +62,8 @@ def test_invalid_parameters_rejected_before_any_device_work(lib_path):
     bad = [dict(tau=0.5), dict(courant=0.8), dict(n=(2, 8)), dict(dim=4, n=(8, 8, 8)), dict(dv=2),
            dict(mu=-1e-3), dict(sigma_z=0.0), dict(sigma_r=-1.0), dict(dx=0.0), dict(closure=5),
            dict(geometry=2), dict(geometry="axisymmetric", dim=3, n=(8, 8, 8)),
-           dict(geometry="axisymmetric", boundary="periodic"), dict(record_tape=-1), dict(checkpoint_every=-5)]
+           dict(geometry="axisymmetric", boundary="periodic"), dict(record_tape=-1), dict(checkpoint_every=-5),
+           dict(n=(16, 4 * 65535 + 1)), dict(dim=3, n=(8, 8, 4 * 65535 + 1)), dict(dim=3, n=(8, 4 * 65535 + 1, 8))]
     for b in bad:
         p, keep = lbpwfa.make_params({**base, **b})
         h = ctypes.c_void_p()
