@@ -366,8 +366,8 @@ typedef struct {
  * lbpwfa_step form the window.  Replaces an earlier recording.  Stepping past
  * max_steps returns STATE; lbpwfa_set_state and lbpwfa_load end the
  * recording.  Errors: INVALID (3D, FP16S storage, a batch member, bad
- * arguments, a grid whose tape entry, the K set moments and the E and B
- * components of each node, passes 2^31 values), OOM, CUDA. */
+ * arguments, a grid of more than 2^31 / max(K + E and B components, K dim,
+ * Q) cells, beyond the reverse kernels' 32-bit offsets), OOM, CUDA. */
 int lbpwfa_record(lbpwfa_t h, const lbpwfa_record_params* rp);
 
 typedef struct {

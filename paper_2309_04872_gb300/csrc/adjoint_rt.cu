@@ -140,12 +140,16 @@ extern "C" int lbpwfa_record(lbpwfa_t h, const lbpwfa_record_params* rp) {
     adj_free(h);
     return LBPWFA_ERR_INVALID;
   }
-  if ((long long)r->ak.NTAPE * h->plane >= (1LL << 31)) {
-    // the kernels address a tape entry's planes with 32-bit offsets
-    adj_free(h);
-    h->err = "lbpwfa_record: a tape entry's " + std::to_string(r->ak.NTAPE) + " planes of " +
-             std::to_string(h->plane) + " cells pass 32-bit offsets";
-    return LBPWFA_ERR_INVALID;
+  {
+    // the kernels address the planes of a tape entry, of the per-set
+    // velocity terms (K x dim) and of a population set with 32-bit offsets
+    const long long span = std::max({(long long)r->ak.NTAPE, (long long)r->ak.K * h->prm.dim, (long long)h->Q});
+    if (span * h->plane >= (1LL << 31)) {
+      adj_free(h);
+      h->err = "lbpwfa_record: " + std::to_string(span) + " planes of " + std::to_string(h->plane) +
+               " cells pass 32-bit offsets";
+      return LBPWFA_ERR_INVALID;
+    }
   }
   r->cap = rp->max_steps;
   r->C = rp->checkpoint_every >= rp->max_steps ? 0 : rp->checkpoint_every;
