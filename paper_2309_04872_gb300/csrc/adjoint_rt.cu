@@ -20,6 +20,10 @@ struct AdjRec {
   AdjKernelSet ak{};
   bool armed = false;
   long long start_step = 0, len = 0, cap = 0, C = 0;
+  // checkpoints: the forward writes the tape of the window's last two
+  // segments (from step pre_from on) into their halves, so the sweep
+  // recomputes neither when the window was stepped to its end; -1: none
+  long long pre_from = -1;
   bool start_from_driver = false;
   int start_have_prev = 0;
   size_t entry_bytes = 0;   // one tape entry
@@ -95,11 +99,15 @@ int adj_before_step(lbpwfa_s* h, void** tape) {
   }
   if (r->C == 0) {
     *tape = (char*)r->tape.p + (size_t)r->len * r->entry_bytes;
-  } else if (r->len % r->C == 0) {
+  } else {
     const long long s = r->len / r->C;
-    int st = save_state(h, (char*)r->ckpt.p + (size_t)s * r->state_bytes);
-    if (st != LBPWFA_OK) return st;
-    r->ckpt_have_prev[s] = h->have_prev;
+    if (r->len % r->C == 0) {
+      int st = save_state(h, (char*)r->ckpt.p + (size_t)s * r->state_bytes);
+      if (st != LBPWFA_OK) return st;
+      r->ckpt_have_prev[s] = h->have_prev;
+    }
+    if (r->pre_from >= 0 && r->len >= r->pre_from)
+      *tape = (char*)r->tape.p + ((size_t)(s & 1) * r->C + (size_t)(r->len - s * r->C)) * r->entry_bytes;
   }
   r->len += 1;
   return LBPWFA_OK;
@@ -163,6 +171,7 @@ extern "C" int lbpwfa_record(lbpwfa_t h, const lbpwfa_record_params* rp) {
     if (st == LBPWFA_OK && h->prev.bytes) st = ab(h, r, r->prev0, h->prev.bytes);
   } else {
     const long long nck = (r->cap + r->C - 1) / r->C;
+    r->pre_from = (nck >= 2 ? nck - 2 : 0) * r->C;
     st = ab(h, r, r->tape, 2 * (size_t)r->C * r->entry_bytes);
     if (st == LBPWFA_OK) st = ab(h, r, r->ckpt, (size_t)nck * r->state_bytes);
     if (st == LBPWFA_OK) st = ab(h, r, r->finalst, r->state_bytes);
@@ -388,12 +397,18 @@ extern "C" int lbpwfa_adjoint_step(lbpwfa_t h, lbpwfa_adjoint_io* io) {
     int st = save_state(h, (char*)r->finalst.p);
     if (st != LBPWFA_OK) return st;
     const long long nseg = (r->len + r->C - 1) / r->C;
+    // segments from pre_seg on hold the tape the forward wrote (the window
+    // was stepped to its end); the halves are overwritten below, so a retry
+    // after an error recomputes every segment
+    const long long pre_seg = r->pre_from >= 0 && r->len == r->cap ? r->pre_from / r->C : nseg;
+    r->pre_from = -1;
     // segment s is recomputed into tape half s % 2 on the second stream, as
     // soon as the reverse of segment s + 2 has consumed that half, so the
     // recompute of segment s - 1 runs while segment s is reversed
     cudaStream_t ms = h->stream;
     auto half = [&](long long s) { return (char*)r->tape.p + (size_t)(s & 1) * r->C * r->entry_bytes; };
     for (int j = 0; j < 2; ++j) CK(h, cudaEventRecord(r->ev_rev[j], ms));  // after the state was saved
+    for (long long s = pre_seg; s < nseg; ++s) CK(h, cudaEventRecord(r->ev_rec[s & 1], ms));  // written in order
     auto recompute = [&](long long s) -> int {
       const long long b = s * r->C, e = std::min(r->len, b + r->C);
       CK(h, cudaStreamWaitEvent(r->rs, r->ev_rev[s & 1], 0));
@@ -407,12 +422,14 @@ extern "C" int lbpwfa_adjoint_step(lbpwfa_t h, lbpwfa_adjoint_io* io) {
       CK(h, cudaEventRecord(r->ev_rec[s & 1], r->rs));
       return LBPWFA_OK;
     };
-    st = recompute(nseg - 1);
-    if (st != LBPWFA_OK) return st;
+    if (nseg - 1 < pre_seg) {
+      st = recompute(nseg - 1);
+      if (st != LBPWFA_OK) return st;
+    }
     for (long long s = nseg - 1; s >= 0; --s) {
       const long long b = s * r->C, e = std::min(r->len, b + r->C);
       CK(h, cudaStreamWaitEvent(ms, r->ev_rec[s & 1], 0));
-      if (s > 0) {
+      if (s > 0 && s - 1 < pre_seg) {
         st = recompute(s - 1);
         if (st != LBPWFA_OK) return st;
       }

@@ -199,6 +199,25 @@ def test_checkpointed_equals_kept_tape(precision, closure):
         assert np.array_equal(g1, g0) and np.array_equal(p1, p0)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpointed_window_stepped_short_of_its_end(precision):
+    """With checkpoints the forward writes the tape of the window's last two
+    segments; a window stepped short of max_steps does not use it and
+    recomputes every segment: the gradient is bitwise the kept tape's."""
+    c = _cfg(2, "warmc")
+    wit = _witness(c)
+    with lb.Run(c, precision) as run:
+        run.record(25, 0)
+        run.step(25)
+        J0, g0, _ = run.adjoint(wit)
+    for cap, C in ((30, 7), (26, 12), (40, 9), (25, 12)):
+        with lb.Run(c, precision) as run:
+            run.record(cap, C)
+            run.step(25)
+            J1, g1, _ = run.adjoint(wit)
+        assert J1 == J0 and np.array_equal(g1, g0), (cap, C, g1, g0)
+
+
 def test_recording_armed_at_create_equals_lbpwfa_record():
     """record_tape / checkpoint_every in the parameters start the window at
     create, as lbpwfa_record does; the gradients are bitwise the same."""
