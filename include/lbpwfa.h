@@ -212,11 +212,15 @@ int lbpwfa_step(lbpwfa_t h, int64_t nsteps);
  *   [theta_xx + theta_zz - theta^00 u^2 - theta_yy (1 + u_x^2)] /
  *   (1 + u_z^2), theta^00 = u_i u_j theta_ij; 2D WARMC only, else 0).
  * dst holds count >= popcount(mask & 0x3FFFF) * ncell doubles, on the device
- * when dst_is_device, else on the host.  Errors: INVALID, CUDA. */
+ * when dst_is_device, else on the host.  A page-locked host buffer that CUDA
+ * maps into the device (cudaHostAlloc, cudaMallocHost) is written in place
+ * by the kernel; other host memory through a device staging buffer.  Host
+ * outputs are complete on return.  Errors: INVALID, CUDA. */
 int lbpwfa_moments(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_is_device);
 
 /* Raw field slots (FP64), mask bits 0 E_x, 1 E_y, 2 E_z, 3 B_x, 4 B_y, 5 B_z;
- * E at t_{n-1/2}, B at t_n, on the dual Yee grid described above. */
+ * E at t_{n-1/2}, B at t_n, on the dual Yee grid described above.  Host
+ * buffers as for lbpwfa_moments. */
 int lbpwfa_fields(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_is_device);
 
 /* Wake diagnostic on the device (the dispersion measurement of Sec. 6,
@@ -263,8 +267,10 @@ int lbpwfa_advected(lbpwfa_t h, double* dst, size_t count, int dst_is_device);
  * Any pointer may be NULL to keep that part.  With open boundaries the
  * boundary nodes take the populations of their nearest bulk node
  * (Eq. open-bc) and wall slots of E are zeroed.  The backward time
- * differences of WARMC restart (zero on the next step).
- * Errors: INVALID, OOM, CUDA. */
+ * differences of WARMC restart (zero on the next step).  Mapped page-locked
+ * host buffers (all given ones) are read in place by the import kernels,
+ * other host memory through a device staging buffer; host inputs may be
+ * reused on return.  Errors: INVALID, OOM, CUDA. */
 int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double* B,
                      int src_is_device);
 

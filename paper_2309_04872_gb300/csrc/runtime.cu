@@ -220,6 +220,21 @@ dim3 step_grid(const lbpwfa_s* h) {
               (unsigned)((h->n[2] + h->ks.ty - 1) / h->ks.ty));
 }
 
+// The device address of a caller's host buffer that the device can read and
+// write directly: page-locked memory mapped into the device's address space
+// (cudaHostAlloc, cudaMallocHost, cudaHostRegister with mapping); null for
+// pageable memory or when CUDA reports no device address for it.  The import
+// and export kernels then move the values over the host link themselves,
+// without a staging copy.
+void* mapped_host(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // Copy device results to a caller buffer (host or device).
 int deliver(lbpwfa_s* h, const void* src, void* dst, size_t bytes, int dst_is_device) {
   CK(h, cudaMemcpyAsync(dst, src, bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -585,14 +600,18 @@ int lbpwfa_moments(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst
   if (count < need) return LBPWFA_ERR_INVALID;
   AuxParams A = aux_params(h);
   double* out = dst;
-  if (!dst_is_device) {
+  double* mapped = dst_is_device ? nullptr : (double*)mapped_host(dst);
+  if (mapped) {
+    out = mapped;
+  } else if (!dst_is_device) {
     int r = ensure_scratch(h, need * sizeof(double));
     if (r != LBPWFA_OK) return r;
     out = (double*)h->scratch.p;
   }
   h->ks.moments(A, h->f[h->cur].p, mask, out, h->stream);
   CK_LAUNCH(h, "moments_kernel launch");
-  if (!dst_is_device) return deliver(h, out, dst, need * sizeof(double), 0);
+  if (mapped) CK(h, cudaStreamSynchronize(h->stream));
+  else if (!dst_is_device) return deliver(h, out, dst, need * sizeof(double), 0);
   return LBPWFA_OK;
 }
 
@@ -609,7 +628,10 @@ int lbpwfa_fields(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_
   if (count < need) return LBPWFA_ERR_INVALID;
   AuxParams A = aux_params(h);
   double* out = dst;
-  if (!dst_is_device) {
+  double* mapped = dst_is_device ? nullptr : (double*)mapped_host(dst);
+  if (mapped) {
+    out = mapped;
+  } else if (!dst_is_device) {
     int r = ensure_scratch(h, need * sizeof(double));
     if (r != LBPWFA_OK) return r;
     out = (double*)h->scratch.p;
@@ -623,7 +645,8 @@ int lbpwfa_fields(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_
                         make_int4(b4[0], b4[1], b4[2], b4[3]), out + (size_t)j0 * h->ncell, h->stream);
     CK_LAUNCH(h, "export_fields_kernel launch");
   }
-  if (!dst_is_device) return deliver(h, out, dst, need * sizeof(double), 0);
+  if (mapped) CK(h, cudaStreamSynchronize(h->stream));
+  else if (!dst_is_device) return deliver(h, out, dst, need * sizeof(double), 0);
   return LBPWFA_OK;
 }
 
@@ -715,15 +738,24 @@ int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double*
   if (!h) return LBPWFA_ERR_INVALID;
   AuxParams A = aux_params(h);
   const size_t nf = (size_t)h->K * h->Q * h->ncell, nfl = 3 * (size_t)h->ncell;
+  const double *fd = f, *Ed = E, *Bd = B;
+  // page-locked host buffers mapped into the device are read in place
+  bool mapped = !src_is_device;
+  if (mapped) {
+    const double* fm = f ? (const double*)mapped_host(f) : nullptr;
+    const double* Em = E ? (const double*)mapped_host(E) : nullptr;
+    const double* Bm = B ? (const double*)mapped_host(B) : nullptr;
+    mapped = (!f || fm) && (!E || Em) && (!B || Bm);
+    if (mapped) { fd = fm; Ed = Em; Bd = Bm; }
+  }
   size_t need = 0;
-  if (!src_is_device) need = (f ? nf : 0) + (E ? nfl : 0) + (B ? nfl : 0);
+  if (!src_is_device && !mapped) need = (f ? nf : 0) + (E ? nfl : 0) + (B ? nfl : 0);
   if (need) {
     int r = ensure_scratch(h, need * sizeof(double));
     if (r != LBPWFA_OK) return r;
   }
   double* sp = (double*)h->scratch.p;
-  const double *fd = f, *Ed = E, *Bd = B;
-  if (!src_is_device) {
+  if (!src_is_device && !mapped) {
     size_t o = 0;
     if (f) { CK(h, cudaMemcpyAsync(sp + o, f, nf * 8, cudaMemcpyHostToDevice, h->stream)); fd = sp + o; o += nf; }
     if (E) { CK(h, cudaMemcpyAsync(sp + o, E, nfl * 8, cudaMemcpyHostToDevice, h->stream)); Ed = sp + o; o += nfl; }
