@@ -196,13 +196,14 @@ __global__ void export_pops_kernel(AuxParams A, const typename Prec<PR>::store* 
 // FP64 advected scalars of node e from the stored populations.
 template <int DIM, int CL, int PR>
 __device__ __forceinline__ void advected_d(const AuxParams& A, const typename Prec<PR>::store* fs,
-                                           const int* e, double* Av) {
+                                           const int* e, double* Av, int nsets = Model<DIM, CL>::K) {
   using L = Lattice<DIM>;
   using M = Model<DIM, CL>;
   int b[3] = {e[0], e[1], e[2]};
   if (!A.periodic)
     for (int a = 0; a < DIM; ++a) b[a] = min(max(e[a], 1), A.n[a] - 2);
-  for (int k = 0; k < M::K; ++k) {
+  for (int k = nsets; k < M::K; ++k) Av[k] = A.Arest[k];
+  for (int k = 0; k < nsets; ++k) {
     double s = 0.0;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
@@ -241,13 +242,17 @@ __global__ void moments_kernel(AuxParams A, const typename Prec<PR>::store* fs, 
   if (c >= A.ncell) return;
   int e[3];
   unflatten(A, c, e);
+  // n alone needs only the density set and no decode
+  const bool decode = (mask & ~1u) != 0;
   double Av[M::K];
-  advected_d<DIM, CL, PR>(A, fs, e, Av);
+  advected_d<DIM, CL, PR>(A, fs, e, Av, decode ? M::K : 1);
   double v[18];
   for (int j = 0; j < 18; ++j) v[j] = 0.0;
   const double n = Av[0];
   v[0] = n;
-  if constexpr (CL == CL_LEC) {
+  if (!decode) {
+    // v[0] = n is all the mask asks for
+  } else if constexpr (CL == CL_LEC) {
     double Ap[DIM], u[DIM], Pi, g;
     for (int a = 0; a < DIM; ++a) Ap[a] = Av[1 + a];
     decode_lec<DIM, double>(n, Ap, (1.0 + 0.5 * A.D) * A.mu, A.D, u, Pi, &g);
