@@ -385,6 +385,21 @@ def test_pinned_host_buffers_are_read_and_written_in_place():
     assert np.abs(got[0][0][0] - 1.0).max() > 0  # a perturbed state, not the rest state
 
 
+@pytest.mark.parametrize("closure", ["lec", "warmc"])
+def test_density_alone_equals_density_of_the_full_decode(closure):
+    """A request for n alone reads only the density set and skips the
+    decode; its values are bitwise the n block of a full request."""
+    cfg = _cfg(2, closure, "open")
+    orc = O.Oracle(cfg)
+    f, E, B = _random_state(orc, 13, cfg["mu"])
+    with lb.Run(cfg, "fp32") as run:
+        run.set_state(f, E, B)
+        run.step(5)
+        n_alone = run.moments(lb.M_N)[0]
+        full = run.moments(0x3FFFF)
+    assert np.array_equal(n_alone, full[0])
+
+
 def test_zero_steps_and_edge_sizes():
     for dim in (1, 2, 3):
         cfg = _cfg(dim, "lec", "open", n=(3, 3, 3)[:dim])
