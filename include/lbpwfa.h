@@ -284,6 +284,22 @@ int lbpwfa_reduce(lbpwfa_t h, double out[3]);
 
 int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info);
 
+/* Choose the run's step kernel by timing: every kernel variant the run can
+ * take (1 plain, 2 TMA box per CTA, 3 persistent, 4 3D marching; the step
+ * of lbpwfa_step, Sec. 2.1 algorithm, which they all compute) steps the
+ * current state twice to warm up and five times under CUDA events, the
+ * state is put back exactly (a device copy of f, E, B and the previous-step
+ * values, allocated for the call), and the fastest is kept for the run's
+ * later steps (lbpwfa_info reports it).  With LBPWFA_TUNE_CACHE naming a
+ * JSON file, the choice is stored there under a key of the device name,
+ * dim, closure, precision, boundary, geometry and grid, and read back by
+ * later calls for the same key, which then time nothing.  ms_out (host,
+ * 5 doubles, may be NULL): per variant the mean step time in ms, -1 where
+ * not timed.  The run's step count and recording are unchanged.
+ * Synchronises.  Errors: INVALID, STATE (a batch member), OOM (no room for
+ * the copy of the state), TIMEOUT, CUDA. */
+int lbpwfa_autotune(lbpwfa_t h, double* ms_out);
+
 /* The sums of lbpwfa_reduce for callers that cannot allocate device memory:
  * code whose device memory belongs to another allocator (a framework's
  * caching allocator, an embedding that reserves the whole device) or whose

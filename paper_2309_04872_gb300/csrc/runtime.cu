@@ -364,6 +364,51 @@ int launch_step(lbpwfa_s* h, void* tape) {
   return LBPWFA_OK;
 }
 
+// The step kernel of a kernel variant (lbpwfa_params.kernel_variant; the
+// axisymmetric geometry's own rules are set by lbpwfa_create).  A variant
+// the run cannot take falls back to the plain kernel, which computes the
+// same step.
+void select_kernel(lbpwfa_s* h, int variant) {
+  const int dim = h->prm.dim;
+  // 3D: marching columns unless the tiled kernel is asked for (variant 1)
+  h->use_march = dim == 3 && (variant == 0 || variant == 4) && h->ks.has_march;
+  if (h->use_march && h->ks.prepare_march() != cudaSuccess) {
+    cudaGetLastError();
+    h->use_march = false;
+  }
+  const bool tma_ok = dim == 2 && h->prm.boundary == LBPWFA_OPEN;
+  // automatic choice for LEC: the persistent refilling CTAs where the tile
+  // table marks them faster, else one TMA box per CTA; WARMC's 72-plane box
+  // leaves two CTAs per SM and the global-memory pull is faster there
+  const bool persist_auto = variant == 0 && h->prm.closure == LBPWFA_LEC && h->ks.persist_auto;
+  h->use_persist = (variant == 3 || persist_auto) && tma_ok && h->ks.has_persist && h->num_sms > 0;
+  if (h->use_persist) {
+    cudaError_t e = h->use_axi ? h->ks.prepare_persist_axi() : h->ks.prepare_persist();
+    bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0], h->ks.per_box) &&
+              make_pop_map(h, h->f[1].p, &h->maps[1], h->ks.per_box);
+    if (!ok) {
+      cudaGetLastError();
+      h->use_persist = false;
+    }
+  }
+  const bool tma_auto = variant == 0 && h->prm.closure == LBPWFA_LEC;
+  h->use_tma = !h->use_persist && !h->use_axi && (tma_auto || variant == 2) && tma_ok && h->ks.has_tma;
+  if (h->use_tma) {
+    cudaError_t e = h->ks.prepare_tma();
+    bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0], h->ks.tma_box) &&
+              make_pop_map(h, h->f[1].p, &h->maps[1], h->ks.tma_box);
+    if (!ok) {
+      cudaGetLastError();
+      h->use_tma = false;  // the plain kernel computes the same step
+    }
+  }
+}
+
+// The variant the run's step uses, as lbpwfa_info reports it.
+int variant_in_use(const lbpwfa_s* h) {
+  return h->use_persist ? 3 : (h->use_axi ? 5 : (h->use_march ? 4 : (h->use_tma ? 2 : 1)));
+}
+
 }  // namespace lbprt
 
 extern "C" {
@@ -503,38 +548,7 @@ int lbpwfa_create(const lbpwfa_params* p, lbpwfa_t* out) {
     cudaError_t e = h->ks.has_axi ? h->ks.prepare_axi() : cudaErrorNotSupported;
     if (e != cudaSuccess) { fail_cuda(h, e, "cudaFuncSetAttribute"); lbpwfa_destroy(h); return LBPWFA_ERR_CUDA; }
   }
-  // 3D: marching columns unless the tiled kernel is asked for (variant 1)
-  h->use_march = dim == 3 && (p->kernel_variant == 0 || p->kernel_variant == 4) && h->ks.has_march;
-  if (h->use_march && h->ks.prepare_march() != cudaSuccess) {
-    cudaGetLastError();
-    h->use_march = false;
-  }
-  const bool tma_ok = dim == 2 && p->boundary == LBPWFA_OPEN;
-  // automatic choice for LEC: the persistent refilling CTAs where the tile
-  // table marks them faster, else one TMA box per CTA; WARMC's 72-plane box
-  // leaves two CTAs per SM and the global-memory pull is faster there
-  const bool persist_auto = p->kernel_variant == 0 && p->closure == LBPWFA_LEC && h->ks.persist_auto;
-  h->use_persist = (p->kernel_variant == 3 || persist_auto) && tma_ok && h->ks.has_persist && h->num_sms > 0;
-  if (h->use_persist) {
-    cudaError_t e = h->use_axi ? h->ks.prepare_persist_axi() : h->ks.prepare_persist();
-    bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0], h->ks.per_box) &&
-              make_pop_map(h, h->f[1].p, &h->maps[1], h->ks.per_box);
-    if (!ok) {
-      cudaGetLastError();
-      h->use_persist = false;
-    }
-  }
-  const bool tma_auto = p->kernel_variant == 0 && p->closure == LBPWFA_LEC;
-  h->use_tma = !h->use_persist && !h->use_axi && (tma_auto || p->kernel_variant == 2) && tma_ok && h->ks.has_tma;
-  if (h->use_tma) {
-    cudaError_t e = h->ks.prepare_tma();
-    bool ok = e == cudaSuccess && make_pop_map(h, h->f[0].p, &h->maps[0], h->ks.tma_box) &&
-              make_pop_map(h, h->f[1].p, &h->maps[1], h->ks.tma_box);
-    if (!ok) {
-      cudaGetLastError();
-      h->use_tma = false;  // the plain kernel computes the same step
-    }
-  }
+  select_kernel(h, p->kernel_variant);
   if (!h->profile_h.empty()) {
     cudaError_t e = cudaMalloc(&h->profile_d, h->profile_h.size() * sizeof(double));
     if (e != cudaSuccess) { lbpwfa_destroy(h); return LBPWFA_ERR_OOM; }
@@ -850,7 +864,7 @@ int lbpwfa_info(lbpwfa_t h, lbpwfa_info_t* info) {
   // FP32 fields: high and low parts
   const double field_words = (ne + nbf) * (h->real_sz == 4 ? 2.0 : 1.0);
   info->bytes_per_update = 2.0 * h->NPL * h->store_sz + 2.0 * (field_words + h->NPREV) * h->real_sz;
-  info->kernel_variant = h->use_persist ? 3 : (h->use_axi ? 5 : (h->use_march ? 4 : (h->use_tma ? 2 : 1)));
+  info->kernel_variant = variant_in_use(h);
   // the method's bytes: populations, one real per field component, and the
   // WARMC previous-step theta^{0 beta}, w^beta (beta = 0..dim)
   const int nalg_prev = h->prm.closure == LBPWFA_WARMC ? 2 * (1 + dim) : 0;
@@ -1512,6 +1526,99 @@ int lbpwfa_batch_info(lbpwfa_batch_t b, lbpwfa_batch_info_t* info) {
   info->graph_steps = b->graph_steps;
   info->step = b->step;
   info->device_bytes = b->device_bytes;
+  return LBPWFA_OK;
+}
+
+int lbpwfa_autotune(lbpwfa_t h, double* ms_out) {
+  if (!h) return LBPWFA_ERR_INVALID;
+  if (ms_out)
+    for (int v = 0; v < 5; ++v) ms_out[v] = -1.0;
+  if (h->in_batch) {
+    h->err = "lbpwfa_autotune: this run belongs to a batch (lbpwfa_batch_create tunes its tiles)";
+    return LBPWFA_ERR_STATE;
+  }
+  // the candidates: the variants this run can take (axisymmetric runs report
+  // their plain kernel as 5)
+  auto takes = [&](int v) {
+    select_kernel(h, v);
+    const int u = variant_in_use(h);
+    return u == v || (v == 1 && u == 5);
+  };
+  std::string key;
+  {
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, h->device);
+    std::string k = std::string(prop.name) + "|run|" + std::to_string(h->prm.dim) + "|" +
+                    std::to_string(h->prm.closure) + "|" + std::to_string(h->prm.precision) + "|" +
+                    std::to_string(h->prm.boundary) + "|" + std::to_string(h->prm.geometry) + "|" +
+                    std::to_string(h->n[0]) + "x" + std::to_string(h->n[1]) + "x" + std::to_string(h->n[2]);
+    char buf[32];
+    std::snprintf(buf, sizeof(buf), "%016zx", std::hash<std::string>{}(k));
+    key = buf;
+  }
+  const int cached = cache_lookup(key);
+  if (cached >= 1 && cached <= 4 && takes(cached)) return LBPWFA_OK;
+  // keep the state while the candidates step it
+  const size_t pb = h->f[0].bytes, fb = h->E[0].bytes, qb = h->prev.bytes;
+  Buf snap;
+  int st = alloc(h, snap, pb + 2 * fb + qb);
+  if (st != LBPWFA_OK) {
+    h->err = "lbpwfa_autotune: no room to keep the state while tuning (" + std::to_string(pb + 2 * fb + qb) + " bytes)";
+    return st;
+  }
+  char* sp = (char*)snap.p;
+  const int cur = h->cur, have_prev = h->have_prev;
+  const long long step = h->step;
+  auto keep = [&](bool back) -> int {
+    char* dst[4] = {sp, sp + pb, sp + pb + fb, sp + pb + 2 * fb};
+    char* src[4] = {(char*)h->f[cur].p, (char*)h->E[cur].p, (char*)h->B[cur].p, (char*)h->prev.p};
+    const size_t n[4] = {pb, fb, fb, qb};
+    for (int j = 0; j < 4; ++j)
+      if (n[j]) CK(h, cudaMemcpyAsync(back ? src[j] : dst[j], back ? dst[j] : src[j], n[j], cudaMemcpyDeviceToDevice,
+                                      h->stream));
+    return LBPWFA_OK;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) st = fail_cuda(h, ce, "lbpwfa_autotune: events");
+  if (st == LBPWFA_OK) st = keep(false);
+  int best = 0;
+  double best_ms = 1e30;
+  for (int v = 1; v <= 4 && st == LBPWFA_OK; ++v) {
+    if (!takes(v)) continue;
+    // two steps to warm up, five timed, then back to the kept state
+    for (int w = 0; w < 2 && st == LBPWFA_OK; ++w) st = launch_step(h, nullptr);
+    if (st == LBPWFA_OK && (ce = cudaEventRecord(e0, h->stream)) != cudaSuccess) st = fail_cuda(h, ce, "event");
+    for (int w = 0; w < 5 && st == LBPWFA_OK; ++w) st = launch_step(h, nullptr);
+    if (st == LBPWFA_OK && (ce = cudaEventRecord(e1, h->stream)) != cudaSuccess) st = fail_cuda(h, ce, "event");
+    if (st == LBPWFA_OK && (ce = cudaEventSynchronize(e1)) != cudaSuccess) st = fail_cuda(h, ce, "event");
+    if (st == LBPWFA_OK) st = check_err_word(h);
+    float ms = 0.f;
+    if (st == LBPWFA_OK) cudaEventElapsedTime(&ms, e0, e1);
+    h->cur = cur;
+    h->step = step;
+    h->have_prev = have_prev;
+    if (st == LBPWFA_OK) st = keep(true);
+    if (st != LBPWFA_OK) break;
+    const double per = ms / 5.0;
+    if (ms_out) ms_out[v] = per;
+    if (per < best_ms) { best_ms = per; best = v; }
+  }
+  if (st == LBPWFA_OK) {
+    ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) st = fail_cuda(h, ce, "lbpwfa_autotune");
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  h->device_bytes -= snap.bytes;
+  release(snap);
+  if (st != LBPWFA_OK) {
+    select_kernel(h, h->prm.kernel_variant);
+    return st;
+  }
+  takes(best);
+  cache_store(key, best);
   return LBPWFA_OK;
 }
 

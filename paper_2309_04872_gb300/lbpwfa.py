@@ -93,7 +93,7 @@ EXPORTED = ["lbpwfa_create", "lbpwfa_step", "lbpwfa_moments", "lbpwfa_fields", "
             "lbpwfa_batch_create", "lbpwfa_batch_step", "lbpwfa_batch_member", "lbpwfa_batch_info",
             "lbpwfa_batch_destroy", "lbpwfa_record", "lbpwfa_adjoint_step", "lbpwfa_line_fit",
             "lbpwfa_gauss_residual", "lbpwfa_set_wait_limit", "lbpwfa_measure_fp64_rate",
-            "lbpwfa_create_batch"]
+            "lbpwfa_create_batch", "lbpwfa_autotune"]
 
 
 def library_path() -> str:
@@ -129,6 +129,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbpwfa_set_stream.argtypes = [vp, vp]
     L.lbpwfa_synchronize.argtypes = [vp]
     L.lbpwfa_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
+    L.lbpwfa_autotune.argtypes = [vp, _DP]
     L.lbpwfa_measure_fp64_rate.argtypes = [_DP]
     L.lbpwfa_destroy.argtypes = [vp]
     L.lbpwfa_destroy.restype = None
@@ -268,6 +269,15 @@ class Run:
 
     def synchronize(self):
         self._check(load_library().lbpwfa_synchronize(self._h), "lbpwfa_synchronize")
+
+    def autotune(self):
+        """Time every step kernel this run can take and keep the fastest
+        (lbpwfa_autotune): returns the step time in ms per variant 1..4
+        (None where not timed, every entry when the choice came from the
+        LBPWFA_TUNE_CACHE file) and the variant in use."""
+        ms = np.full(5, -1.0)
+        self._check(load_library().lbpwfa_autotune(self._h, ms.ctypes.data_as(_DP)), "lbpwfa_autotune")
+        return {v: (float(ms[v]) if ms[v] >= 0 else None) for v in range(1, 5)}, self.info().kernel_variant
 
     def set_wait_limit(self, polls: int):
         """Polls of each tile's first barrier wait before it gives up

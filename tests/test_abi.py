@@ -79,6 +79,7 @@ def test_invalid_parameters_rejected_before_any_device_work(lib_path):
     assert lib.lbpwfa_create(ctypes.byref(p), ctypes.byref(h)) == -1
     assert lib.lbpwfa_create(None, ctypes.byref(h)) == -1
     assert lib.lbpwfa_step(None, 1) == -1
+    assert lib.lbpwfa_autotune(None, None) == -1
     # the diagnostics check their handle and arguments on the host
     fp = lbpwfa.FitParams()
     out = (ctypes.c_double * 5)()
