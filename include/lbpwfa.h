@@ -213,8 +213,9 @@ int lbpwfa_step(lbpwfa_t h, int64_t nsteps);
  *   (1 + u_z^2), theta^00 = u_i u_j theta_ij; 2D WARMC only, else 0).
  * dst holds count >= popcount(mask & 0x3FFFF) * ncell doubles, on the device
  * when dst_is_device, else on the host.  A page-locked host buffer that CUDA
- * maps into the device (cudaHostAlloc, cudaMallocHost) is written in place
- * by the kernel; other host memory through a device staging buffer.  Host
+ * maps into the device (cudaHostAlloc, cudaMallocHost), 8-byte aligned and
+ * lying inside the allocation CUDA reports for it, is written in place by
+ * the kernel; other host memory through a device staging buffer.  Host
  * outputs are complete on return.  Errors: INVALID, CUDA. */
 int lbpwfa_moments(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_is_device);
 

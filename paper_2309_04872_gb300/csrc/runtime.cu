@@ -220,19 +220,43 @@ dim3 step_grid(const lbpwfa_s* h) {
               (unsigned)((h->n[2] + h->ks.ty - 1) / h->ks.ty));
 }
 
-// The device address of a caller's host buffer that the device can read and
-// write directly: page-locked memory mapped into the device's address space
-// (cudaHostAlloc, cudaMallocHost, cudaHostRegister with mapping); null for
-// pageable memory or when CUDA reports no device address for it.  The import
-// and export kernels then move the values over the host link themselves,
-// without a staging copy.
-void* mapped_host(const void* p) {
+PFN_cuPointerGetAttribute_v4000 pointer_attr_fn() {
+  static PFN_cuPointerGetAttribute_v4000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuPointerGetAttribute_v4000)p;
+  }
+  return fn;
+}
+
+// The device address of a caller's host buffer of `bytes` bytes that the
+// device can read and write directly: page-locked memory mapped into the
+// device's address space (cudaHostAlloc, cudaMallocHost, cudaHostRegister
+// with mapping), aligned for the kernels' 8-byte accesses, the whole buffer
+// inside the allocation CUDA reports for it.  Null otherwise (pageable
+// memory, or a range CUDA cannot confirm), and the caller stages the copy.
+// The import and export kernels then move the values over the host link
+// themselves, without a staging copy.
+void* mapped_host(const void* p, size_t bytes) {
+  if (reinterpret_cast<uintptr_t>(p) % alignof(double) != 0) return nullptr;
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+  const uintptr_t d = reinterpret_cast<uintptr_t>(at.devicePointer);
+  if (at.type != cudaMemoryTypeHost || d == 0 || d % alignof(double) != 0) return nullptr;
+  PFN_cuPointerGetAttribute_v4000 fn = pointer_attr_fn();
+  CUdeviceptr start = 0;
+  size_t size = 0;
+  if (!fn || fn(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)d) != CUDA_SUCCESS ||
+      fn(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)d) != CUDA_SUCCESS)
+    return nullptr;
+  if (d < start || bytes > size || d - start > size - bytes) return nullptr;
+  return at.devicePointer;
 }
 
 // Copy device results to a caller buffer (host or device).
@@ -614,7 +638,7 @@ int lbpwfa_moments(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst
   if (count < need) return LBPWFA_ERR_INVALID;
   AuxParams A = aux_params(h);
   double* out = dst;
-  double* mapped = dst_is_device ? nullptr : (double*)mapped_host(dst);
+  double* mapped = dst_is_device ? nullptr : (double*)mapped_host(dst, need * sizeof(double));
   if (mapped) {
     out = mapped;
   } else if (!dst_is_device) {
@@ -642,7 +666,7 @@ int lbpwfa_fields(lbpwfa_t h, uint32_t mask, double* dst, size_t count, int dst_
   if (count < need) return LBPWFA_ERR_INVALID;
   AuxParams A = aux_params(h);
   double* out = dst;
-  double* mapped = dst_is_device ? nullptr : (double*)mapped_host(dst);
+  double* mapped = dst_is_device ? nullptr : (double*)mapped_host(dst, need * sizeof(double));
   if (mapped) {
     out = mapped;
   } else if (!dst_is_device) {
@@ -756,9 +780,9 @@ int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double*
   // page-locked host buffers mapped into the device are read in place
   bool mapped = !src_is_device;
   if (mapped) {
-    const double* fm = f ? (const double*)mapped_host(f) : nullptr;
-    const double* Em = E ? (const double*)mapped_host(E) : nullptr;
-    const double* Bm = B ? (const double*)mapped_host(B) : nullptr;
+    const double* fm = f ? (const double*)mapped_host(f, nf * sizeof(double)) : nullptr;
+    const double* Em = E ? (const double*)mapped_host(E, nfl * sizeof(double)) : nullptr;
+    const double* Bm = B ? (const double*)mapped_host(B, nfl * sizeof(double)) : nullptr;
     mapped = (!f || fm) && (!E || Em) && (!B || Bm);
     if (mapped) { fd = fm; Ed = Em; Bd = Bm; }
   }

@@ -383,6 +383,22 @@ def test_pinned_host_buffers_are_read_and_written_in_place():
     for a, b in zip(got[0], got[1]):
         assert np.array_equal(a, b)
     assert np.abs(got[0][0][0] - 1.0).max() > 0  # a perturbed state, not the rest state
+    # buffers that start inside a larger page-locked allocation
+    def pinned_view(x, lead=1000):
+        big = torch.zeros(lead + x.size, dtype=torch.float64).pin_memory()
+        v = big[lead:].view(x.shape)
+        v.copy_(torch.from_numpy(np.ascontiguousarray(x)))
+        return big, v
+    keep = [pinned_view(a) for a in (f, E, B)]
+    with lb.Run(cfg, "fp32") as run:
+        run.set_state(*(v for _, v in keep))
+        run.step(7)
+        mb, m = pinned_view(np.zeros((3, run.ncell)), lead=517)
+        eb, e = pinned_view(np.zeros((6, run.ncell)), lead=33)
+        run.moments(0b111, out=m)
+        run.fields(0x3F, out=e)
+        assert np.array_equal(m.numpy(), got[0][0]) and np.array_equal(e.numpy(), got[0][1])
+        assert not mb[:517].any() and not eb[:33].any()  # nothing written before the view
 
 
 @pytest.mark.parametrize("closure", ["lec", "warmc"])
