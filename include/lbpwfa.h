@@ -260,7 +260,7 @@ int lbpwfa_line_fit(lbpwfa_t h, const lbpwfa_fit_params* fp, double* out);
 int lbpwfa_gauss_residual(lbpwfa_t h, const int* lo, const int* hi, double* out);
 
 /* Advected scalars A_k = sum_i f_ki (Eq. disc-moments-ade), FP64,
- * [K][ncell]; count >= K * ncell. */
+ * [K][ncell]; count >= K * ncell.  Host buffers as for lbpwfa_moments. */
 int lbpwfa_advected(lbpwfa_t h, double* dst, size_t count, int dst_is_device);
 
 /* Replace the state: f = populations at t_n after streaming, FP64
@@ -275,7 +275,8 @@ int lbpwfa_advected(lbpwfa_t h, double* dst, size_t count, int dst_is_device);
 int lbpwfa_set_state(lbpwfa_t h, const double* f, const double* E, const double* B,
                      int src_is_device);
 
-/* Read the state in the layout of lbpwfa_set_state (FP64). */
+/* Read the state in the layout of lbpwfa_set_state (FP64).  Host buffers as
+ * for lbpwfa_moments. */
 int lbpwfa_get_state(lbpwfa_t h, double* f, double* E, double* B, int dst_is_device);
 
 /* FP64 global sums over nodes, in a fixed order (deterministic):

@@ -617,14 +617,18 @@ int lbpwfa_advected(lbpwfa_t h, double* dst, size_t count, int dst_is_device) {
   if (count < need) return LBPWFA_ERR_INVALID;
   AuxParams A = aux_params(h);
   double* out = dst;
-  if (!dst_is_device) {
+  double* mapped = dst_is_device ? nullptr : (double*)mapped_host(dst, need * sizeof(double));
+  if (mapped) {
+    out = mapped;
+  } else if (!dst_is_device) {
     int r = ensure_scratch(h, need * sizeof(double));
     if (r != LBPWFA_OK) return r;
     out = (double*)h->scratch.p;
   }
   h->ks.advected(A, h->f[h->cur].p, out, h->stream);
   CK_LAUNCH(h, "advected_kernel launch");
-  if (!dst_is_device) return deliver(h, out, dst, need * sizeof(double), 0);
+  if (mapped) CK(h, cudaStreamSynchronize(h->stream));
+  else if (!dst_is_device) return deliver(h, out, dst, need * sizeof(double), 0);
   return LBPWFA_OK;
 }
 
@@ -823,16 +827,21 @@ int lbpwfa_get_state(lbpwfa_t h, double* f, double* E, double* B, int dst_is_dev
   if (!h) return LBPWFA_ERR_INVALID;
   AuxParams A = aux_params(h);
   const size_t nf = (size_t)h->K * h->Q * h->ncell, nfl = 3 * (size_t)h->ncell;
+  bool any_mapped = false;
   if (f) {
     double* out = f;
-    if (!dst_is_device) {
+    double* mapped = dst_is_device ? nullptr : (double*)mapped_host(f, nf * 8);
+    if (mapped) {
+      out = mapped;
+      any_mapped = true;
+    } else if (!dst_is_device) {
       int r = ensure_scratch(h, nf * 8);
       if (r != LBPWFA_OK) return r;
       out = (double*)h->scratch.p;
     }
     h->ks.export_pops(A, h->f[h->cur].p, out, h->stream);
     CK_LAUNCH(h, "export_pops_kernel launch");
-    if (!dst_is_device) {
+    if (!dst_is_device && !mapped) {
       int r = deliver(h, out, f, nf * 8, 0);
       if (r != LBPWFA_OK) return r;
     }
@@ -842,7 +851,11 @@ int lbpwfa_get_state(lbpwfa_t h, double* f, double* E, double* B, int dst_is_dev
     double* dst = which == 0 ? E : B;
     if (!dst) continue;
     double* out = dst;
-    if (!dst_is_device) {
+    double* mapped = dst_is_device ? nullptr : (double*)mapped_host(dst, nfl * 8);
+    if (mapped) {
+      out = mapped;
+      any_mapped = true;
+    } else if (!dst_is_device) {
       int r = ensure_scratch(h, nfl * 8);
       if (r != LBPWFA_OK) return r;
       out = (double*)h->scratch.p;
@@ -851,11 +864,12 @@ int lbpwfa_get_state(lbpwfa_t h, double* f, double* E, double* B, int dst_is_dev
                         make_int4(0, 1, 2, 0),
                         make_int4(which, which, which, 0), out, h->stream);
     CK_LAUNCH(h, "export_fields_kernel launch");
-    if (!dst_is_device) {
+    if (!dst_is_device && !mapped) {
       int r = deliver(h, out, dst, nfl * 8, 0);
       if (r != LBPWFA_OK) return r;
     }
   }
+  if (any_mapped) CK(h, cudaStreamSynchronize(h->stream));
   return LBPWFA_OK;
 }
 

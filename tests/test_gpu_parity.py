@@ -399,6 +399,17 @@ def test_pinned_host_buffers_are_read_and_written_in_place():
         run.fields(0x3F, out=e)
         assert np.array_equal(m.numpy(), got[0][0]) and np.array_equal(e.numpy(), got[0][1])
         assert not mb[:517].any() and not eb[:33].any()  # nothing written before the view
+        # the state and the advected scalars read back into page-locked buffers
+        import ctypes
+        f_np, E_np, B_np = run.get_state()
+        fp, Ep, Bp = (torch.zeros(x.shape, dtype=torch.float64).pin_memory() for x in (f_np, E_np, B_np))
+        st = lb.load_library().lbpwfa_get_state(run._h, *(ctypes.c_void_p(x.data_ptr()) for x in (fp, Ep, Bp)), 0)
+        assert st == 0
+        for a, b in ((fp, f_np), (Ep, E_np), (Bp, B_np)):
+            assert np.array_equal(a.numpy(), b)
+        ap = torch.zeros((run.K, run.ncell), dtype=torch.float64).pin_memory()
+        run.advected(out=ap)
+        assert np.array_equal(ap.numpy(), run.advected())
 
 
 @pytest.mark.parametrize("closure", ["lec", "warmc"])
