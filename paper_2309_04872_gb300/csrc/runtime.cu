@@ -1620,7 +1620,7 @@ int lbpwfa_autotune(lbpwfa_t h, double* ms_out) {
   cudaError_t ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
   if (ce != cudaSuccess) st = fail_cuda(h, ce, "lbpwfa_autotune: events");
-  if (st == LBPWFA_OK) st = keep(false);
+  const bool kept = st == LBPWFA_OK && (st = keep(false)) == LBPWFA_OK;
   int best = 0;
   double best_ms = 1e30;
   for (int v = 1; v <= 4 && st == LBPWFA_OK; ++v) {
@@ -1634,19 +1634,19 @@ int lbpwfa_autotune(lbpwfa_t h, double* ms_out) {
     if (st == LBPWFA_OK) st = check_err_word(h);
     float ms = 0.f;
     if (st == LBPWFA_OK) cudaEventElapsedTime(&ms, e0, e1);
+    // back to the kept state, after a failed step as well
     h->cur = cur;
     h->step = step;
     h->have_prev = have_prev;
-    if (st == LBPWFA_OK) st = keep(true);
+    const int back = kept ? keep(true) : LBPWFA_OK;
+    if (st == LBPWFA_OK) st = back;
     if (st != LBPWFA_OK) break;
     const double per = ms / 5.0;
     if (ms_out) ms_out[v] = per;
     if (per < best_ms) { best_ms = per; best = v; }
   }
-  if (st == LBPWFA_OK) {
-    ce = cudaStreamSynchronize(h->stream);
-    if (ce != cudaSuccess) st = fail_cuda(h, ce, "lbpwfa_autotune");
-  }
+  ce = cudaStreamSynchronize(h->stream);  // the copies back read the kept state
+  if (st == LBPWFA_OK && ce != cudaSuccess) st = fail_cuda(h, ce, "lbpwfa_autotune");
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   h->device_bytes -= snap.bytes;
